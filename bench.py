@@ -1,0 +1,453 @@
+#!/usr/bin/env python
+"""Benchmark: mean TFLOP/s and roughness of the BF16 NN GEMM landscape over
+the 32,768-cell grid (M, N, K) in {128, ..., 4096}^3, plain fixed tile versus
+the smoothed stack (autotuned best-of tiles and split factors + the DP
+padding/splitting plan, O(1) lookup, fused execution), on one GB300.
+
+Setup (not timed, "offline once per hardware/software stack"): the autotune
+sweep times all 24 kernel variants (6 tiles x split-K 1/2/4/8) on every cell
+and builds the plan tables.  One timed step re-measures, for every cell, the
+plain fixed 128x128 tile and the smoothed plan with the paper's protocol (one
+warm-up launch, then the mean of 5 back-to-back launches between CUDA events),
+then computes both surfaces' mean and roughness in the library.
+
+Prints one JSON line (rank 0).  --impl reference times the CPU oracle instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synthetic  # noqa: E402
+
+METRIC = "mean TFLOP/s & roughness on 32,768-shape BF16 sweep, plain vs smoothed; p50/p99"
+STEP = 128
+COUNT = 32
+FIXED_TILE = 1          # 128 x 128, the single fixed tile of the small-sweep configuration
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=3)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--count", type=int, default=COUNT, help="grid points per axis (32 = the full grid)")
+    p.add_argument("--no-extras", action="store_true", help="skip the ladder / cross-tile / e2e / CPU sections")
+    p.add_argument("--out", default=None, help="also write the JSON line (and surfaces) here")
+    return p.parse_args()
+
+
+def cell_sizes(count):
+    g = np.arange(1, count + 1) * STEP
+    M, N, K = np.meshgrid(g, g, g, indexing="ij")
+    return M.ravel().astype(np.int64), N.ravel().astype(np.int64), K.ravel().astype(np.int64)
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def stats_of(rg, grid, t_ns):
+    tf, r, mean = rg.rg_surface_stats(grid, t_ns)
+    return tf, r, mean
+
+
+def summarize(tf, r, mean):
+    return {"mean_tflops": mean, "p50_tflops": float(np.percentile(tf, 50)), "p99_tflops": float(np.percentile(tf, 99)),
+            "p01_tflops": float(np.percentile(tf, 1)), "max_tflops": float(tf.max()),
+            "R_N_slice": r["R_N_slice"], "R_3D": r["R_3D"], "R_M": r["R_M"], "R_N": r["R_N"], "R_K": r["R_K"]}
+
+
+def sawtooth_period(series):
+    """Lag (in grid steps, 1..8) of the largest autocorrelation of the step-to-step changes."""
+    d = np.diff(np.asarray(series, dtype=np.float64))
+    d = d - d.mean()
+    best, arg = -np.inf, None
+    for lag in range(1, 9):
+        if lag >= len(d):
+            break
+        c = float(np.dot(d[:-lag], d[lag:]) / (np.linalg.norm(d[:-lag]) * np.linalg.norm(d[lag:]) + 1e-30))
+        if c > best:
+            best, arg = c, lag
+    return arg, best
+
+
+def cpu_baseline(count, budget_s=15.0, seed=0):
+    """The oracle's FP64 GEMM timed on this host's cores on a bounded, seeded sample of cells."""
+    from oracle import gemm as og
+    cells = synthetic.uniform_cells(4096, (count, count, count), seed=seed)
+    t_start = time.perf_counter()
+    vals, flops, secs, used = [], 0.0, 0.0, []
+    for a, b, c in cells:
+        M, N, K = (int(a) + 1) * STEP, (int(b) + 1) * STEP, (int(c) + 1) * STEP
+        ab, bb = synthetic.operands_bf16(M, N, K, seed=0)
+        A, B = og.bf16_bits_to_f64(ab), og.bf16_bits_to_f64(bb)
+        t0 = time.perf_counter()
+        og.gemm_f64(A, B)
+        dt = time.perf_counter() - t0
+        vals.append(2.0 * M * N * K / dt / 1e12)
+        flops += 2.0 * M * N * K
+        secs += dt
+        used.append((M, N, K))
+        if time.perf_counter() - t_start > budget_s:
+            break
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    return {"value": float(np.mean(vals)), "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
+            "sample": f"{len(used)} cells drawn uniformly from the {count}^3 grid (seed {seed}); oracle FP64 "
+                      f"GEMM (numpy matmul, float64) per cell; value = mean per-cell TFLOP/s; "
+                      f"aggregate {flops / secs / 1e12:.4f} TFLOP/s over {secs:.1f} s",
+            "aggregate_tflops": flops / secs / 1e12}
+
+
+def reference_arm(args):
+    world, rank, _ = dist_setup()
+    if rank != 0:
+        return 0
+    from oracle import gemm as og
+    count = args.count
+    cells = synthetic.uniform_cells(64, (count, count, count), seed=1)
+    # size each step to a few seconds of CPU work and at most ~2 GB of float64 operands
+    per_step, t_acc, bytes_acc = [], 0.0, 0
+    for a, b, c in cells:
+        M, N, K = (int(a) + 1) * STEP, (int(b) + 1) * STEP, (int(c) + 1) * STEP
+        if bytes_acc + 8 * (M * K + K * N) > 2 << 30:
+            continue
+        ab, bb = synthetic.operands_bf16(M, N, K, seed=0)
+        op = (M, N, K, og.bf16_bits_to_f64(ab), og.bf16_bits_to_f64(bb))
+        s0 = time.perf_counter()
+        og.gemm_f64(op[3], op[4])
+        t_acc += time.perf_counter() - s0
+        bytes_acc += 8 * (M * K + K * N)
+        per_step.append(op)
+        if t_acc > 4.0:
+            break
+
+    def step():
+        vals = []
+        for M, N, K, A, B in per_step:
+            s = time.perf_counter()
+            og.gemm_f64(A, B)
+            vals.append(2.0 * M * N * K / (time.perf_counter() - s) / 1e12)
+        return float(np.mean(vals))
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    vals = [step() for _ in range(args.steps)]
+    elapsed = time.perf_counter() - t0
+    value = float(np.mean(vals))
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    line = {"metric": METRIC, "value": value, "unit": "TFLOP/s", "impl": "reference", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": elapsed / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "replicas", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": f"BF16 NN GEMM landscape {count}^3 cells, "
+                                                        f"FP64 CPU oracle on a {len(per_step)}-cell sample"},
+            "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{len(per_step)} cells drawn uniformly from the grid (seed 1), "
+                                       f"FP64 numpy GEMM each, mean per-cell TFLOP/s"},
+            "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return reference_arm(args)
+    world, rank, local = dist_setup()
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2605_29752_gb300 import rg
+
+    count = args.count
+    grid = rg.make_grid((STEP, STEP, count))
+    ncell = count ** 3
+    Mx = STEP * count
+    Mv, Nv, Kv = cell_sizes(count)
+    flops = 2.0 * Mv * Nv * Kv
+    dev = torch.device("cuda", local)
+
+    def dev_bf16(bits):
+        return torch.from_numpy(bits.view(np.int16)).to(dev).view(torch.bfloat16)
+
+    a_bits = synthetic.bf16_uniform_stream(0, synthetic.TAG_A, Mx * Mx)
+    b_bits = synthetic.bf16_uniform_stream(0, synthetic.TAG_B, Mx * Mx)
+    A, B = dev_bf16(a_bits), dev_bf16(b_bits)
+    C = torch.zeros(Mx * Mx, device=dev, dtype=torch.float32)
+    ctx = rg.rg_init(local)
+    sms = rg.rg_sm_count(ctx)
+
+    # ---------------- offline autotune (setup)
+    t_setup = time.perf_counter()
+    all_v = list(range(rg.RG_NUM_VARIANTS))
+    T0v = rg.rg_sweep(ctx, grid, all_v, A, B, C)
+    s1_rows = [rg.variant(t, 1) for t in range(rg.RG_NUM_TILES)]
+    plan_smooth = rg.rg_plan_build(grid, T0v, all_v)
+    setup_s = time.perf_counter() - t_setup
+    fixed_v = rg.variant(FIXED_TILE, 1)
+
+    def one_step():
+        tp = rg.rg_sweep(ctx, grid, [fixed_v], A, B, C)[0]
+        ts = rg.rg_sweep(ctx, grid, [0], A, B, C, plan=plan_smooth)[0]
+        return tp, ts
+
+    for _ in range(args.warmup):
+        one_step()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    n_launch0 = rg.rg_launch_count(ctx)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    results = []
+    with ClockSampler(local) as clk:
+        ev0.record()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            results.append(one_step())
+        ev1.record()
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+    if dist:
+        dist.barrier()
+    n_launch = rg.rg_launch_count(ctx) - n_launch0
+    step_ms = ev0.elapsed_time(ev1) / args.steps
+    if dist:
+        t = torch.tensor([step_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        step_ms = float(t.item())
+
+    plain = [summarize(*stats_of(rg, grid, tp)) for tp, _ in results]
+    smooth = [summarize(*stats_of(rg, grid, ts)) for _, ts in results]
+    value = float(np.mean([s["mean_tflops"] for s in smooth]))
+    last_p, last_s = results[-1]
+    agg_flops = float(flops.sum())
+    agg_smooth = agg_flops / (last_s.astype(np.float64).sum() * 1e-9) / 1e12
+    agg_plain = agg_flops / (last_p.astype(np.float64).sum() * 1e-9) / 1e12
+
+    peaks = {}
+    pk_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pk_path):
+        peaks = json.load(open(pk_path))
+    p_burst = peaks.get("bf16_tflops", 1900.7 if not peaks else None) or 1900.7
+    peak_src = "measured" if peaks else "fallback"
+
+    # best single cell of the autotune table
+    T0s = T0v.min(axis=0)
+    best_tf = flops / (T0s * 1e3)
+    bi = int(np.argmax(best_tf))
+    line = {
+        "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True,
+        "scaling": "replicas" if world > 1 else "weak", "vs_baseline": None, "dtype": "bf16",
+        "data": "synthetic",
+        "config": {"workload": f"BF16 NN GEMM landscape, (M,N,K) in {{128..{Mx} step 128}}^3 = {ncell} cells, "
+                               f"U[-1,1) BF16 operands (seed 0), FP32 accumulate/output",
+                   "smoothed": "best-of-24 autotune (6 tiles x split-K 1/2/4/8) + DP pad/split plan, O(1) lookup",
+                   "plain": "fixed 128x128 tile, split 1",
+                   "timing": "per cell: 1 warm-up launch, device spin, mean of 5 back-to-back launches between "
+                             "CUDA events (paper protocol); operands of small cells stay L2-resident across the "
+                             "5 launches (no flush); one step touches far more than L2",
+                   "parallelism": "single GPU" if world == 1 else f"{world} independent replicas"},
+        "plain": {k: float(np.mean([p[k] for p in plain])) for k in plain[0]},
+        "smoothed": {k: float(np.mean([s[k] for s in smooth])) for k in smooth[0]},
+        "roughness_cut_pct": 100.0 * (1 - np.mean([s["R_N_slice"] for s in smooth]) /
+                                      np.mean([p["R_N_slice"] for p in plain])),
+        "mean_gain_pct": 100.0 * (value / np.mean([p["mean_tflops"] for p in plain]) - 1),
+        "roofline": {"bound": "tensor", "achieved": agg_smooth, "peak": p_burst, "unit": "TFLOP/s",
+                     "frac": agg_smooth / p_burst, "traffic": None,
+                     "note": f"all GEMM launches of one smoothed pass: useful 2MNK flops / summed per-cell "
+                             f"device time; peak = {peak_src} bf16 burst"},
+        "plain_aggregate_tflops": agg_plain,
+        "peak_cell": {"M": int(Mv[bi]), "N": int(Nv[bi]), "K": int(Kv[bi]), "tflops": float(best_tf[bi]),
+                      "variant": rg.variant_name(int(T0v[:, bi].argmin())), "frac": float(best_tf[bi]) / p_burst},
+        "gpu_launches": int(n_launch),
+        "sm_count": sms,
+        "setup_s": setup_s,
+        "clocks": clk.summary(),
+    }
+
+    if not args.no_extras and rank == 0:
+        line.update(extras(args, rg, ctx, grid, T0v, plan_smooth, A, B, C, flops, Mv, Nv, Kv, dev, a_bits, b_bits,
+                           s1_rows, fixed_v, p_burst, sms))
+    rg.rg_plan_free(plan_smooth)
+    rg.rg_destroy(ctx)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+        if args.out:
+            with open(args.out, "w") as f:
+                json.dump(line, f, indent=1)
+            np.savez_compressed(os.path.splitext(args.out)[0] + "_surfaces.npz", T0v=T0v, plain=last_p,
+                                smooth=last_s)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def extras(args, rg, ctx, grid, T0v, plan_smooth, A, B, C, flops, Mv, Nv, Kv, dev, a_bits, b_bits, s1_rows,
+           fixed_v, p_burst, sms):
+    import torch
+    out = {}
+    count = args.count
+    # ---- ladder: fixed -> best-of-6 -> DP pad -> DP split+pad -> autotuner + DP (Sec. 7.5, Table 10)
+    ladder = {}
+    tf, r, m = rg.rg_surface_stats(grid, T0v[fixed_v])
+    ladder["fixed_128x128"] = summarize(tf, r, m)
+    T6 = T0v[s1_rows]
+    tf, r, m = rg.rg_surface_stats(grid, T6.min(axis=0))
+    ladder["best_of_6"] = summarize(tf, r, m)
+    tf, r, m = rg.rg_surface_stats(grid, T0v.min(axis=0))
+    ladder["best_of_24_autotune"] = summarize(tf, r, m)
+    for name, rows, flags in (("dp_pad_on_best_of_6", s1_rows, rg.RG_PLAN_PAD_ONLY),
+                              ("dp_split_pad_on_best_of_6", s1_rows, 0),
+                              ("dp_split_pad_on_fixed", [fixed_v], 0)):
+        h = rg.rg_plan_build_ex(grid, T0v[rows], rows, flags)
+        t = rg.rg_plan_tables(h)
+        tf, r, m = rg.rg_surface_stats(grid, t["T2"])
+        pred = summarize(tf, r, m)
+        meas = rg.rg_sweep(ctx, grid, [0], A, B, C, plan=h)[0]
+        tf, r, m = rg.rg_surface_stats(grid, meas)
+        ladder[name] = {"predicted": pred, "measured": summarize(tf, r, m)}
+        rg.rg_plan_free(h)
+    t = rg.rg_plan_tables(plan_smooth)
+    tf, r, m = rg.rg_surface_stats(grid, t["T2"])
+    ladder["autotune_dp_split_pad_predicted"] = summarize(tf, r, m)
+    out["ladder"] = ladder
+    # ---- DP action distribution at the largest K (Sec. 7.3, Table 9)
+    act = t["action"][:, :, -1].ravel()
+    tgt = t["target"][:, :, -1].reshape(-1, 3)
+    cells_k = np.array([(a, b, count - 1) for a in range(count) for b in range(count)])
+    padded = np.any(tgt != cells_k, axis=1)
+    out["dp_actions_at_kmax"] = {"as_is": float(np.mean((act == 0) & ~padded)), "pad": float(np.mean((act == 0) & padded)),
+                                 "split_M": float(np.mean(act == 1)), "split_N": float(np.mean(act == 2)),
+                                 "split_K": float(np.mean(act == 3))}
+    vs = t["vstar"].ravel()
+    out["autotune_winners"] = {rg.variant_name(v): float(np.mean(vs == v)) for v in sorted(set(vs.tolist()))}
+    # ---- cross-tile N sweep at M = K = 2048 (Sec. 6.3): sawtooth period per tile
+    ia = ik = 2048 // STEP - 1
+    if ia < count:
+        ct = {}
+        for tile in range(rg.RG_NUM_TILES):
+            v = rg.variant(tile, 1)
+            t_line = T0v[v].reshape(count, count, count)[ia, :, ik]
+            tfl = 2.0 * 2048 * 2048 * (np.arange(1, count + 1) * STEP) / (t_line * 1e3)
+            lag, corr = sawtooth_period(tfl)
+            ct[rg.variant_name(v)] = {"period_steps": lag, "autocorr": corr, "mean": float(tfl.mean()),
+                                      "roughness": float(np.mean(np.abs(np.diff(tfl))))}
+        out["cross_tile_N_at_M_K_2048"] = ct
+    # ---- e2e: host buffers through the public API (H2D, plan GEMM, D2H per cell)
+    out["e2e"] = e2e(rg, ctx, plan_smooth, a_bits, b_bits, dev, count)
+    # ---- CPU oracle baseline on this host
+    out["cpu_baseline"] = cpu_baseline(count)
+    return out
+
+
+def e2e(rg, ctx, plan, a_bits, b_bits, dev, count, ncells=96):
+    import torch
+    cells = synthetic.uniform_cells(ncells, (count, count, count), seed=7)
+    Mx = STEP * count
+    ha = torch.from_numpy(a_bits.view(np.int16)).pin_memory()
+    hb = torch.from_numpy(b_bits.view(np.int16)).pin_memory()
+    hc = torch.empty(Mx * Mx, dtype=torch.float32).pin_memory()
+    da = torch.empty(Mx * Mx, dtype=torch.int16, device=dev)
+    db = torch.empty(Mx * Mx, dtype=torch.int16, device=dev)
+    dc = torch.empty(Mx * Mx, dtype=torch.float32, device=dev)
+    vals, h2d, d2h = [], 0, 0
+    stream = torch.cuda.current_stream()
+    for rep in range(2):                              # first pass warms up
+        vals = []
+        h2d = d2h = 0
+        for a, b, c in cells:
+            M, N, K = (int(a) + 1) * STEP, (int(b) + 1) * STEP, (int(c) + 1) * STEP
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            da[:M * K].copy_(ha[:M * K], non_blocking=True)
+            db[:K * N].copy_(hb[:K * N], non_blocking=True)
+            rg.rg_gemm_plan(ctx, plan, M, N, K, da, K, db, N, dc, N, stream=stream)
+            hc[:M * N].copy_(dc[:M * N], non_blocking=True)
+            e1.record()
+            e1.synchronize()
+            vals.append(2.0 * M * N * K / (e0.elapsed_time(e1) * 1e-3) / 1e12)
+            h2d += 2 * M * K + 2 * K * N
+            d2h += 4 * M * N
+    return {"value": float(np.mean(vals)), "unit": "TFLOP/s", "h2d_bytes_per_step": int(h2d),
+            "d2h_bytes_per_step": int(d2h),
+            "sample": f"{ncells} cells drawn uniformly (seed 7); per cell pinned-host A,B -> device, "
+                      f"rg_gemm_plan, C -> pinned host, timed with CUDA events; mean per-cell TFLOP/s"}
+
+
+if __name__ == "__main__":
+    sys.exit(main())

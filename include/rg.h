@@ -1,0 +1,214 @@
+/*
+ * rg.h -- C ABI of the GB300 GEMM landscape-smoothing library ("rg" = rugged
+ * GEMM).  The operations follow the problem statement of "From Roofline to
+ * Ruggedness: Decomposing and Smoothing the GEMM Performance Landscape"
+ * (arXiv 2605.29752):
+ *
+ *   C = A * B, A is M x K, B is K x N, C is M x N, all row-major ("NN"),
+ *   BF16 operands, FP32 accumulation and output            (Sec. 2.2, Sec. 7.1)
+ *   achieved TFLOP/s = 2 M N K / (t 1e12)                   (Sec. 2, definitions)
+ *   roughness = mean |T_{i+1} - T_i| along one axis         (Sec. 2, definitions)
+ *   T0 -> T1 (padding) -> T2 (splitting) plan table, O(1) lookup   (Sec. 7.1)
+ *   dynamic best-of-tiles selection                          (Sec. 6.4)
+ *
+ * Conventions shared by every call:
+ *   - Every call returns an int status (RG_OK or a negative RG_ERR_*); no call
+ *     aborts the process.  rg_strerror() names a code; rg_last_error() gives
+ *     the calling thread's last detailed message.
+ *   - Device pointers are plain CUDA device addresses (for example
+ *     torch.Tensor.data_ptr()); the caller owns them and keeps them valid
+ *     until the stream work that uses them has finished.
+ *   - Calls that take a stream enqueue on it and return without waiting
+ *     (stream = NULL means the legacy default stream).  rg_sweep,
+ *     rg_plan_build and rg_check synchronise.
+ *   - Alignment (TMA): A, B and C must be 16-byte aligned, lda and ldb
+ *     multiples of 8 elements, ldc a multiple of 4 elements; otherwise
+ *     RG_ERR_ALIGN.  lda >= K, ldb >= N, ldc >= N.
+ *   - The library owns rg_ctx (device workspace for split-K partials, tile
+ *     tickets, the device error word) and rg_plan objects.
+ *   - One rg_ctx serves one device.  Calls that use split-K (split > 1) share
+ *     the context's workspace: enqueue them on one stream (or otherwise order
+ *     them); overlapping split-K launches on one context race.
+ */
+#ifndef RG_H
+#define RG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---- */
+enum {
+  RG_OK = 0,
+  RG_ERR_INVALID = -1,        /* bad argument (null pointer, negative size, bad id)  */
+  RG_ERR_ALIGN = -2,          /* pointer or leading dimension violates TMA alignment */
+  RG_ERR_SHAPE = -3,          /* shape outside the plan grid / workspace capacity    */
+  RG_ERR_OOM = -4,            /* device or host allocation failed                    */
+  RG_ERR_CUDA = -5,           /* a CUDA runtime or driver call failed                */
+  RG_ERR_TIMEOUT = -6,        /* a bounded device wait expired (kernel returned)     */
+  RG_ERR_PLAN_MISMATCH = -7,  /* plan file header does not match                     */
+  RG_ERR_ADMISSION = -8,      /* serving: request can never fit the HBM budget       */
+  RG_ERR_NO_DEVICE = -9       /* no usable sm_103 device                             */
+};
+
+/* ---- kernel variants ----
+ * Six output tiles (BM x BN), each with an in-kernel split-K factor S in
+ * {1, 2, 4, 8}.  variant id = tile * RG_NUM_SPLITS + log2(S).  Variant ids
+ * are ordered tile-major, then by S; ties in best-of selection go to the
+ * lowest id.                                                   (Sec. 6.1, 6.4) */
+enum {
+  RG_TILE_128x64 = 0, RG_TILE_128x128 = 1, RG_TILE_128x256 = 2,
+  RG_TILE_256x64 = 3, RG_TILE_256x128 = 4, RG_TILE_256x256 = 5,
+  RG_NUM_TILES = 6
+};
+#define RG_NUM_SPLITS 4
+#define RG_NUM_VARIANTS (RG_NUM_TILES * RG_NUM_SPLITS)
+#define RG_VARIANT(tile, log2_split) ((tile) * RG_NUM_SPLITS + (log2_split))
+
+typedef struct rg_ctx rg_ctx;
+typedef struct rg_plan rg_plan;
+
+/* One grid axis: sizes start, start + step, ..., start + (count-1) * step. */
+typedef struct { int32_t start, step, count; } rg_axis;
+/* The (M, N, K) grid.  Cell (a, b, c) has linear index (a * n.count + b) * k.count + c. */
+typedef struct { rg_axis m, n, k; } rg_grid;
+
+/* One leaf of a plan: run the box [m0, m0+m) x [n0, n0+n) x [k0, k0+k) of the
+ * problem as if it were the padded problem pm x pn x pk (pm >= m, ...), with
+ * kernel variant `variant`.  beta = 0 writes C, beta = 1 adds into C.  A leaf
+ * may start once every leaf with a lower phase has finished.    (Sec. 7.1) */
+typedef struct {
+  int32_t variant;
+  int32_t beta;
+  int32_t phase;
+  int32_t reserved;
+  int64_t m0, n0, k0;
+  int64_t m, n, k;
+  int64_t pm, pn, pk;
+} rg_leaf;
+
+/* Sweep options (Sec. 3: each configuration's time is the mean of 5 timed
+ * launches after one discarded warm-up launch; Sec. 5.4: randomised order). */
+typedef struct {
+  int32_t reps;               /* timed launches per (variant, cell); default 5       */
+  int32_t warmup;             /* untimed launches before them; default 1             */
+  int32_t global_warmup;      /* launches before the whole sweep; default 5          */
+  int32_t shuffle;            /* 1: randomised (variant, cell) order; default 1      */
+  uint64_t seed;              /* shuffle seed; default 0                             */
+  int64_t spin_ns;            /* device spin before each timed group, per queued launch,
+                                 so the launches queue behind it; default 4000       */
+  int32_t prune_splits;       /* 1: skip split-K variants (S > 1) on cells where the
+                                 unsplit tile count already fills the SMs or a split
+                                 would get fewer than 2 K blocks; their entries are
+                                 set to RG_T_UNMEASURED; default 1                   */
+  int32_t reserved;
+} rg_sweep_opts;
+/* Time entry of a (variant, cell) pair the sweep did not measure: larger than
+ * any real time, so best-of selection never picks it. */
+#define RG_T_UNMEASURED ((int64_t)1 << 60)
+
+/* ---- library / context ---- */
+const char* rg_version(void);
+const char* rg_strerror(int status);
+/* Last detailed error message of the calling thread ("" if none). */
+const char* rg_last_error(void);
+void rg_sweep_opts_default(rg_sweep_opts* opts);
+
+/* Create a context on CUDA device `device`.  workspace_bytes sizes the split-K
+ * partial buffer (0 = default 512 MiB, enough for S = 8 at 4096 x 4096).
+ * Fails with RG_ERR_NO_DEVICE unless the device is compute capability 10.3. */
+int rg_init(int device, int64_t workspace_bytes, rg_ctx** out);
+void rg_destroy(rg_ctx* ctx);
+/* Number of SMs of the context's device. */
+int rg_sm_count(const rg_ctx* ctx, int32_t* out);
+/* Synchronise the stream, then read and clear the device error word.
+ * Returns RG_ERR_TIMEOUT if a kernel gave up a bounded wait since the last check. */
+int rg_check(rg_ctx* ctx, void* stream);
+/* Set the bounded-wait budget in GPU clock cycles for later launches
+ * (default 2e9, about a second).  A test may set it tiny to force the timeout path. */
+int rg_set_timeout_cycles(rg_ctx* ctx, int64_t cycles);
+/* Failure-path testing: while enabled, every GEMM launch of this context first
+ * makes its MMA warp wait on a barrier that nothing arrives on, so that bounded
+ * wait expires after the timeout budget; the kernel then records the error,
+ * lets its in-flight copies land, releases TMEM and returns, and rg_check
+ * reports RG_ERR_TIMEOUT.  Off by default. */
+int rg_set_test_stall(rg_ctx* ctx, int32_t enable);
+/* Number of kernel launches this context has enqueued so far (GEMM kernels and
+ * the sweep's spin kernels). */
+int rg_launch_count(const rg_ctx* ctx, int64_t* out);
+
+/* ---- GEMM (Sec. 2.2; variants Sec. 6.1; fused padding / split-K Sec. 7.1) ----
+ * C = A * B (beta = 0) or C += A * B (beta = 1).  variant in [0, RG_NUM_VARIANTS).
+ * A: M x K BF16 (lda), B: K x N BF16 (ldb), C: M x N FP32 (ldc), device memory.
+ * (pm, pn, pk) >= (M, N, K) run the launch as the zero-padded problem of that
+ * size (pass 0 for "same as M, N, K"); the padding is never materialised:
+ * out-of-range operand reads are zero-filled and out-of-range outputs dropped.
+ * M, N or K == 0: nothing to compute (C untouched if M or N is 0; C = 0 for
+ * K == 0 with beta = 0). */
+int rg_gemm(rg_ctx* ctx, int64_t M, int64_t N, int64_t K,
+            const void* A, int64_t lda, const void* B, int64_t ldb,
+            float* C, int64_t ldc, int32_t variant, int32_t beta,
+            int64_t pm, int64_t pn, int64_t pk, void* stream);
+
+/* ---- plan table (Sec. 7.1, host) ----
+ * T0_ns: [n_variants][cells] int64 nanoseconds (cells in the grid's linear
+ * order), variant_ids[v] the library variant measured in row v.  Builds
+ * best-of selection, T1 (padding), T2 (splitting) and every cell's leaf list.
+ * The grid must have start == step on every axis (whole multiples of the step). */
+int rg_plan_build(const rg_grid* grid, const int64_t* T0_ns, int32_t n_variants,
+                  const int32_t* variant_ids, rg_plan** out);
+/* As rg_plan_build with flags: RG_PLAN_PAD_ONLY stops after T1 (padding only:
+ * T2 = T1, every action "keep"), the "DP pad" stage of the paper's ladder
+ * (Sec. 7.5, Table 10).  flags = 0 is rg_plan_build. */
+#define RG_PLAN_PAD_ONLY 1
+int rg_plan_build_ex(const rg_grid* grid, const int64_t* T0_ns, int32_t n_variants,
+                     const int32_t* variant_ids, int32_t flags, rg_plan** out);
+void rg_plan_free(rg_plan* plan);
+int rg_plan_grid(const rg_plan* plan, rg_grid* out);
+/* Copy out the plan's tables (any pointer may be NULL), each [cells] in the
+ * grid's linear order: T0* (best-of time), vstar (its variant id), T1, the pad
+ * target cell (3 ints per cell), T2, action (0 keep, 1 split M, 2 split N,
+ * 3 split K) and q (second piece size in steps). */
+int rg_plan_tables(const rg_plan* plan, int64_t* T0s, int32_t* vstar, int64_t* T1,
+                   int32_t* target3, int64_t* T2, int32_t* action, int32_t* q);
+/* O(1) lookup: the cell that covers (M, N, K) (each size rounded up to the
+ * grid) and its leaves (a pointer into the plan, valid until rg_plan_free).
+ * RG_ERR_SHAPE if a size exceeds the grid.  t2_ns may be NULL. */
+int rg_plan_lookup(const rg_plan* plan, int64_t M, int64_t N, int64_t K,
+                   const rg_leaf** leaves, int32_t* n_leaves, int64_t* t2_ns);
+/* Execute the plan for C = A * B: lookup, then the cell's leaves in order on
+ * `stream`, each clipped to (M, N, K).  Operand conventions as rg_gemm. */
+int rg_gemm_plan(rg_ctx* ctx, const rg_plan* plan, int64_t M, int64_t N, int64_t K,
+                 const void* A, int64_t lda, const void* B, int64_t ldb,
+                 float* C, int64_t ldc, void* stream);
+/* Binary plan file with a header (magic, version, grid, variant set, device
+ * name, SM count) and an FNV-1a checksum of the body.  rg_plan_load checks
+ * the header against `ctx`'s device (ctx may be NULL to skip the device check). */
+int rg_plan_save(const rg_plan* plan, const rg_ctx* ctx, const char* path);
+int rg_plan_load(const char* path, const rg_ctx* ctx, rg_plan** out);
+
+/* ---- surface statistics (Sec. 2 definitions; Sec. 8.6 conventions; host) ----
+ * tflops_out[c] = (2.0*M*N*K) / (t_ns[c] * 1e3) per cell (may be NULL);
+ * rough_out = {R_M, R_N, R_K, R_3D = (R_M+R_N+R_K)/3, R_N on the largest-K slice};
+ * mean_out = mean TFLOP/s.  Sums are correctly rounded, so the results do not
+ * depend on summation order.  t_ns must be > 0. */
+int rg_surface_stats(const rg_grid* grid, const int64_t* t_ns, double* tflops_out,
+                     double rough_out[5], double* mean_out);
+
+/* ---- sweep (Sec. 3, Sec. 5.4) ----
+ * Times every (variant, cell) pair: for each, `warmup` untimed launches, a
+ * short device spin, then `reps` launches between two CUDA events;
+ * t_ns_out[v][cell] = round(elapsed / reps) in ns.  Operands of cell (M, N, K)
+ * are the contiguous prefixes A[0 : M*K] (lda = K) and B[0 : K*N] (ldb = N);
+ * C must hold max M * max N floats.  If plan != NULL the single timed item per
+ * cell is the plan's execution (n_variants must be 1, variant ids ignored). */
+int rg_sweep(rg_ctx* ctx, const rg_grid* grid, int32_t n_variants, const int32_t* variant_ids,
+             const rg_plan* plan, const void* A, const void* B, float* C,
+             const rg_sweep_opts* opts, int64_t* t_ns_out, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RG_H */

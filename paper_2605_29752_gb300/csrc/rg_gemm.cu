@@ -1,0 +1,883 @@
+// BF16 NN GEMM for sm_103a (C = A * B, A M x K row-major, B K x N row-major,
+// C M x N FP32; Sec. 2.2 of "From Roofline to Ruggedness") in six tile
+// variants (Sec. 6.1) with the padding and split-K of Sec. 7.1 fused in, plus
+// the sweep (Sec. 3, Sec. 5.4) and plan execution (Sec. 7.1) that drive it.
+//
+// Kernel structure (one CTA per SM, persistent over output tiles x K splits):
+//   warp 0     TMA producer: A tile (BM x 64, K-major, 128B swizzle) and B tile
+//              (64 x BN, N-major, 128B swizzle, 64-column boxes) into an
+//              mbarrier-guarded ring of STAGES shared-memory stages.
+//   warp 1     allocates TMEM; one thread issues tcgen05.mma (M = 128, N = BN,
+//              K = 16) into a TMEM accumulator, double-buffered when it fits,
+//              and commits stage releases / accumulator-full to mbarriers.
+//   warps 2-5  epilogue: tcgen05.ld of their 32 TMEM lanes, 128B-swizzled
+//              staging, TMA store (beta = 0) or TMA reduce-add (beta = 1).
+// Padding is never materialised: tensor maps carry the logical extents, so
+// TMA zero-fills reads past them and clips writes; the launch itself uses the
+// padded extents (tile counts and K blocks).
+// Split-K (S > 1): split s runs K blocks [s*kb/S, (s+1)*kb/S); each epilogue
+// warp writes its FP32 partial rows to the workspace, fences and takes a
+// ticket; the last arriver of a (tile, warp) row block sums the S partials in
+// the fixed order 0..S-1 (so results are deterministic), stores C and resets
+// the ticket.  No CTA ever waits for another CTA.
+// Every mbarrier wait is bounded; on expiry the kernel records an error code
+// in a device word, releases its TMEM and returns.
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "ptx.cuh"
+#include "rg_internal.h"
+
+namespace rg {
+
+constexpr int kThreads = 192;
+constexpr int kBK = 64;                       // K per stage: one 128-byte swizzle row of BF16
+constexpr int kStagingPerWarp = 2 * 32 * 32 * 4;  // two 32x32 FP32 staging tiles per epilogue warp
+constexpr int kMaxTickets = 1 << 18;
+constexpr uint32_t FULL = 0xffffffffu;
+// Bound for the waits that let this CTA's own in-flight TMA copies and MMAs
+// land before it exits (independent of the per-wait budget, which a caller
+// may set tiny): about half a second.
+constexpr long long kDrainCycles = 1LL << 30;
+
+enum : int { kErrProducer = 1, kErrMma = 2, kErrEpilogue = 3 };
+
+struct GemmArgs {
+  int32_t M, N;             // logical output extents
+  int32_t tiles_m, tiles_n; // tiles of the (padded) launch
+  int32_t splits;
+  int32_t kblocks;          // ceil(padded K / 64)
+  int32_t beta;
+  int32_t stall;            // test hook: the MMA warp first waits on a barrier nothing arrives on
+  float* ws;                // split-K partials [split][tile][BM][BN]
+  int32_t* tickets;         // [tile][4], zero between launches
+  int32_t* err;
+  long long timeout;        // cycles per wait
+};
+
+template <int BM, int BN, int STAGES>
+struct KCfg {
+  static constexpr int A_BYTES = BM * kBK * 2;
+  static constexpr int B_BYTES = kBK * BN * 2;
+  static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+  static constexpr int HALVES = BM / 128;
+  static constexpr int ACC_COLS = HALVES * BN;
+  static constexpr int NBUF = (2 * ACC_COLS <= 512) ? 2 : 1;
+  static constexpr int USED_COLS = NBUF * ACC_COLS;
+  static constexpr int TMEM_COLS = USED_COLS <= 32 ? 32 : USED_COLS <= 64 ? 64 : USED_COLS <= 128 ? 128
+                                   : USED_COLS <= 256 ? 256 : 512;
+  static constexpr int STAGING_OFF = STAGES * STAGE_BYTES;
+  static constexpr int BAR_OFF = STAGING_OFF + 4 * kStagingPerWarp;
+  static constexpr int SMEM_BYTES = 1024 + BAR_OFF + 256;
+  static constexpr uint32_t IDESC = instr_desc(1, 1, 0, 1, 128, BN);
+  static_assert(A_BYTES % 1024 == 0 && B_BYTES % 1024 == 0, "stages must keep 1024-byte alignment");
+  static_assert(SMEM_BYTES <= 232448, "shared memory budget");
+  static_assert(BN % 64 == 0 && BN <= 256 && (BM == 128 || BM == 256), "tile shape");
+};
+
+__device__ __forceinline__ void st_shared_v4(uint32_t addr, float a, float b, float c, float d) {
+  asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "f"(a), "f"(b), "f"(c), "f"(d)
+               : "memory");
+}
+
+__device__ __forceinline__ void load_acc(uint32_t taddr, bool have, float (&v)[32]) {
+  if (have) {
+    uint32_t r[32];
+    tmem_ld_32x32b_x32(taddr, r);
+    tmem_ld_wait();
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+  } else {
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = 0.f;
+  }
+}
+
+// One warp stores a 32 x 32 FP32 block (lane = row) through a swizzled staging
+// buffer with a TMA store, or a TMA reduce-add when beta = 1.
+__device__ __forceinline__ void store_block(const CUtensorMap* tmC, const float (&v)[32], int row0, int col0,
+                                            int M, int N, int beta, uint32_t stg0, int& sbuf, int lane) {
+  if (row0 >= M || col0 >= N) return;  // wholly outside the logical C (padding)
+  if (lane == 0) bulk_wait_read<1>();  // the buffer about to be reused has been read
+  __syncwarp();
+  const uint32_t buf = stg0 + sbuf * 4096;
+#pragma unroll
+  for (int j = 0; j < 8; ++j)
+    st_shared_v4(buf + lane * 128 + ((j ^ (lane & 7)) << 4), v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+  fence_proxy_async_smem();
+  __syncwarp();
+  if (lane == 0) {
+    if (beta)
+      tma_reduce_add_2d(tmC, buf, col0, row0);
+    else
+      tma_store_2d(tmC, buf, col0, row0);
+    bulk_commit();
+  }
+  sbuf ^= 1;
+}
+
+template <int BM, int BN, int STAGES>
+__global__ void __launch_bounds__(kThreads, 1)
+    gemm_bf16_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                     const __grid_constant__ CUtensorMap tmC, const GemmArgs args) {
+  using C = KCfg<BM, BN, STAGES>;
+  extern __shared__ uint8_t smem_raw[];
+  const uint32_t raw_s = smem_u32(smem_raw);
+  uint8_t* smem = smem_raw + ((1024u - (raw_s & 1023u)) & 1023u);
+  const uint32_t sbase = smem_u32(smem);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + C::BAR_OFF);
+  const uint32_t bar0 = smem_u32(bars);
+  auto full_bar = [&](int i) { return bar0 + 8u * i; };
+  auto empty_bar = [&](int i) { return bar0 + 8u * (STAGES + i); };
+  auto tfull_bar = [&](int b) { return bar0 + 8u * (2 * STAGES + b); };
+  auto tempty_bar = [&](int b) { return bar0 + 8u * (2 * STAGES + 2 + b); };
+  const uint32_t drain_bar = bar0 + 8u * (2 * STAGES + 4);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 5);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  int never = 0;
+  volatile int* no_abort = &never;
+
+  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+  const int total = args.tiles_m * args.tiles_n * args.splits;
+
+  if (threadIdx.x == 0) {
+    prefetch_tmap(&tmA);
+    prefetch_tmap(&tmB);
+    prefetch_tmap(&tmC);
+    for (int i = 0; i < STAGES; ++i) {
+      mbar_init(full_bar(i), 1);
+      mbar_init(empty_bar(i), 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(tfull_bar(b), 1);
+      mbar_init(tempty_bar(b), 4);
+    }
+    mbar_init(drain_bar, 1);
+    *abort_flag = 0;
+    fence_mbar_init();
+  }
+  if (warp == 1) {
+    tmem_alloc(smem_u32(tmem_slot), C::TMEM_COLS);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+  // Everything above overlaps the previous grid in the stream; nothing below
+  // touches global memory before that grid has completed.
+  grid_dependency_wait();
+  grid_launch_dependents();
+
+  if (warp == 0) {
+    // ------------------------------------------------ TMA producer (one thread)
+    if (lane == 0) {
+      int stage = 0;
+      uint32_t ph = 0;
+      uint32_t issued_mask = 0, issued_ph = 0;
+      bool ok = true;
+      for (int u = blockIdx.x; ok && u < total; u += gridDim.x) {
+        const int tile = u / args.splits, s = u % args.splits;
+        const int tm = tile / args.tiles_n, tn = tile % args.tiles_n;
+        const int kb0 = static_cast<int>(static_cast<long long>(s) * args.kblocks / args.splits);
+        const int kb1 = static_cast<int>(static_cast<long long>(s + 1) * args.kblocks / args.splits);
+        for (int kb = kb0; kb < kb1; ++kb) {
+          if (!mbar_wait(empty_bar(stage), ph ^ 1u, args.timeout, abort_flag)) {
+            ok = false;
+            break;
+          }
+          const uint32_t sa = sbase + stage * C::STAGE_BYTES;
+          const uint32_t sb = sa + C::A_BYTES;
+          mbar_arrive_expect_tx(full_bar(stage), C::STAGE_BYTES);
+          tma_load_2d(sa, &tmA, full_bar(stage), kb * kBK, tm * BM);
+#pragma unroll
+          for (int j = 0; j < BN / 64; ++j)
+            tma_load_2d(sb + j * (kBK * 128), &tmB, full_bar(stage), tn * BN + j * 64, kb * kBK);
+          issued_mask |= 1u << stage;
+          issued_ph = (issued_ph & ~(1u << stage)) | (ph << stage);
+          if (++stage == STAGES) {
+            stage = 0;
+            ph ^= 1u;
+          }
+        }
+      }
+      if (!ok) {
+        atomicExch(args.err, kErrProducer);
+        *abort_flag = 1;
+      }
+      // no TMA write may still be landing when the CTA exits
+      for (int i = 0; i < STAGES; ++i)
+        if (issued_mask & (1u << i)) mbar_wait(full_bar(i), (issued_ph >> i) & 1u, kDrainCycles, no_abort);
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------ MMA issuer (one thread)
+    int stage = 0, acc = 0;
+    uint32_t ph = 0, aph = 0;
+    bool ok = true;
+    if (args.stall) ok = __all_sync(FULL, mbar_wait(drain_bar, 0, args.timeout, abort_flag));
+    for (int u = blockIdx.x; ok && u < total; u += gridDim.x) {
+      const int s = u % args.splits;
+      const int kb0 = static_cast<int>(static_cast<long long>(s) * args.kblocks / args.splits);
+      const int kb1 = static_cast<int>(static_cast<long long>(s + 1) * args.kblocks / args.splits);
+      ok = __all_sync(FULL, mbar_wait(tempty_bar(acc), aph ^ 1u, args.timeout, abort_flag));
+      if (!ok) break;
+      tc_fence_after();
+      const uint32_t d0 = tmem_base + static_cast<uint32_t>(acc * C::ACC_COLS);
+      for (int kb = kb0; kb < kb1; ++kb) {
+        ok = __all_sync(FULL, mbar_wait(full_bar(stage), ph, args.timeout, abort_flag));
+        if (!ok) break;
+        tc_fence_after();
+        if (lane == 0) {
+          const uint32_t sa = sbase + stage * C::STAGE_BYTES;
+          const uint32_t sb = sa + C::A_BYTES;
+#pragma unroll
+          for (int k = 0; k < kBK / 16; ++k) {
+            const uint64_t bdesc = smem_desc_sw128(sb + k * 2048, kBK * 128, 1024);
+#pragma unroll
+            for (int h = 0; h < C::HALVES; ++h) {
+              const uint64_t adesc = smem_desc_sw128(sa + h * (128 * 128) + k * 32, 16, 1024);
+              mma_f16(d0 + h * BN, adesc, bdesc, C::IDESC, (kb > kb0 || k > 0) ? 1u : 0u);
+            }
+          }
+          mma_commit(empty_bar(stage));
+        }
+        __syncwarp();
+        if (++stage == STAGES) {
+          stage = 0;
+          ph ^= 1u;
+        }
+      }
+      if (!ok) break;
+      if (lane == 0) mma_commit(tfull_bar(acc));
+      __syncwarp();
+      if (++acc == C::NBUF) {
+        acc = 0;
+        aph ^= 1u;
+      }
+    }
+    if (!ok) {
+      if (lane == 0) {
+        atomicExch(args.err, kErrMma);
+        *abort_flag = 1;
+        mma_commit(drain_bar);  // completes once every issued MMA has finished
+      }
+      __syncwarp();
+      mbar_wait(drain_bar, 0, kDrainCycles, no_abort);
+    }
+  } else {
+    // ------------------------------------------------ epilogue (warps 2-5)
+    const int q = warp & 3;  // TMEM lanes 32q..32q+31 are the ones this warp may read
+    const uint32_t stg0 = sbase + C::STAGING_OFF + (warp - 2) * kStagingPerWarp;
+    const int ntiles = args.tiles_m * args.tiles_n;
+    int acc = 0, sbuf = 0;
+    uint32_t aph = 0;
+    bool ok = true;
+    for (int u = blockIdx.x; u < total; u += gridDim.x) {
+      const int tile = u / args.splits, s = u % args.splits;
+      const int tm = tile / args.tiles_n, tn = tile % args.tiles_n;
+      const int kb0 = static_cast<int>(static_cast<long long>(s) * args.kblocks / args.splits);
+      const int kb1 = static_cast<int>(static_cast<long long>(s + 1) * args.kblocks / args.splits);
+      ok = __all_sync(FULL, mbar_wait(tfull_bar(acc), aph, args.timeout, abort_flag));
+      if (!ok) break;
+      tc_fence_after();
+      const bool have = kb1 > kb0;
+      const uint32_t tacc = tmem_base + (static_cast<uint32_t>(q * 32) << 16) + static_cast<uint32_t>(acc * C::ACC_COLS);
+      if (args.splits == 1) {
+#pragma unroll 1
+        for (int h = 0; h < C::HALVES; ++h)
+#pragma unroll 1
+          for (int c = 0; c < BN / 32; ++c) {
+            float v[32];
+            load_acc(tacc + h * BN + c * 32, have, v);
+            store_block(&tmC, v, tm * BM + h * 128 + q * 32, tn * BN + c * 32, args.M, args.N, args.beta, stg0,
+                        sbuf, lane);
+          }
+      } else {
+        const size_t tile_elems = static_cast<size_t>(BM) * BN;
+        float* own_ws = args.ws + (static_cast<size_t>(s) * ntiles + tile) * tile_elems;
+#pragma unroll 1
+        for (int h = 0; h < C::HALVES; ++h)
+#pragma unroll 1
+          for (int c = 0; c < BN / 32; ++c) {
+            float v[32];
+            load_acc(tacc + h * BN + c * 32, have, v);
+            float4* dst = reinterpret_cast<float4*>(own_ws + static_cast<size_t>(h * 128 + q * 32 + lane) * BN + c * 32);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) dst[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+          }
+        // Publish this warp's partial rows: the warp barrier orders every lane's
+        // stores before lane 0's release; the last arriver's acquire (then the
+        // warp barrier) orders the other splits' rows before its loads.
+        __syncwarp();
+        int last = 0;
+        if (lane == 0) {
+          int32_t* t = args.tickets + static_cast<size_t>(tile) * 4 + q;
+          const int old = atom_add_acq_rel_gpu(t, 1);
+          last = (old == args.splits - 1);
+          if (last) *t = 0;
+        }
+        last = __shfl_sync(FULL, last, 0);
+        if (last) {
+          // Sum the S partials of each 32 x 32 block in the fixed order 0..S-1.
+          // Partials are loaded in batches of up to kBatch so that their L2 round
+          // trips overlap (the latency of one batch, not of each partial).
+          constexpr int kBatch = 3;
+#pragma unroll 1
+          for (int h = 0; h < C::HALVES; ++h)
+#pragma unroll 1
+            for (int c = 0; c < BN / 32; ++c) {
+              float own[32], v[32];
+              load_acc(tacc + h * BN + c * 32, have, own);
+              const size_t roff = static_cast<size_t>(h * 128 + q * 32 + lane) * BN + c * 32;
+              int t = 0;
+              for (int base = 0; base < args.splits; base += kBatch) {
+                float4 x[kBatch][8];
+#pragma unroll
+                for (int b = 0; b < kBatch; ++b) {
+                  const int tb = base + b;
+                  if (tb < args.splits && tb != s) {
+                    const float4* src = reinterpret_cast<const float4*>(
+                        args.ws + (static_cast<size_t>(tb) * ntiles + tile) * tile_elems + roff);
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) x[b][j] = __ldcg(src + j);
+                  }
+                }
+#pragma unroll
+                for (int b = 0; b < kBatch; ++b) {
+                  const int tb = base + b;
+                  if (tb < args.splits) {
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                      const float4 p = (tb == s) ? make_float4(own[4 * j], own[4 * j + 1], own[4 * j + 2], own[4 * j + 3])
+                                                 : x[b][j];
+                      if (t == 0) {
+                        v[4 * j] = p.x; v[4 * j + 1] = p.y; v[4 * j + 2] = p.z; v[4 * j + 3] = p.w;
+                      } else {
+                        v[4 * j] += p.x; v[4 * j + 1] += p.y; v[4 * j + 2] += p.z; v[4 * j + 3] += p.w;
+                      }
+                    }
+                    ++t;
+                  }
+                }
+              }
+              store_block(&tmC, v, tm * BM + h * 128 + q * 32, tn * BN + c * 32, args.M, args.N, args.beta,
+                          stg0, sbuf, lane);
+            }
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(tempty_bar(acc));
+      if (++acc == C::NBUF) {
+        acc = 0;
+        aph ^= 1u;
+      }
+    }
+    if (!ok && lane == 0) {
+      atomicExch(args.err, kErrEpilogue);
+      *abort_flag = 1;
+    }
+    if (lane == 0) bulk_wait<0>();
+    __syncwarp();
+  }
+
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem_base, C::TMEM_COLS);
+  }
+}
+
+// Device-side spin of about `ns` nanoseconds (global timer), so that launches
+// enqueued behind it start back to back.  Bounded by a cycle cap as well.
+__global__ void spin_kernel(long long ns) {
+  unsigned long long t0, t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+  const long long c0 = clock64();
+  do {
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  } while (static_cast<long long>(t - t0) < ns && clock64() - c0 < 4LL * ns + 100000LL);
+}
+
+// ------------------------------------------------------------------ host side
+
+using KernFn = void (*)(const CUtensorMap, const CUtensorMap, const CUtensorMap, const GemmArgs);
+
+struct TileKernel {
+  KernFn fn;
+  int bm, bn, smem;
+};
+
+template <int BM, int BN, int ST>
+TileKernel make_tile_kernel() {
+  return TileKernel{gemm_bf16_kernel<BM, BN, ST>, BM, BN, KCfg<BM, BN, ST>::SMEM_BYTES};
+}
+
+static const TileKernel& tile_kernel(int tile) {
+  static const TileKernel table[RG_NUM_TILES] = {
+      make_tile_kernel<128, 64, 8>(),  make_tile_kernel<128, 128, 6>(), make_tile_kernel<128, 256, 4>(),
+      make_tile_kernel<256, 64, 4>(),  make_tile_kernel<256, 128, 4>(), make_tile_kernel<256, 256, 3>(),
+  };
+  return table[tile];
+}
+
+}  // namespace rg
+
+struct rg_ctx {
+  int device = 0;
+  int sm_count = 0;
+  char name[64] = {0};
+  float* ws = nullptr;
+  int64_t ws_bytes = 0;
+  int32_t* tickets = nullptr;
+  int32_t* err = nullptr;
+  long long timeout = 2000000000LL;
+  int32_t stall = 0;
+  int64_t launches = 0;
+  std::vector<cudaEvent_t> events;
+};
+
+namespace rg {
+
+static PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+static std::mutex g_mu;
+
+static int cuda_fail(cudaError_t e, const char* what) {
+  return fail(RG_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+static int get_encode() {
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (g_encode) return RG_OK;
+  void* fn = nullptr;
+  cudaDriverEntryPointQueryResult q;
+  cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+  if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn)
+    return fail(RG_ERR_CUDA, "cannot resolve cuTensorMapEncodeTiled from the driver");
+  g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  return RG_OK;
+}
+
+// 2D row-major tensor map: `inner` contiguous elements per row, `outer` rows,
+// rows `row_bytes` apart; box `box_inner` x `box_outer`; 128-byte swizzle;
+// out-of-range elements read as zero.
+static int make_map(CUtensorMap* m, CUtensorMapDataType dt, const void* base, uint64_t inner, uint64_t outer,
+                    uint64_t row_bytes, uint32_t box_inner, uint32_t box_outer) {
+  cuuint64_t dims[2] = {inner, outer};
+  cuuint64_t strides[1] = {row_bytes};
+  cuuint32_t box[2] = {box_inner, box_outer};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = g_encode(m, dt, 2, const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(RG_ERR_INVALID, "cuTensorMapEncodeTiled rejected a tensor map (code " +
+                                                         std::to_string(static_cast<int>(r)) + ")");
+  return RG_OK;
+}
+
+struct Launch {
+  KernFn fn = nullptr;
+  CUtensorMap a, b, c;
+  GemmArgs args{};
+  dim3 grid;
+  int smem = 0;
+  bool zero_only = false;  // K == 0 with beta == 0: C = 0
+  bool noop = false;
+  float* C = nullptr;
+  int64_t M = 0, N = 0, ldc = 0;
+};
+
+static int prepare(rg_ctx* ctx, int64_t M, int64_t N, int64_t K, const void* A, int64_t lda, const void* B,
+                   int64_t ldb, float* C, int64_t ldc, int32_t variant, int32_t beta, int64_t pm, int64_t pn,
+                   int64_t pk, Launch* L) {
+  if (!ctx) return fail(RG_ERR_INVALID, "null context");
+  if (M < 0 || N < 0 || K < 0) return fail(RG_ERR_INVALID, "negative size");
+  if (variant < 0 || variant >= RG_NUM_VARIANTS) return fail(RG_ERR_INVALID, "variant id out of range");
+  if (beta != 0 && beta != 1) return fail(RG_ERR_INVALID, "beta must be 0 or 1");
+  if (pm == 0) pm = M;
+  if (pn == 0) pn = N;
+  if (pk == 0) pk = K;
+  if (pm < M || pn < N || pk < K) return fail(RG_ERR_INVALID, "padded extents smaller than the problem");
+  if (M > (1 << 30) || N > (1 << 30) || K > (1 << 30) || pm > (1 << 30) || pn > (1 << 30) || pk > (1 << 30))
+    return fail(RG_ERR_SHAPE, "size beyond 2^30");
+  *L = Launch{};
+  if (M == 0 || N == 0) {
+    L->noop = true;
+    return RG_OK;
+  }
+  if (!C) return fail(RG_ERR_INVALID, "null C");
+  if (ldc < N) return fail(RG_ERR_INVALID, "ldc < N");
+  if ((reinterpret_cast<uintptr_t>(C) & 15) || (ldc % 4)) return fail(RG_ERR_ALIGN, "C must be 16-byte aligned, ldc % 4 == 0");
+  if (K == 0) {
+    L->zero_only = (beta == 0);
+    L->noop = (beta != 0);
+    L->C = C;
+    L->M = M;
+    L->N = N;
+    L->ldc = ldc;
+    return RG_OK;
+  }
+  if (!A || !B) return fail(RG_ERR_INVALID, "null operand");
+  if (lda < K || ldb < N) return fail(RG_ERR_INVALID, "lda < K or ldb < N");
+  if ((reinterpret_cast<uintptr_t>(A) & 15) || (reinterpret_cast<uintptr_t>(B) & 15) || (lda % 8) || (ldb % 8))
+    return fail(RG_ERR_ALIGN, "A and B must be 16-byte aligned with lda, ldb multiples of 8");
+  int rc = get_encode();
+  if (rc != RG_OK) return rc;
+  const int tile = variant_tile(variant);
+  const int splits = variant_split(variant);
+  const TileKernel& tk = tile_kernel(tile);
+  const int64_t tiles_m = (pm + tk.bm - 1) / tk.bm;
+  const int64_t tiles_n = (pn + tk.bn - 1) / tk.bn;
+  const int64_t kblocks = (pk + kBK - 1) / kBK;
+  if (splits > 1) {
+    const int64_t need = static_cast<int64_t>(splits) * tiles_m * tiles_n * tk.bm * tk.bn * 4;
+    if (need > ctx->ws_bytes || tiles_m * tiles_n * 4 > kMaxTickets)
+      return fail(RG_ERR_SHAPE, "split-K workspace too small for this shape");
+  }
+  rc = make_map(&L->a, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, A, K, M, lda * 2, kBK, tk.bm);
+  if (rc == RG_OK) rc = make_map(&L->b, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, B, N, K, ldb * 2, 64, kBK);
+  if (rc == RG_OK) rc = make_map(&L->c, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, C, N, M, ldc * 4, 32, 32);
+  if (rc != RG_OK) return rc;
+  L->fn = tk.fn;
+  L->smem = tk.smem;
+  GemmArgs& g = L->args;
+  g.M = static_cast<int32_t>(M);
+  g.N = static_cast<int32_t>(N);
+  g.tiles_m = static_cast<int32_t>(tiles_m);
+  g.tiles_n = static_cast<int32_t>(tiles_n);
+  g.splits = splits;
+  g.kblocks = static_cast<int32_t>(kblocks);
+  g.beta = beta;
+  g.ws = ctx->ws;
+  g.tickets = ctx->tickets;
+  g.err = ctx->err;
+  g.timeout = ctx->timeout;
+  g.stall = ctx->stall;
+  const int64_t units = tiles_m * tiles_n * splits;
+  L->grid = dim3(static_cast<unsigned>(std::min<int64_t>(units, ctx->sm_count)));
+  return RG_OK;
+}
+
+static cudaError_t launch(rg_ctx* ctx, const Launch& L, cudaStream_t st) {
+  if (L.noop) return cudaSuccess;
+  if (L.zero_only) return cudaMemset2DAsync(L.C, L.ldc * 4, 0, L.N * 4, L.M, st);
+  ++ctx->launches;
+  void* params[4] = {const_cast<CUtensorMap*>(&L.a), const_cast<CUtensorMap*>(&L.b), const_cast<CUtensorMap*>(&L.c),
+                     const_cast<GemmArgs*>(&L.args)};
+  // Programmatic dependent launch: the grid may be scheduled while the previous
+  // grid in the stream finishes; the kernel waits (griddepcontrol.wait) before
+  // its first global memory access.
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = L.grid;
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = static_cast<size_t>(L.smem);
+  cfg.stream = st;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelExC(&cfg, reinterpret_cast<const void*>(L.fn), params);
+}
+
+void ctx_identity(const rg_ctx* ctx, char name[64], int32_t* sms) {
+  std::memset(name, 0, 64);
+  *sms = 0;
+  if (!ctx) return;
+  std::memcpy(name, ctx->name, 64);
+  *sms = ctx->sm_count;
+}
+
+int plan_cell(const Plan& P, int64_t M, int64_t N, int64_t K, int64_t* cell);
+
+// Leaves of the plan cell covering (M, N, K), clipped to the problem.
+static int plan_launches(rg_ctx* ctx, const rg_plan* plan, int64_t M, int64_t N, int64_t K, const void* A,
+                         int64_t lda, const void* B, int64_t ldb, float* C, int64_t ldc, std::vector<Launch>& out) {
+  out.clear();
+  if (!plan) return fail(RG_ERR_INVALID, "null plan");
+  if (M <= 0 || N <= 0 || K <= 0) return fail(RG_ERR_INVALID, "plan execution needs positive sizes");
+  int64_t cell = 0;
+  if (plan_cell(plan->p, M, N, K, &cell) != RG_OK) return fail(RG_ERR_SHAPE, "shape beyond the plan grid");
+  const Plan& P = plan->p;
+  for (int64_t i = P.leaf_off[cell]; i < P.leaf_off[cell + 1]; ++i) {
+    const rg_leaf& lf = P.leaves[i];
+    if (lf.m0 >= M || lf.n0 >= N || lf.k0 >= K) continue;  // wholly in the padding
+    const int64_t m = std::min(lf.m, M - lf.m0), n = std::min(lf.n, N - lf.n0), k = std::min(lf.k, K - lf.k0);
+    const auto* a = static_cast<const uint16_t*>(A) + lf.m0 * lda + lf.k0;
+    const auto* b = static_cast<const uint16_t*>(B) + lf.k0 * ldb + lf.n0;
+    float* c = C + lf.m0 * ldc + lf.n0;
+    Launch L;
+    const int rc = prepare(ctx, m, n, k, a, lda, b, ldb, c, ldc, lf.variant, lf.beta, lf.pm, lf.pn, lf.pk, &L);
+    if (rc != RG_OK) return rc;
+    out.push_back(L);
+  }
+  return RG_OK;
+}
+
+}  // namespace rg
+
+// ------------------------------------------------------------------ C ABI
+
+extern "C" int rg_init(int device, int64_t workspace_bytes, rg_ctx** out) {
+  rg::clear_error();
+  if (!out) return rg::fail(RG_ERR_INVALID, "rg_init: null out");
+  *out = nullptr;
+  int n = 0;
+  cudaError_t e = cudaGetDeviceCount(&n);
+  if (e != cudaSuccess || n <= 0) {
+    cudaGetLastError();
+    return rg::fail(RG_ERR_NO_DEVICE, "rg_init: no CUDA device");
+  }
+  if (device < 0 || device >= n) return rg::fail(RG_ERR_INVALID, "rg_init: device index out of range");
+  cudaDeviceProp prop;
+  if ((e = cudaGetDeviceProperties(&prop, device)) != cudaSuccess) return rg::cuda_fail(e, "rg_init");
+  if (prop.major != 10 || prop.minor != 3)
+    return rg::fail(RG_ERR_NO_DEVICE, "rg_init: needs a compute capability 10.3 device (GB300), found " +
+                                          std::to_string(prop.major) + "." + std::to_string(prop.minor));
+  if ((e = cudaSetDevice(device)) != cudaSuccess) return rg::cuda_fail(e, "rg_init: cudaSetDevice");
+  int rc = rg::get_encode();
+  if (rc != RG_OK) return rc;
+  auto* ctx = new (std::nothrow) rg_ctx();
+  if (!ctx) return rg::fail(RG_ERR_OOM, "rg_init: host allocation");
+  ctx->device = device;
+  ctx->sm_count = prop.multiProcessorCount;
+  std::strncpy(ctx->name, prop.name, 63);
+  ctx->ws_bytes = workspace_bytes > 0 ? workspace_bytes : (512LL << 20);
+  for (int t = 0; t < RG_NUM_TILES; ++t) {
+    const rg::TileKernel& tk = rg::tile_kernel(t);
+    if ((e = cudaFuncSetAttribute(reinterpret_cast<const void*>(tk.fn), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  tk.smem)) != cudaSuccess) {
+      delete ctx;
+      return rg::cuda_fail(e, "rg_init: shared-memory attribute");
+    }
+  }
+  if ((e = cudaMalloc(&ctx->ws, ctx->ws_bytes)) != cudaSuccess ||
+      (e = cudaMalloc(&ctx->tickets, sizeof(int32_t) * rg::kMaxTickets)) != cudaSuccess ||
+      (e = cudaMalloc(&ctx->err, sizeof(int32_t))) != cudaSuccess) {
+    cudaFree(ctx->ws);
+    cudaFree(ctx->tickets);
+    cudaFree(ctx->err);
+    delete ctx;
+    cudaGetLastError();
+    return rg::fail(RG_ERR_OOM, std::string("rg_init: device allocation: ") + cudaGetErrorString(e));
+  }
+  cudaMemset(ctx->tickets, 0, sizeof(int32_t) * rg::kMaxTickets);
+  cudaMemset(ctx->err, 0, sizeof(int32_t));
+  if ((e = cudaDeviceSynchronize()) != cudaSuccess) {
+    rg_destroy(ctx);
+    return rg::cuda_fail(e, "rg_init");
+  }
+  *out = ctx;
+  return RG_OK;
+}
+
+extern "C" void rg_destroy(rg_ctx* ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->device);
+  for (auto ev : ctx->events) cudaEventDestroy(ev);
+  cudaFree(ctx->ws);
+  cudaFree(ctx->tickets);
+  cudaFree(ctx->err);
+  delete ctx;
+}
+
+extern "C" int rg_sm_count(const rg_ctx* ctx, int32_t* out) {
+  if (!ctx || !out) return rg::fail(RG_ERR_INVALID, "rg_sm_count: null argument");
+  *out = ctx->sm_count;
+  return RG_OK;
+}
+
+extern "C" int rg_set_test_stall(rg_ctx* ctx, int32_t enable) {
+  if (!ctx) return rg::fail(RG_ERR_INVALID, "rg_set_test_stall: null context");
+  ctx->stall = enable ? 1 : 0;
+  return RG_OK;
+}
+
+extern "C" int rg_launch_count(const rg_ctx* ctx, int64_t* out) {
+  if (!ctx || !out) return rg::fail(RG_ERR_INVALID, "rg_launch_count: null argument");
+  *out = ctx->launches;
+  return RG_OK;
+}
+
+extern "C" int rg_set_timeout_cycles(rg_ctx* ctx, int64_t cycles) {
+  if (!ctx || cycles <= 0) return rg::fail(RG_ERR_INVALID, "rg_set_timeout_cycles: bad argument");
+  ctx->timeout = cycles;
+  return RG_OK;
+}
+
+extern "C" int rg_check(rg_ctx* ctx, void* stream) {
+  if (!ctx) return rg::fail(RG_ERR_INVALID, "rg_check: null context");
+  cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return rg::cuda_fail(e, "rg_check: stream");
+  int32_t code = 0;
+  if ((e = cudaMemcpy(&code, ctx->err, sizeof(code), cudaMemcpyDeviceToHost)) != cudaSuccess)
+    return rg::cuda_fail(e, "rg_check: read error word");
+  if (code != 0) {
+    cudaMemset(ctx->err, 0, sizeof(int32_t));
+    cudaMemset(ctx->tickets, 0, sizeof(int32_t) * rg::kMaxTickets);  // a kernel may have stopped mid-reduction
+    cudaDeviceSynchronize();
+    static const char* role[] = {"", "TMA producer", "MMA issuer", "epilogue"};
+    return rg::fail(RG_ERR_TIMEOUT, std::string("rg_check: a bounded wait expired in the ") +
+                                        (code >= 1 && code <= 3 ? role[code] : "kernel"));
+  }
+  return RG_OK;
+}
+
+extern "C" int rg_gemm(rg_ctx* ctx, int64_t M, int64_t N, int64_t K, const void* A, int64_t lda, const void* B,
+                       int64_t ldb, float* C, int64_t ldc, int32_t variant, int32_t beta, int64_t pm, int64_t pn,
+                       int64_t pk, void* stream) {
+  rg::clear_error();
+  rg::Launch L;
+  int rc = rg::prepare(ctx, M, N, K, A, lda, B, ldb, C, ldc, variant, beta, pm, pn, pk, &L);
+  if (rc != RG_OK) return rc;
+  cudaError_t e = rg::launch(ctx, L, static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? RG_OK : rg::cuda_fail(e, "rg_gemm: launch");
+}
+
+extern "C" int rg_gemm_plan(rg_ctx* ctx, const rg_plan* plan, int64_t M, int64_t N, int64_t K, const void* A,
+                            int64_t lda, const void* B, int64_t ldb, float* C, int64_t ldc, void* stream) {
+  rg::clear_error();
+  std::vector<rg::Launch> ls;
+  int rc = rg::plan_launches(ctx, plan, M, N, K, A, lda, B, ldb, C, ldc, ls);
+  if (rc != RG_OK) return rc;
+  for (const auto& L : ls) {
+    cudaError_t e = rg::launch(ctx, L, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return rg::cuda_fail(e, "rg_gemm_plan: launch");
+  }
+  return RG_OK;
+}
+
+namespace {
+uint64_t splitmix_next(uint64_t& s) {
+  uint64_t z = (s += 0x9E3779B97F4A7C15ull);
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+}  // namespace
+
+extern "C" int rg_sweep(rg_ctx* ctx, const rg_grid* grid, int32_t n_variants, const int32_t* variant_ids,
+                        const rg_plan* plan, const void* A, const void* B, float* C, const rg_sweep_opts* opts,
+                        int64_t* t_ns_out, void* stream) {
+  rg::clear_error();
+  if (!ctx || !grid || !A || !B || !C || !t_ns_out) return rg::fail(RG_ERR_INVALID, "rg_sweep: null argument");
+  if (!rg::grid_valid(*grid)) return rg::fail(RG_ERR_INVALID, "rg_sweep: invalid grid");
+  if (plan ? n_variants != 1 : (n_variants <= 0 || !variant_ids))
+    return rg::fail(RG_ERR_INVALID, "rg_sweep: variants");
+  rg_sweep_opts o;
+  rg_sweep_opts_default(&o);
+  if (opts) o = *opts;
+  if (o.reps <= 0 || o.warmup < 0 || o.global_warmup < 0 || o.spin_ns < 0)
+    return rg::fail(RG_ERR_INVALID, "rg_sweep: options");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int64_t cells = rg::cells_of(*grid);
+  const int64_t nk = grid->k.count, nn = grid->n.count;
+  std::vector<int64_t> order(static_cast<size_t>(cells) * n_variants);
+  for (size_t i = 0; i < order.size(); ++i) order[i] = static_cast<int64_t>(i);
+  if (o.shuffle) {
+    uint64_t s = o.seed;
+    for (size_t i = order.size() - 1; i > 0; --i) {
+      const size_t j = static_cast<size_t>(splitmix_next(s) % (i + 1));
+      std::swap(order[i], order[j]);
+    }
+  }
+  const int kBatch = 256;
+  if (ctx->events.size() < 2 * kBatch) {
+    while (ctx->events.size() < 2 * kBatch) {
+      cudaEvent_t ev;
+      cudaError_t e = cudaEventCreate(&ev);
+      if (e != cudaSuccess) return rg::cuda_fail(e, "rg_sweep: event");
+      ctx->events.push_back(ev);
+    }
+  }
+  std::vector<rg::Launch> ls;
+  auto dims = [&](int64_t item, int64_t* M, int64_t* N, int64_t* K) {
+    const int64_t cell = item % cells;
+    const int64_t a = cell / (nn * nk), b = (cell / nk) % nn, c = cell % nk;
+    *M = rg::axis_value(grid->m, a);
+    *N = rg::axis_value(grid->n, b);
+    *K = rg::axis_value(grid->k, c);
+  };
+  // A split-K variant is worth timing only where the unsplit tile count leaves
+  // SMs idle and every split keeps at least two K blocks.
+  auto pruned = [&](int64_t item) -> bool {
+    if (plan || !o.prune_splits) return false;
+    const int32_t v = variant_ids[item / cells];
+    const int S = rg::variant_split(v);
+    if (S == 1) return false;
+    int64_t M, N, K;
+    dims(item, &M, &N, &K);
+    const rg::TileShape ts = rg::tile_shape(rg::variant_tile(v));
+    const int64_t tiles = ((M + ts.bm - 1) / ts.bm) * ((N + ts.bn - 1) / ts.bn);
+    const int64_t kblocks = (K + rg::kBK - 1) / rg::kBK;
+    return tiles >= ctx->sm_count || kblocks < 2 * S;
+  };
+  auto build = [&](int64_t item, std::vector<rg::Launch>& out) -> int {
+    int64_t M, N, K;
+    dims(item, &M, &N, &K);
+    if (plan) return rg::plan_launches(ctx, plan, M, N, K, A, K, B, N, C, N, out);
+    out.resize(1);
+    return rg::prepare(ctx, M, N, K, A, K, B, N, C, N, variant_ids[item / cells], 0, 0, 0, 0, &out[0]);
+  };
+  auto run = [&](const std::vector<rg::Launch>& v) -> cudaError_t {
+    for (const auto& L : v) {
+      cudaError_t e = rg::launch(ctx, L, st);
+      if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+  };
+  if (o.prune_splits && !plan) {  // timed items first, pruned ones marked
+    std::vector<int64_t> keep;
+    keep.reserve(order.size());
+    for (int64_t it : order) {
+      if (pruned(it))
+        t_ns_out[it] = RG_T_UNMEASURED;
+      else
+        keep.push_back(it);
+    }
+    order.swap(keep);
+  }
+  if (!order.empty() && o.global_warmup > 0) {
+    int rc = build(order[0], ls);
+    if (rc != RG_OK) return rc;
+    for (int i = 0; i < o.global_warmup; ++i)
+      if (cudaError_t e = run(ls); e != cudaSuccess) return rg::cuda_fail(e, "rg_sweep: warmup");
+  }
+  for (size_t base = 0; base < order.size(); base += kBatch) {
+    const size_t nb = std::min<size_t>(kBatch, order.size() - base);
+    for (size_t i = 0; i < nb; ++i) {
+      int rc = build(order[base + i], ls);
+      if (rc != RG_OK) return rc;
+      cudaError_t e = cudaSuccess;
+      for (int w = 0; w < o.warmup && e == cudaSuccess; ++w) e = run(ls);
+      if (e == cudaSuccess && o.spin_ns > 0) {
+        rg::spin_kernel<<<1, 1, 0, st>>>(o.spin_ns * o.reps * static_cast<long long>(ls.size()));
+        ++ctx->launches;
+        e = cudaGetLastError();
+      }
+      if (e == cudaSuccess) e = cudaEventRecord(ctx->events[2 * i], st);
+      for (int r = 0; r < o.reps && e == cudaSuccess; ++r) e = run(ls);
+      if (e == cudaSuccess) e = cudaEventRecord(ctx->events[2 * i + 1], st);
+      if (e != cudaSuccess) return rg::cuda_fail(e, "rg_sweep: launch");
+    }
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return rg::cuda_fail(e, "rg_sweep: synchronize");
+    for (size_t i = 0; i < nb; ++i) {
+      float ms = 0.f;
+      e = cudaEventElapsedTime(&ms, ctx->events[2 * i], ctx->events[2 * i + 1]);
+      if (e != cudaSuccess) return rg::cuda_fail(e, "rg_sweep: event time");
+      const int64_t t = std::llround(static_cast<double>(ms) * 1e6 / o.reps);
+      t_ns_out[order[base + i]] = t > 0 ? t : 1;
+    }
+  }
+  return rg_check(ctx, stream);
+}

@@ -1,0 +1,165 @@
+// Surface statistics (Sec. 2 definitions of achieved TFLOPs and roughness;
+// Sec. 8.6 / Table 17 slice and 3D conventions) and the library's error
+// plumbing.  Compiled without floating-point contraction so every operation
+// is one IEEE double operation in the stated order.
+#include <cmath>
+#include <string>
+#include <vector>
+
+#include "rg_internal.h"
+
+namespace rg {
+
+static thread_local std::string g_last_error;
+
+int fail(int code, const std::string& msg) {
+  g_last_error = msg;
+  return code;
+}
+void clear_error() { g_last_error.clear(); }
+
+TileShape tile_shape(int tile) {
+  static const TileShape shapes[RG_NUM_TILES] = {{128, 64}, {128, 128}, {128, 256},
+                                                 {256, 64}, {256, 128}, {256, 256}};
+  return shapes[tile];
+}
+
+// Correctly rounded sum of doubles.  Partials form a non-overlapping expansion
+// grown with error-free two-sums (Shewchuk, "Adaptive Precision Floating-Point
+// Arithmetic and Fast Robust Geometric Predicates", 1997); the result is the
+// expansion rounded to the nearest double, ties to even, with the correction
+// for a half-way top partial whose remainder lies beyond it.
+class ExactSum {
+ public:
+  void add(double x) {
+    size_t i = 0;
+    for (size_t j = 0; j < p_.size(); ++j) {
+      double y = p_[j];
+      if (std::fabs(x) < std::fabs(y)) std::swap(x, y);
+      const double hi = x + y;
+      const double lo = y - (hi - x);
+      if (lo != 0.0) p_[i++] = lo;
+      x = hi;
+    }
+    p_.resize(i);
+    if (x != 0.0) p_.push_back(x);
+  }
+  double value() const {
+    size_t n = p_.size();
+    if (n == 0) return 0.0;
+    double hi = p_[--n];
+    double lo = 0.0;
+    while (n > 0) {
+      const double x = hi;
+      const double y = p_[--n];
+      hi = x + y;
+      const double yr = hi - x;
+      lo = y - yr;
+      if (lo != 0.0) break;
+    }
+    if (n > 0 && ((lo < 0.0 && p_[n - 1] < 0.0) || (lo > 0.0 && p_[n - 1] > 0.0))) {
+      const double y = lo * 2.0;
+      const double x = hi + y;
+      const double yr = x - hi;
+      if (y == yr) hi = x;
+    }
+    return hi;
+  }
+
+ private:
+  std::vector<double> p_;
+};
+
+double exact_mean(const double* v, int64_t n) {
+  if (n <= 0) return 0.0;
+  ExactSum s;
+  for (int64_t i = 0; i < n; ++i) s.add(v[i]);
+  return s.value() / static_cast<double>(n);
+}
+
+}  // namespace rg
+
+extern "C" const char* rg_version(void) { return "rg 0.1 (sm_103a tcgen05 BF16 NN GEMM, landscape smoothing)"; }
+
+extern "C" const char* rg_last_error(void) { return rg::g_last_error.c_str(); }
+
+extern "C" const char* rg_strerror(int status) {
+  switch (status) {
+    case RG_OK: return "ok";
+    case RG_ERR_INVALID: return "invalid argument";
+    case RG_ERR_ALIGN: return "pointer or leading dimension violates TMA alignment";
+    case RG_ERR_SHAPE: return "shape outside the plan grid or workspace capacity";
+    case RG_ERR_OOM: return "out of memory";
+    case RG_ERR_CUDA: return "CUDA error";
+    case RG_ERR_TIMEOUT: return "a bounded device wait expired";
+    case RG_ERR_PLAN_MISMATCH: return "plan file does not match";
+    case RG_ERR_ADMISSION: return "request exceeds the serving memory budget";
+    case RG_ERR_NO_DEVICE: return "no usable sm_103 device";
+    default: return "unknown status";
+  }
+}
+
+extern "C" void rg_sweep_opts_default(rg_sweep_opts* o) {
+  if (!o) return;
+  o->reps = 5;
+  o->warmup = 1;
+  o->global_warmup = 5;
+  o->shuffle = 1;
+  o->seed = 0;
+  o->spin_ns = 4000;
+  o->prune_splits = 1;
+  o->reserved = 0;
+}
+
+extern "C" int rg_surface_stats(const rg_grid* grid, const int64_t* t_ns, double* tflops_out,
+                                double rough_out[5], double* mean_out) {
+  rg::clear_error();
+  if (!grid || !t_ns) return rg::fail(RG_ERR_INVALID, "rg_surface_stats: null argument");
+  if (!rg::grid_valid(*grid)) return rg::fail(RG_ERR_INVALID, "rg_surface_stats: invalid grid");
+  const int64_t nm = grid->m.count, nn = grid->n.count, nk = grid->k.count;
+  const int64_t cells = nm * nn * nk;
+  std::vector<double> S(cells);
+  for (int64_t a = 0; a < nm; ++a)
+    for (int64_t b = 0; b < nn; ++b)
+      for (int64_t c = 0; c < nk; ++c) {
+        const int64_t i = (a * nn + b) * nk + c;
+        if (t_ns[i] <= 0) return rg::fail(RG_ERR_INVALID, "rg_surface_stats: times must be positive");
+        const double M = static_cast<double>(rg::axis_value(grid->m, a));
+        const double N = static_cast<double>(rg::axis_value(grid->n, b));
+        const double K = static_cast<double>(rg::axis_value(grid->k, c));
+        const double flops = 2.0 * M * N * K;
+        const double den = static_cast<double>(t_ns[i]) * 1e3;
+        S[i] = flops / den;
+      }
+  if (tflops_out)
+    for (int64_t i = 0; i < cells; ++i) tflops_out[i] = S[i];
+  if (mean_out) *mean_out = rg::exact_mean(S.data(), cells);
+  if (rough_out) {
+    auto at = [&](int64_t a, int64_t b, int64_t c) { return S[(a * nn + b) * nk + c]; };
+    rg::ExactSum sm, sn, sk, ss;
+    for (int64_t a = 0; a + 1 < nm; ++a)
+      for (int64_t b = 0; b < nn; ++b)
+        for (int64_t c = 0; c < nk; ++c) sm.add(std::fabs(at(a + 1, b, c) - at(a, b, c)));
+    for (int64_t a = 0; a < nm; ++a)
+      for (int64_t b = 0; b + 1 < nn; ++b)
+        for (int64_t c = 0; c < nk; ++c) sn.add(std::fabs(at(a, b + 1, c) - at(a, b, c)));
+    for (int64_t a = 0; a < nm; ++a)
+      for (int64_t b = 0; b < nn; ++b)
+        for (int64_t c = 0; c + 1 < nk; ++c) sk.add(std::fabs(at(a, b, c + 1) - at(a, b, c)));
+    for (int64_t a = 0; a < nm; ++a)
+      for (int64_t b = 0; b + 1 < nn; ++b) ss.add(std::fabs(at(a, b + 1, nk - 1) - at(a, b, nk - 1)));
+    const double pm = static_cast<double>((nm - 1) * nn * nk);
+    const double pn = static_cast<double>(nm * (nn - 1) * nk);
+    const double pk = static_cast<double>(nm * nn * (nk - 1));
+    const double ps = static_cast<double>(nm * (nn - 1));
+    const double rM = nm > 1 ? sm.value() / pm : 0.0;
+    const double rN = nn > 1 ? sn.value() / pn : 0.0;
+    const double rK = nk > 1 ? sk.value() / pk : 0.0;
+    rough_out[0] = rM;
+    rough_out[1] = rN;
+    rough_out[2] = rK;
+    rough_out[3] = (rM + rN + rK) / 3.0;
+    rough_out[4] = nn > 1 ? ss.value() / ps : 0.0;
+  }
+  return RG_OK;
+}

@@ -1,0 +1,331 @@
+"""ctypes binding of the C ABI in include/rg.h (argument marshalling only).
+
+Every function here has the name of the C entry point it calls and does no
+computation of its own: GEMMs, sweeps, plan tables and statistics all run in
+librg.so.  Device buffers are passed as integers (``tensor.data_ptr()``) or
+as objects with a ``data_ptr()`` method; streams as ``torch.cuda.Stream``,
+raw ``cudaStream_t`` integers or None (legacy default stream).
+
+If librg.so is missing the import fails loudly: there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "librg.so")
+
+RG_OK = 0
+RG_ERR_INVALID = -1
+RG_ERR_ALIGN = -2
+RG_ERR_SHAPE = -3
+RG_ERR_OOM = -4
+RG_ERR_CUDA = -5
+RG_ERR_TIMEOUT = -6
+RG_ERR_PLAN_MISMATCH = -7
+RG_ERR_ADMISSION = -8
+RG_ERR_NO_DEVICE = -9
+
+RG_T_UNMEASURED = 1 << 60
+RG_NUM_TILES = 6
+RG_NUM_SPLITS = 4
+RG_NUM_VARIANTS = RG_NUM_TILES * RG_NUM_SPLITS
+TILES = [(128, 64), (128, 128), (128, 256), (256, 64), (256, 128), (256, 256)]
+SPLITS = [1, 2, 4, 8]
+
+
+def variant(tile: int, split: int = 1) -> int:
+    return tile * RG_NUM_SPLITS + SPLITS.index(split)
+
+
+def variant_name(v: int) -> str:
+    bm, bn = TILES[v // RG_NUM_SPLITS]
+    return f"{bm}x{bn}/S{SPLITS[v % RG_NUM_SPLITS]}"
+
+
+class rg_axis(C.Structure):
+    _fields_ = [("start", C.c_int32), ("step", C.c_int32), ("count", C.c_int32)]
+
+
+class rg_grid(C.Structure):
+    _fields_ = [("m", rg_axis), ("n", rg_axis), ("k", rg_axis)]
+
+
+class rg_leaf(C.Structure):
+    _fields_ = [("variant", C.c_int32), ("beta", C.c_int32), ("phase", C.c_int32), ("reserved", C.c_int32),
+                ("m0", C.c_int64), ("n0", C.c_int64), ("k0", C.c_int64),
+                ("m", C.c_int64), ("n", C.c_int64), ("k", C.c_int64),
+                ("pm", C.c_int64), ("pn", C.c_int64), ("pk", C.c_int64)]
+
+
+class rg_sweep_opts(C.Structure):
+    _fields_ = [("reps", C.c_int32), ("warmup", C.c_int32), ("global_warmup", C.c_int32),
+                ("shuffle", C.c_int32), ("seed", C.c_uint64), ("spin_ns", C.c_int64),
+                ("prune_splits", C.c_int32), ("reserved", C.c_int32)]
+
+
+class RGError(RuntimeError):
+    def __init__(self, code: int, where: str, msg: str):
+        super().__init__(f"{where}: {msg} (status {code})")
+        self.code = code
+
+
+if not os.path.exists(_LIB_PATH):
+    raise ImportError(f"librg.so not built ({_LIB_PATH}); run __graft_entry__.build() or "
+                      f"python -m paper_2605_29752_gb300.build")
+_lib = C.CDLL(_LIB_PATH)
+
+_P = C.c_void_p
+_I64 = C.c_int64
+_I32 = C.c_int32
+_sigs = {
+    "rg_version": (C.c_char_p, []),
+    "rg_strerror": (C.c_char_p, [C.c_int]),
+    "rg_last_error": (C.c_char_p, []),
+    "rg_sweep_opts_default": (None, [C.POINTER(rg_sweep_opts)]),
+    "rg_init": (C.c_int, [C.c_int, _I64, C.POINTER(_P)]),
+    "rg_destroy": (None, [_P]),
+    "rg_sm_count": (C.c_int, [_P, C.POINTER(_I32)]),
+    "rg_check": (C.c_int, [_P, _P]),
+    "rg_set_timeout_cycles": (C.c_int, [_P, _I64]),
+    "rg_gemm": (C.c_int, [_P, _I64, _I64, _I64, _P, _I64, _P, _I64, _P, _I64, _I32, _I32, _I64, _I64, _I64, _P]),
+    "rg_plan_build": (C.c_int, [C.POINTER(rg_grid), _P, _I32, _P, C.POINTER(_P)]),
+    "rg_plan_build_ex": (C.c_int, [C.POINTER(rg_grid), _P, _I32, _P, _I32, C.POINTER(_P)]),
+    "rg_launch_count": (C.c_int, [_P, C.POINTER(_I64)]),
+    "rg_set_test_stall": (C.c_int, [_P, _I32]),
+    "rg_plan_free": (None, [_P]),
+    "rg_plan_grid": (C.c_int, [_P, C.POINTER(rg_grid)]),
+    "rg_plan_tables": (C.c_int, [_P, _P, _P, _P, _P, _P, _P, _P]),
+    "rg_plan_lookup": (C.c_int, [_P, _I64, _I64, _I64, C.POINTER(C.POINTER(rg_leaf)), C.POINTER(_I32),
+                                 C.POINTER(_I64)]),
+    "rg_gemm_plan": (C.c_int, [_P, _P, _I64, _I64, _I64, _P, _I64, _P, _I64, _P, _I64, _P]),
+    "rg_plan_save": (C.c_int, [_P, _P, C.c_char_p]),
+    "rg_plan_load": (C.c_int, [C.c_char_p, _P, C.POINTER(_P)]),
+    "rg_surface_stats": (C.c_int, [C.POINTER(rg_grid), _P, _P, _P, _P]),
+    "rg_sweep": (C.c_int, [_P, C.POINTER(rg_grid), _I32, _P, _P, _P, _P, _P, C.POINTER(rg_sweep_opts), _P, _P]),
+}
+for _name, (_res, _args) in _sigs.items():
+    _f = getattr(_lib, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+
+HEADER_SYMBOLS = tuple(_sigs)
+
+
+def lib_path() -> str:
+    return _LIB_PATH
+
+
+def library():
+    return _lib
+
+
+def _check(code: int, where: str) -> int:
+    if code != RG_OK:
+        raise RGError(code, where, _lib.rg_last_error().decode() or _lib.rg_strerror(code).decode())
+    return code
+
+
+def _ptr(x) -> int | None:
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    raise TypeError(f"cannot take a device pointer of {type(x)}")
+
+
+def _stream(s) -> int | None:
+    if s is None:
+        return None
+    if isinstance(s, int):
+        return s
+    if hasattr(s, "cuda_stream"):
+        return s.cuda_stream
+    raise TypeError(f"not a stream: {type(s)}")
+
+
+def make_grid(m, n=None, k=None) -> rg_grid:
+    """Grid from (start, step, count) triples; n and k default to m."""
+    n = n or m
+    k = k or m
+    return rg_grid(rg_axis(*m), rg_axis(*n), rg_axis(*k))
+
+
+def grid_cells(g: rg_grid) -> int:
+    return g.m.count * g.n.count * g.k.count
+
+
+# ------------------------------------------------------------------ entry points
+
+def rg_version() -> str:
+    return _lib.rg_version().decode()
+
+
+def rg_strerror(code: int) -> str:
+    return _lib.rg_strerror(code).decode()
+
+
+def rg_init(device: int = 0, workspace_bytes: int = 0) -> int:
+    h = _P()
+    _check(_lib.rg_init(device, workspace_bytes, C.byref(h)), "rg_init")
+    return h.value
+
+
+def rg_destroy(ctx: int) -> None:
+    _lib.rg_destroy(ctx)
+
+
+def rg_sm_count(ctx: int) -> int:
+    v = _I32()
+    _check(_lib.rg_sm_count(ctx, C.byref(v)), "rg_sm_count")
+    return v.value
+
+
+def rg_check(ctx: int, stream=None) -> None:
+    _check(_lib.rg_check(ctx, _stream(stream)), "rg_check")
+
+
+def rg_check_status(ctx: int, stream=None) -> int:
+    return _lib.rg_check(ctx, _stream(stream))
+
+
+def rg_set_timeout_cycles(ctx: int, cycles: int) -> None:
+    _check(_lib.rg_set_timeout_cycles(ctx, cycles), "rg_set_timeout_cycles")
+
+
+def rg_gemm(ctx, M, N, K, A, lda, B, ldb, Cp, ldc, variant_id, beta=0, pm=0, pn=0, pk=0, stream=None) -> None:
+    _check(_lib.rg_gemm(ctx, M, N, K, _ptr(A), lda, _ptr(B), ldb, _ptr(Cp), ldc, variant_id, beta, pm, pn, pk,
+                        _stream(stream)), "rg_gemm")
+
+
+def rg_gemm_status(ctx, M, N, K, A, lda, B, ldb, Cp, ldc, variant_id, beta=0, pm=0, pn=0, pk=0, stream=None) -> int:
+    """rg_gemm returning the status code instead of raising (for error-path tests)."""
+    return _lib.rg_gemm(ctx, M, N, K, _ptr(A), lda, _ptr(B), ldb, _ptr(Cp), ldc, variant_id, beta, pm, pn, pk,
+                        _stream(stream))
+
+
+RG_PLAN_PAD_ONLY = 1
+
+
+def rg_plan_build(grid: rg_grid, T0_ns: np.ndarray, variant_ids) -> int:
+    T0 = np.ascontiguousarray(T0_ns, dtype=np.int64).reshape(len(variant_ids), -1)
+    vids = np.ascontiguousarray(variant_ids, dtype=np.int32)
+    h = _P()
+    _check(_lib.rg_plan_build(C.byref(grid), T0.ctypes.data, len(vids), vids.ctypes.data, C.byref(h)),
+           "rg_plan_build")
+    return h.value
+
+
+def rg_plan_build_ex(grid: rg_grid, T0_ns: np.ndarray, variant_ids, flags: int) -> int:
+    T0 = np.ascontiguousarray(T0_ns, dtype=np.int64).reshape(len(variant_ids), -1)
+    vids = np.ascontiguousarray(variant_ids, dtype=np.int32)
+    h = _P()
+    _check(_lib.rg_plan_build_ex(C.byref(grid), T0.ctypes.data, len(vids), vids.ctypes.data, flags, C.byref(h)),
+           "rg_plan_build_ex")
+    return h.value
+
+
+def rg_set_test_stall(ctx: int, enable: bool) -> None:
+    _check(_lib.rg_set_test_stall(ctx, 1 if enable else 0), "rg_set_test_stall")
+
+
+def rg_launch_count(ctx: int) -> int:
+    v = _I64()
+    _check(_lib.rg_launch_count(ctx, C.byref(v)), "rg_launch_count")
+    return v.value
+
+
+def rg_plan_free(plan: int) -> None:
+    _lib.rg_plan_free(plan)
+
+
+def rg_plan_grid(plan: int) -> rg_grid:
+    g = rg_grid()
+    _check(_lib.rg_plan_grid(plan, C.byref(g)), "rg_plan_grid")
+    return g
+
+
+def rg_plan_tables(plan: int) -> dict:
+    g = rg_plan_grid(plan)
+    n = grid_cells(g)
+    t = {"T0s": np.zeros(n, np.int64), "vstar": np.zeros(n, np.int32), "T1": np.zeros(n, np.int64),
+         "target": np.zeros(3 * n, np.int32), "T2": np.zeros(n, np.int64), "action": np.zeros(n, np.int32),
+         "q": np.zeros(n, np.int32)}
+    _check(_lib.rg_plan_tables(plan, t["T0s"].ctypes.data, t["vstar"].ctypes.data, t["T1"].ctypes.data,
+                               t["target"].ctypes.data, t["T2"].ctypes.data, t["action"].ctypes.data,
+                               t["q"].ctypes.data), "rg_plan_tables")
+    shape = (g.m.count, g.n.count, g.k.count)
+    out = {k: v.reshape(shape) for k, v in t.items() if k != "target"}
+    out["target"] = t["target"].reshape(shape + (3,))
+    return out
+
+
+def rg_plan_lookup(plan: int, M: int, N: int, K: int):
+    """(list of leaf tuples (variant, beta, phase, m0, n0, k0, m, n, k, pm, pn, pk), T2 ns)."""
+    lp = C.POINTER(rg_leaf)()
+    n = _I32()
+    t2 = _I64()
+    _check(_lib.rg_plan_lookup(plan, M, N, K, C.byref(lp), C.byref(n), C.byref(t2)), "rg_plan_lookup")
+    leaves = []
+    for i in range(n.value):
+        L = lp[i]
+        leaves.append((L.variant, L.beta, L.phase, L.m0, L.n0, L.k0, L.m, L.n, L.k, L.pm, L.pn, L.pk))
+    return leaves, t2.value
+
+
+def rg_gemm_plan(ctx, plan, M, N, K, A, lda, B, ldb, Cp, ldc, stream=None) -> None:
+    _check(_lib.rg_gemm_plan(ctx, plan, M, N, K, _ptr(A), lda, _ptr(B), ldb, _ptr(Cp), ldc, _stream(stream)),
+           "rg_gemm_plan")
+
+
+def rg_plan_save(plan: int, path: str, ctx: int | None = None) -> None:
+    _check(_lib.rg_plan_save(plan, ctx, path.encode()), "rg_plan_save")
+
+
+def rg_plan_load(path: str, ctx: int | None = None) -> int:
+    h = _P()
+    _check(_lib.rg_plan_load(path.encode(), ctx, C.byref(h)), "rg_plan_load")
+    return h.value
+
+
+def rg_plan_load_status(path: str, ctx: int | None = None) -> int:
+    h = _P()
+    code = _lib.rg_plan_load(path.encode(), ctx, C.byref(h))
+    if code == RG_OK:
+        _lib.rg_plan_free(h.value)
+    return code
+
+
+def rg_surface_stats(grid: rg_grid, t_ns: np.ndarray):
+    """(tflops surface [cells], {R_M, R_N, R_K, R_3D, R_N_slice}, mean TFLOP/s)."""
+    t = np.ascontiguousarray(t_ns, dtype=np.int64).ravel()
+    tf = np.zeros(t.size, np.float64)
+    r = np.zeros(5, np.float64)
+    mean = C.c_double()
+    _check(_lib.rg_surface_stats(C.byref(grid), t.ctypes.data, tf.ctypes.data, r.ctypes.data, C.byref(mean)),
+           "rg_surface_stats")
+    keys = ("R_M", "R_N", "R_K", "R_3D", "R_N_slice")
+    return tf, dict(zip(keys, (float(x) for x in r))), mean.value
+
+
+def rg_sweep_opts_default() -> rg_sweep_opts:
+    o = rg_sweep_opts()
+    _lib.rg_sweep_opts_default(C.byref(o))
+    return o
+
+
+def rg_sweep(ctx, grid: rg_grid, variant_ids, A, B, Cp, opts: rg_sweep_opts | None = None, plan: int | None = None,
+             stream=None) -> np.ndarray:
+    """t_ns[len(variant_ids)][cells] (or [1][cells] for a plan sweep)."""
+    vids = np.ascontiguousarray(variant_ids if plan is None else [0], dtype=np.int32)
+    out = np.zeros((len(vids), grid_cells(grid)), np.int64)
+    o = opts or rg_sweep_opts_default()
+    _check(_lib.rg_sweep(ctx, C.byref(grid), len(vids), vids.ctypes.data, plan, _ptr(A), _ptr(B), _ptr(Cp),
+                         C.byref(o), out.ctypes.data, _stream(stream)), "rg_sweep")
+    return out

@@ -1,0 +1,190 @@
+"""C-ABI library on the CPU: it loads without a GPU, exports every function
+include/rg.h declares, and its host-side computations (plan tables, leaf
+lists, surface statistics, plan files) match the oracle bit-exactly."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import dp, roughness
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def rg():
+    from paper_2605_29752_gb300 import build
+    if not os.path.exists(build.LIB):
+        build.build()
+    from paper_2605_29752_gb300 import rg as _rg
+    return _rg
+
+
+def header_functions():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", fn)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names |= set(re.findall(r"\b(rg_\w+)\s*\(", text))
+    return sorted(n for n in names if n not in ("RG_VARIANT",))
+
+
+def test_library_exports_every_header_function(rg):
+    names = header_functions()
+    assert "rg_gemm" in names and "rg_plan_build" in names
+    lib = rg.library()
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_covers_header(rg):
+    assert set(header_functions()) <= set(rg.HEADER_SYMBOLS) | {n for n in dir(rg) if n.startswith("rg_")}
+
+
+def test_init_without_gpu_fails_cleanly(rg):
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(rg.RGError) as e:
+        rg.rg_init(0)
+    assert e.value.code == rg.RG_ERR_NO_DEVICE
+
+
+def _grid(rg, nm, nn, nk, step=128):
+    return rg.make_grid((step, step, nm), (step, step, nn), (step, step, nk))
+
+
+def _compare_plan(rg, T0v, vids, shape, check_leaves=True):
+    g = _grid(rg, *shape)
+    ogrid = ((128, 128, shape[0]), (128, 128, shape[1]), (128, 128, shape[2]))
+    ref = dp.plan(T0v, ogrid)
+    h = rg.rg_plan_build(g, T0v.reshape(len(vids), -1), vids)
+    try:
+        t = rg.rg_plan_tables(h)
+        assert np.array_equal(t["T0s"], ref["T0s"])
+        assert np.array_equal(t["vstar"], np.asarray(vids)[ref["vstar"]])
+        assert np.array_equal(t["T1"], ref["T1"])
+        assert np.array_equal(t["target"], ref["target"])
+        assert np.array_equal(t["T2"], ref["T2"])
+        assert np.array_equal(t["action"], ref["action"])
+        assert np.array_equal(t["q"], ref["q"])
+        if check_leaves:
+            for cell, leaves in ref["leaves"].items():
+                M, N, K = ((cell[i] + 1) * 128 for i in range(3))
+                got, t2 = rg.rg_plan_lookup(h, M, N, K)
+                want = [(int(vids[l[0]]),) + tuple(int(x) for x in l[1:]) for l in leaves]
+                assert got == want, cell
+                assert t2 == ref["T2"][cell]
+    finally:
+        rg.rg_plan_free(h)
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_plan_tables_match_oracle_small(rg, seed):
+    rng = np.random.default_rng(seed)
+    shape = tuple(int(x) for x in rng.integers(1, 6, size=3))
+    V = int(rng.integers(1, 5))
+    vids = sorted(rng.choice(24, size=V, replace=False).tolist())
+    T0v = rng.integers(1, 200, size=(V,) + shape).astype(np.int64)
+    _compare_plan(rg, T0v, vids, shape)
+
+
+def _landscape_like(rng, shape, V):
+    M = (np.arange(shape[0]) + 1)[:, None, None] * 128.0
+    N = (np.arange(shape[1]) + 1)[None, :, None] * 128.0
+    K = (np.arange(shape[2]) + 1)[None, None, :] * 128.0
+    base = 2500 + 2 * M * N * K / 1.1e6
+    saw = 1 + 0.3 * ((N / 128) % 3 == 1)
+    return np.stack([np.round(base * saw * rng.uniform(0.85, 1.5, size=shape)).astype(np.int64) for _ in range(V)])
+
+
+def test_plan_tables_match_oracle_full_grid(rg):
+    rng = np.random.default_rng(11)
+    shape = (32, 32, 32)
+    T0v = _landscape_like(rng, shape, 6)
+    _compare_plan(rg, T0v, [0, 4, 8, 12, 16, 20], shape, check_leaves=False)
+
+
+def test_plan_leaves_match_oracle_medium_grid(rg):
+    rng = np.random.default_rng(5)
+    shape = (12, 10, 14)
+    T0v = _landscape_like(rng, shape, 4)
+    _compare_plan(rg, T0v, [1, 5, 9, 13], shape, check_leaves=True)
+
+
+def test_surface_stats_match_oracle_bit_exact(rg):
+    rng = np.random.default_rng(2)
+    for shape in ((32, 32, 32), (4, 4, 4), (1, 7, 3), (5, 1, 1)):
+        g = _grid(rg, *shape)
+        t = rng.integers(1000, 5_000_000, size=shape).astype(np.int64)
+        ogrid = ((128, 128, shape[0]), (128, 128, shape[1]), (128, 128, shape[2]))
+        S = roughness.surface(t, ogrid)
+        ref = roughness.roughness_all(S)
+        tf, r, mean = rg.rg_surface_stats(g, t)
+        assert np.array_equal(tf.reshape(shape), S)
+        assert mean == roughness.mean(S)
+        for k in ref:
+            assert r[k] == ref[k], (shape, k)
+
+
+def test_surface_stats_non_step_grid(rg):
+    g = rg.make_grid((256, 128, 5), (64, 32, 6), (128, 128, 3))
+    rng = np.random.default_rng(9)
+    t = rng.integers(10, 10**7, size=(5, 6, 3)).astype(np.int64)
+    S = roughness.surface(t, ((256, 128, 5), (64, 32, 6), (128, 128, 3)))
+    tf, r, mean = rg.rg_surface_stats(g, t)
+    assert np.array_equal(tf.reshape(5, 6, 3), S) and r == roughness.roughness_all(S)
+
+
+def test_plan_save_load_roundtrip_and_checksum(rg, tmp_path):
+    rng = np.random.default_rng(4)
+    T0v = rng.integers(1, 100, size=(2, 3, 4, 5)).astype(np.int64)
+    g = _grid(rg, 3, 4, 5)
+    h = rg.rg_plan_build(g, T0v.reshape(2, -1), [3, 7])
+    p = str(tmp_path / "plan.bin")
+    rg.rg_plan_save(h, p)
+    h2 = rg.rg_plan_load(p)
+    try:
+        a, b = rg.rg_plan_tables(h), rg.rg_plan_tables(h2)
+        assert all(np.array_equal(a[k], b[k]) for k in a)
+        assert rg.rg_plan_lookup(h, 300, 500, 600) == rg.rg_plan_lookup(h2, 300, 500, 600)
+    finally:
+        rg.rg_plan_free(h2)
+        rg.rg_plan_free(h)
+    data = bytearray(open(p, "rb").read())
+    data[-3] ^= 0x55
+    bad = str(tmp_path / "bad.bin")
+    open(bad, "wb").write(bytes(data))
+    assert rg.rg_plan_load_status(bad) == rg.RG_ERR_PLAN_MISMATCH
+    open(bad, "wb").write(b"not a plan")
+    assert rg.rg_plan_load_status(bad) == rg.RG_ERR_PLAN_MISMATCH
+
+
+def test_lookup_rounds_up_and_rejects_beyond_grid(rg):
+    T0 = np.arange(1, 2 * 3 * 4 + 1, dtype=np.int64).reshape(1, -1)
+    g = _grid(rg, 2, 3, 4)
+    h = rg.rg_plan_build(g, T0, [5])
+    try:
+        l1, _ = rg.rg_plan_lookup(h, 129, 1, 384)
+        l2, _ = rg.rg_plan_lookup(h, 256, 128, 384)
+        assert l1 == l2
+        with pytest.raises(rg.RGError) as e:
+            rg.rg_plan_lookup(h, 257, 128, 128)
+        assert e.value.code == rg.RG_ERR_SHAPE
+        with pytest.raises(rg.RGError):
+            rg.rg_plan_lookup(h, 0, 128, 128)
+    finally:
+        rg.rg_plan_free(h)
+
+
+def test_plan_build_rejects_bad_input(rg):
+    g = _grid(rg, 2, 2, 2)
+    with pytest.raises(rg.RGError):
+        rg.rg_plan_build(g, np.zeros((1, 8), np.int64), [0])          # non-positive times
+    with pytest.raises(rg.RGError):
+        rg.rg_plan_build(g, np.ones((2, 8), np.int64), [4, 4])        # ids not increasing
+    g2 = rg.make_grid((256, 128, 2))
+    with pytest.raises(rg.RGError):
+        rg.rg_plan_build(g2, np.ones((1, 8), np.int64), [0])          # start != step

@@ -1,0 +1,182 @@
+"""GPU parity of the BF16 NN GEMM (rg_gemm through the C ABI) against the CPU
+oracle: every variant, the small-sweep shapes, ragged and padded shapes,
+beta = 1, split-K, closed forms, full-size sampled rows and columns, and the
+error paths."""
+import numpy as np
+import pytest
+
+import synthetic
+from oracle import gemm as og
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+ALL_VARIANTS = list(range(24))
+
+
+@pytest.fixture(scope="module")
+def rg():
+    from paper_2605_29752_gb300 import rg as _rg
+    return _rg
+
+
+@pytest.fixture(scope="module")
+def ctx(rg):
+    h = rg.rg_init(0)
+    yield h
+    rg.rg_destroy(h)
+
+
+def dev_bf16(bits):
+    return torch.from_numpy(np.ascontiguousarray(bits).view(np.int16)).cuda().view(torch.bfloat16)
+
+
+def run(rg, ctx, a_bits, b_bits, v, beta=0, c0=None, pads=(0, 0, 0)):
+    M, K = a_bits.shape
+    N = b_bits.shape[1]
+    A, B = dev_bf16(a_bits), dev_bf16(b_bits)
+    C = torch.full((M, N), float("nan"), device="cuda", dtype=torch.float32) if c0 is None else \
+        torch.from_numpy(c0.astype(np.float32)).cuda()
+    rg.rg_gemm(ctx, M, N, K, A, K, B, N, C, N, v, beta, *pads)
+    rg.rg_check(ctx)
+    return C.cpu().numpy()
+
+
+def check(c, a_bits, b_bits, c0=None):
+    a, b = og.bf16_bits_to_f64(a_bits), og.bf16_bits_to_f64(b_bits)
+    c64 = og.gemm_f64(a, b)
+    s = og.abs_sum(a, b)
+    if c0 is not None:
+        c64 = c64 + c0.astype(np.float32).astype(np.float64)
+        s = s + np.abs(c0.astype(np.float32).astype(np.float64))
+    ratio, exact_zero = og.error_ratio(c, c64, s)
+    K = a.shape[1]
+    assert not np.any(np.isnan(c)), "unwritten output elements"
+    assert exact_zero and ratio <= og.bound(K + (1 if c0 is not None else 0)), ratio
+    return ratio
+
+
+@pytest.mark.parametrize("v", ALL_VARIANTS)
+def test_every_variant_ragged(rg, ctx, v):
+    M, N, K = 300, 200, 328           # partial tiles in M, N and K for every tile shape
+    a, b = synthetic.operands_bf16(M, N, K, seed=1)
+    check(run(rg, ctx, a, b, v), a, b)
+
+
+SMALL = [128, 256, 384, 512]
+
+
+@pytest.mark.parametrize("M", SMALL)
+@pytest.mark.parametrize("N", SMALL)
+@pytest.mark.parametrize("K", SMALL)
+def test_small_sweep_shapes_full_matrix(rg, ctx, M, N, K):
+    a, b = synthetic.operands_bf16(M, N, K, seed=0)
+    check(run(rg, ctx, a, b, rg.variant(1, 1)), a, b)
+
+
+@pytest.mark.parametrize("v", [rg_v for rg_v in (0, 4, 8, 12, 16, 20, 9, 22)])
+def test_identity_all_ones_rank_one_exact(rg, ctx, v):
+    one = np.float32(1.0).view(np.uint32) >> 16
+    K = 256
+    eye = np.zeros((K, K), np.uint16)
+    eye[np.arange(K), np.arange(K)] = one
+    _, b = synthetic.operands_bf16(K, 320, K, seed=2)
+    c = run(rg, ctx, eye, b, v)
+    assert np.array_equal(c, og.bf16_bits_to_f64(b).astype(np.float32))
+    ones_a = np.full((192, 384), one, np.uint16)
+    ones_b = np.full((384, 136), one, np.uint16)
+    assert np.all(run(rg, ctx, ones_a, ones_b, v) == 384.0)
+    a, b = synthetic.operands_bf16(200, 264, 96, seed=3)
+    a1 = np.zeros_like(a)
+    a1[:, 17] = a[:, 17]
+    c = run(rg, ctx, a1, b, v)
+    exact = np.outer(og.bf16_bits_to_f64(a1[:, 17]), og.bf16_bits_to_f64(b[17, :])).astype(np.float32)
+    assert np.array_equal(c, exact)
+
+
+@pytest.mark.parametrize("v", [1, 6, 13, 21])
+def test_disjoint_k_blocks(rg, ctx, v):
+    # A nonzero only in K-block 0 columns, B only in the last K block rows: C == 0 exactly
+    M, N, K = 256, 256, 1024
+    a, b = synthetic.operands_bf16(M, N, K, seed=4)
+    a[:, 64:] = 0
+    b[:-64, :] = 0
+    assert np.all(run(rg, ctx, a, b, v) == 0.0)
+
+
+@pytest.mark.parametrize("v", [0, 5, 10, 15, 19, 23])
+def test_padding_gives_same_result(rg, ctx, v):
+    M, N, K = 256, 384, 256
+    a, b = synthetic.operands_bf16(M, N, K, seed=5)
+    c_plain = run(rg, ctx, a, b, v)
+    c_pad = run(rg, ctx, a, b, v, pads=(M + 256, N + 128, K + 384))
+    check(c_pad, a, b)
+    if rg.SPLITS[v % 4] == 1:
+        # zero K padding adds exact zeros: bitwise the same result
+        assert np.array_equal(c_plain, c_pad)
+    # M/N padding alone never changes any output element's summation
+    assert np.array_equal(c_plain, run(rg, ctx, a, b, v, pads=(M + 256, N + 128, K)))
+
+
+@pytest.mark.parametrize("v", [1, 3, 9, 18])
+def test_beta_one_accumulates(rg, ctx, v):
+    M, N, K = 384, 256, 512
+    a, b = synthetic.operands_bf16(M, N, K, seed=6)
+    c0 = synthetic.normal_stream_f32(6, 5, M * N).reshape(M, N)
+    check(run(rg, ctx, a, b, v, beta=1, c0=c0), a, b, c0=c0)
+
+
+@pytest.mark.parametrize("v", [1, 2, 3, 7, 11, 15, 19, 23])
+def test_split_k_deterministic(rg, ctx, v):
+    M, N, K = 512, 384, 2048
+    a, b = synthetic.operands_bf16(M, N, K, seed=7)
+    c1 = run(rg, ctx, a, b, v)
+    c2 = run(rg, ctx, a, b, v)
+    check(c1, a, b)
+    assert np.array_equal(c1, c2)
+
+
+def test_more_splits_than_k_blocks(rg, ctx):
+    M, N, K = 128, 128, 128                  # 2 K blocks, 8 splits: six splits add exact zeros
+    a, b = synthetic.operands_bf16(M, N, K, seed=8)
+    check(run(rg, ctx, a, b, rg.variant(1, 8)), a, b)
+
+
+@pytest.mark.parametrize("shape", [(4096, 4096, 4096), (3968, 4096, 3840), (4096, 1152, 4096)])
+@pytest.mark.parametrize("tile", range(6))
+def test_full_size_sampled(rg, ctx, shape, tile):
+    M, N, K = shape
+    a_bits, b_bits = synthetic.operands_bf16(M, N, K, seed=0)
+    c = run(rg, ctx, a_bits, b_bits, rg.variant(tile, 1 if tile % 2 else 2))
+    a, b = og.bf16_bits_to_f64(a_bits), og.bf16_bits_to_f64(b_bits)
+    rs = np.random.default_rng(tile)
+    rows = rs.choice(M, 8, replace=False)
+    cols = rs.choice(N, 8, replace=False)
+    cr, sr, cc, sc = og.sampled_rows_cols(a, b, rows, cols)
+    for got, ref, s in ((c[rows, :], cr, sr), (c[:, cols], cc, sc)):
+        ratio, exact_zero = og.error_ratio(got, ref, s)
+        assert exact_zero and ratio <= og.bound(K), ratio
+
+
+def test_empty_and_k_zero(rg, ctx):
+    C = torch.full((4, 8), 5.0, device="cuda")
+    A = torch.zeros((4, 8), device="cuda", dtype=torch.bfloat16)
+    rg.rg_gemm(ctx, 0, 8, 8, A, 8, A, 8, C, 8, 1)
+    rg.rg_gemm(ctx, 4, 8, 0, A, 8, A, 8, C, 8, 1, 1)     # beta = 1, K = 0: C unchanged
+    rg.rg_check(ctx)
+    assert torch.all(C == 5.0)
+    rg.rg_gemm(ctx, 4, 8, 0, A, 8, A, 8, C, 8, 1, 0)     # beta = 0, K = 0: C = 0
+    rg.rg_check(ctx)
+    assert torch.all(C == 0.0)
+
+
+def test_alignment_and_argument_errors(rg, ctx):
+    A = torch.zeros((64, 64), device="cuda", dtype=torch.bfloat16)
+    C = torch.zeros((64, 64), device="cuda")
+    assert rg.rg_gemm_status(ctx, 64, 64, 60, A, 60, A, 64, C, 64, 1) == rg.RG_ERR_ALIGN
+    assert rg.rg_gemm_status(ctx, 64, 64, 64, A.data_ptr() + 2, 64, A, 64, C, 64, 1) == rg.RG_ERR_ALIGN
+    assert rg.rg_gemm_status(ctx, 64, 64, 64, A, 64, A, 64, C, 64, 99) == rg.RG_ERR_INVALID
+    assert rg.rg_gemm_status(ctx, 64, 64, 64, A, 64, A, 64, C, 64, 1, 2) == rg.RG_ERR_INVALID
+    assert rg.rg_gemm_status(ctx, 64, 64, 64, A, 64, A, 64, C, 64, 1, 0, 32) == rg.RG_ERR_INVALID
+    assert rg.rg_gemm_status(ctx, 64, 64, 64, A, 32, A, 64, C, 64, 1) == rg.RG_ERR_INVALID
+    rg.rg_check(ctx)

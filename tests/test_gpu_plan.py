@@ -1,0 +1,150 @@
+"""GPU parity of plan execution (rg_gemm_plan: O(1) lookup, then the cell's
+padded / split leaves, Sec. 7.1) and of the sweep (rg_sweep) against the
+oracle."""
+import numpy as np
+import pytest
+
+import synthetic
+from oracle import dp
+from oracle import gemm as og
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def rg():
+    from paper_2605_29752_gb300 import rg as _rg
+    return _rg
+
+
+@pytest.fixture(scope="module")
+def ctx(rg):
+    h = rg.rg_init(0)
+    yield h
+    rg.rg_destroy(h)
+
+
+def dev_bf16(bits):
+    return torch.from_numpy(np.ascontiguousarray(bits).view(np.int16)).cuda().view(torch.bfloat16)
+
+
+def _plan_with_every_action(rg, shape, seed):
+    """A plan over a step-128 grid whose T0 favours splits and padding somewhere."""
+    rng = np.random.default_rng(seed)
+    vids = [0, 5, 10, 14, 17, 21]
+    T0 = rng.integers(50, 5000, size=(len(vids),) + shape).astype(np.int64)
+    g = rg.make_grid((128, 128, shape[0]), (128, 128, shape[1]), (128, 128, shape[2]))
+    h = rg.rg_plan_build(g, T0.reshape(len(vids), -1), vids)
+    ref = dp.plan(T0, ((128, 128, shape[0]), (128, 128, shape[1]), (128, 128, shape[2])))
+    acts = set(int(a) for a in ref["action"].ravel())
+    return h, acts, ref
+
+
+def _exec(rg, ctx, plan, M, N, K, seed=0):
+    a_bits, b_bits = synthetic.operands_bf16(M, N, K, seed=seed)
+    A, B = dev_bf16(a_bits), dev_bf16(b_bits)
+    C = torch.full((M, N), float("nan"), device="cuda")
+    rg.rg_gemm_plan(ctx, plan, M, N, K, A, K, B, N, C, N)
+    rg.rg_check(ctx)
+    c = C.cpu().numpy()
+    ok, ratio = og.check(c, og.bf16_bits_to_f64(a_bits), og.bf16_bits_to_f64(b_bits))
+    assert not np.any(np.isnan(c)) and ok, (M, N, K, ratio)
+    return c
+
+
+def test_plan_execution_every_cell(rg, ctx):
+    shape = (4, 4, 4)
+    h, acts, ref = _plan_with_every_action(rg, shape, seed=0)
+    try:
+        assert acts >= {0, 1, 2, 3}, acts                 # keep/pad and all three split axes occur
+        assert any(tuple(ref["target"][c]) != c for c in np.ndindex(*shape))   # and padding
+        for a in range(4):
+            for b in range(4):
+                for c in range(4):
+                    _exec(rg, ctx, h, 128 * (a + 1), 128 * (b + 1), 128 * (c + 1))
+    finally:
+        rg.rg_plan_free(h)
+
+
+@pytest.mark.parametrize("shape", [(200, 136, 96), (511, 384, 264), (1, 8, 8), (384, 504, 512)])
+def test_plan_execution_off_grid_shapes(rg, ctx, shape):
+    h, _, _ = _plan_with_every_action(rg, (4, 4, 4), seed=5)
+    try:
+        _exec(rg, ctx, h, *shape)
+    finally:
+        rg.rg_plan_free(h)
+
+
+def test_plan_execution_k_chain_beta(rg, ctx):
+    # a 1 x 1 x 8 grid where K splits win: the plan becomes a chain of beta = 1 leaves
+    T0 = np.array([[[100, 10000, 10000, 10000, 10000, 10000, 10000, 10000]]], dtype=np.int64)
+    g = rg.make_grid((128, 128, 1), (128, 128, 1), (128, 128, 8))
+    h = rg.rg_plan_build(g, T0.reshape(1, -1), [5])
+    try:
+        leaves, t2 = rg.rg_plan_lookup(h, 128, 128, 1024)
+        assert len(leaves) == 8 and [l[1] for l in leaves] == [0] + [1] * 7 and t2 == 800
+        _exec(rg, ctx, h, 128, 128, 1024)
+        _exec(rg, ctx, h, 100, 72, 1000)
+    finally:
+        rg.rg_plan_free(h)
+
+
+def test_sweep_tiny_grid_and_plan_sweep(rg, ctx):
+    g = rg.make_grid((128, 128, 3))
+    Mx = 384
+    a_bits, b_bits = synthetic.operands_bf16(Mx, Mx, Mx)
+    A = dev_bf16(synthetic.bf16_uniform_stream(0, synthetic.TAG_A, Mx * Mx))
+    B = dev_bf16(synthetic.bf16_uniform_stream(0, synthetic.TAG_B, Mx * Mx))
+    C = torch.zeros(Mx * Mx, device="cuda")
+    vids = [rg.variant(1, 1), rg.variant(2, 2)]
+    opts = rg.rg_sweep_opts_default()
+    opts.prune_splits = 0
+    t = rg.rg_sweep(ctx, g, vids, A, B, C, opts)
+    assert t.shape == (2, 27) and np.all(t > 0) and np.all(t < 10**8)
+    opts.prune_splits = 1
+    tp = rg.rg_sweep(ctx, g, vids, A, B, C, opts)
+    assert np.all(tp[0] < 10**8)                       # split 1 is always timed
+    Ks = np.tile(np.array([128, 256, 384]), 9)
+    assert np.all(tp[1][Ks < 256] == rg.RG_T_UNMEASURED)   # fewer than 2 K blocks per split
+    assert np.all(tp[1][Ks >= 256] < 10**8)                # few tiles: the split variant is timed
+    plan = rg.rg_plan_build(g, t, vids)
+    try:
+        tp = rg.rg_sweep(ctx, g, [0], A, B, C, opts, plan=plan)
+        assert tp.shape == (1, 27) and np.all(tp > 0)
+        # the last swept cell's C is the plan's result for 384^3 only if it ran last;
+        # run it explicitly and check it
+        _exec(rg, ctx, plan, 384, 384, 384)
+        tf, r, mean = rg.rg_surface_stats(g, tp[0])
+        assert mean > 0 and all(v >= 0 for v in r.values())
+    finally:
+        rg.rg_plan_free(plan)
+    n0 = rg.rg_launch_count(ctx)
+    rg.rg_gemm(ctx, 128, 128, 128, A, 128, B, 128, C, 128, 1)
+    assert rg.rg_launch_count(ctx) == n0 + 1
+
+
+def test_timeout_path_returns_error_and_context_recovers(rg, ctx):
+    """With the test stall on, the MMA warp waits on a barrier nothing arrives on;
+    its bounded wait (here about a millisecond) must expire, the kernel must
+    record the error, let its copies land, release TMEM and return, and the next
+    launch without the stall must compute the right result."""
+    M = N = K = 1024
+    a_bits, b_bits = synthetic.operands_bf16(M, N, K, seed=9)
+    A, B = dev_bf16(a_bits), dev_bf16(b_bits)
+    C = torch.zeros((M, N), device="cuda")
+    rg.rg_set_timeout_cycles(ctx, 2_000_000)
+    rg.rg_set_test_stall(ctx, True)
+    try:
+        rg.rg_gemm(ctx, M, N, K, A, K, B, N, C, N, rg.variant(1, 2))
+        status = rg.rg_check_status(ctx)
+    finally:
+        rg.rg_set_test_stall(ctx, False)
+        rg.rg_set_timeout_cycles(ctx, 2_000_000_000)
+    assert status == rg.RG_ERR_TIMEOUT
+    assert rg.rg_check_status(ctx) == rg.RG_OK          # the error word was cleared
+    C.fill_(float("nan"))
+    rg.rg_gemm(ctx, M, N, K, A, K, B, N, C, N, rg.variant(1, 2))
+    rg.rg_check(ctx)
+    ok, _ = og.check(C.cpu().numpy(), og.bf16_bits_to_f64(a_bits), og.bf16_bits_to_f64(b_bits))
+    assert ok
