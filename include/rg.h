@@ -208,6 +208,38 @@ int rg_sweep(rg_ctx* ctx, const rg_grid* grid, int32_t n_variants, const int32_t
              const rg_plan* plan, const void* A, const void* B, float* C,
              const rg_sweep_opts* opts, int64_t* t_ns_out, void* stream);
 
+/* ---- GEMM without device allocation ----
+ * The paper has no counterpart to this entry point.  It is for callers that
+ * must not allocate device memory on their call path (a host framework whose
+ * own allocator owns the device memory budget, or code that cannot afford the
+ * implicit device synchronisation cudaMalloc may cause).  It computes exactly
+ * what rg_gemm computes (same kernel, same summation order) but needs no
+ * rg_ctx: its split-K scratch -- partial sums, tile tickets and the
+ * bounded-wait error word -- lives in one fixed device array inside the
+ * library, RG_NOALLOC_PARTIAL_BYTES of partials plus tickets for
+ * RG_NOALLOC_MAX_TILES output tiles (about 16.3 MiB), which every GPU that
+ * loads the library holds until the process exits.
+ *   - Runs on the calling thread's current device, on `stream`.  The caller
+ *     still owns and passes A, B and C (device memory, rg_gemm conventions).
+ *   - The first call on a device does a one-time set-up on that device (device
+ *     check, kernel attributes, the scratch array's device address); make that
+ *     first call before any stream capture.
+ *   - Split-K launches (variant with S > 1) whose partials would exceed the
+ *     scratch (S * tiles * BM * BN * 4 > RG_NOALLOC_PARTIAL_BYTES, or more than
+ *     RG_NOALLOC_MAX_TILES tiles) are rejected with RG_ERR_SHAPE before any
+ *     work is enqueued; split 1 has no size limit beyond rg_gemm's.
+ *   - Every call shares the one scratch array and it keeps the previous call's
+ *     contents; each call clears the tickets and error word it uses (an async
+ *     memset on `stream`).  Calls whose work overlaps on the GPU (other streams,
+ *     other threads) race on the scratch: order them.
+ *   - Calls no cudaMalloc, cudaFree or other allocating routine.  A bounded
+ *     wait that expires is recorded only in the scratch's error word; the
+ *     kernel still returns. */
+#define RG_NOALLOC_PARTIAL_BYTES ((int64_t)16 << 20)
+#define RG_NOALLOC_MAX_TILES 4096
+int rg_gemm_noalloc(int64_t M, int64_t N, int64_t K, const void* A, int64_t lda, const void* B, int64_t ldb,
+                    float* C, int64_t ldc, int32_t variant, int32_t beta, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -881,3 +881,112 @@ extern "C" int rg_sweep(rg_ctx* ctx, const rg_grid* grid, int32_t n_variants, co
   }
   return rg_check(ctx, stream);
 }
+
+// ------------------------------------------------------------------ entry point without allocation
+//
+// rg_gemm_noalloc runs the same kernel as rg_gemm, but its split-K scratch
+// (partial sums, tile tickets, the bounded-wait error word) lives in one
+// file-scope device array instead of memory from cudaMalloc.  It is for
+// callers that must not allocate device memory on their call path: a host
+// framework whose own allocator owns the device memory budget, or code that
+// cannot afford the implicit device synchronisation cudaMalloc may cause.
+// The array is part of the library image: every GPU that loads the library
+// holds it until the process exits.
+namespace rg {
+
+constexpr int64_t kNoallocPartialBytes = RG_NOALLOC_PARTIAL_BYTES;
+constexpr int64_t kNoallocTickets = 4 * RG_NOALLOC_MAX_TILES;
+// layout: [partials | error word, padded to 256 B | tickets]
+constexpr int64_t kNoallocErrOff = kNoallocPartialBytes;
+constexpr int64_t kNoallocTicketOff = kNoallocErrOff + 256;
+constexpr int64_t kNoallocBytes = kNoallocTicketOff + kNoallocTickets * 4;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
+
+struct NoallocDevice {
+  bool ready = false;
+  unsigned char* scratch = nullptr;  // device address of g_noalloc_scratch on this device
+  int sm_count = 0;
+};
+constexpr int kNoallocMaxDevices = 64;
+static NoallocDevice g_noalloc_dev[kNoallocMaxDevices];
+static std::mutex g_noalloc_mu;
+
+// One-time set-up per device, run by the first call on that device with the
+// device current: checks the device, resolves the tensor-map encoder, sets the
+// kernels' shared-memory limit and looks up the array's device address.
+static int noalloc_setup(int dev, NoallocDevice** out) {
+  if (dev < 0 || dev >= kNoallocMaxDevices) return fail(RG_ERR_INVALID, "rg_gemm_noalloc: device index too large");
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  NoallocDevice& d = g_noalloc_dev[dev];
+  if (!d.ready) {
+    int major = 0, minor = 0, sms = 0;
+    cudaError_t e = cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return cuda_fail(e, "rg_gemm_noalloc: device attributes");
+    if (major != 10 || minor != 3) return fail(RG_ERR_NO_DEVICE, "rg_gemm_noalloc: needs a compute capability 10.3 device");
+    int rc = get_encode();
+    if (rc != RG_OK) return rc;
+    for (int t = 0; t < RG_NUM_TILES; ++t) {
+      const TileKernel& tk = tile_kernel(t);
+      e = cudaFuncSetAttribute(reinterpret_cast<const void*>(tk.fn), cudaFuncAttributeMaxDynamicSharedMemorySize, tk.smem);
+      if (e != cudaSuccess) return cuda_fail(e, "rg_gemm_noalloc: shared-memory attribute");
+    }
+    void* ptr = nullptr;
+    e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+    if (e != cudaSuccess || ptr == nullptr) return cuda_fail(e, "rg_gemm_noalloc: cudaGetSymbolAddress of the scratch array");
+    d.scratch = static_cast<unsigned char*>(ptr);
+    d.sm_count = sms;
+    d.ready = true;
+  }
+  *out = &d;
+  return RG_OK;
+}
+
+}  // namespace rg
+
+extern "C" int rg_gemm_noalloc(int64_t M, int64_t N, int64_t K, const void* A, int64_t lda, const void* B,
+                               int64_t ldb, float* C, int64_t ldc, int32_t variant, int32_t beta, void* stream) {
+  rg::clear_error();
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return rg::cuda_fail(e, "rg_gemm_noalloc: cudaGetDevice");
+  rg::NoallocDevice* d = nullptr;
+  int rc = rg::noalloc_setup(dev, &d);
+  if (rc != RG_OK) return rc;
+  if (variant < 0 || variant >= RG_NUM_VARIANTS) return rg::fail(RG_ERR_INVALID, "rg_gemm_noalloc: variant id out of range");
+  const int splits = rg::variant_split(variant);
+  if (splits > 1 && M > 0 && N > 0) {
+    const rg::TileShape ts = rg::tile_shape(rg::variant_tile(variant));
+    const int64_t tiles = ((M + ts.bm - 1) / ts.bm) * ((N + ts.bn - 1) / ts.bn);
+    const int64_t need = static_cast<int64_t>(splits) * tiles * ts.bm * ts.bn * 4;
+    if (need > rg::kNoallocPartialBytes || tiles > RG_NOALLOC_MAX_TILES)
+      return rg::fail(RG_ERR_SHAPE, "rg_gemm_noalloc: split-K needs " + std::to_string(need) +
+                                        " scratch bytes and " + std::to_string(tiles) + " tiles; the fixed scratch holds " +
+                                        std::to_string(rg::kNoallocPartialBytes) + " bytes and " +
+                                        std::to_string(RG_NOALLOC_MAX_TILES) + " tiles");
+  }
+  // A context whose workspace, tickets and error word are views of the scratch
+  // array; constructing it allocates nothing on the device.
+  rg_ctx view;
+  view.device = dev;
+  view.sm_count = d->sm_count;
+  view.ws = reinterpret_cast<float*>(d->scratch);
+  view.ws_bytes = rg::kNoallocPartialBytes;
+  view.err = reinterpret_cast<int32_t*>(d->scratch + rg::kNoallocErrOff);
+  view.tickets = reinterpret_cast<int32_t*>(d->scratch + rg::kNoallocTicketOff);
+  rg::Launch L;
+  rc = rg::prepare(&view, M, N, K, A, lda, B, ldb, C, ldc, variant, beta, 0, 0, 0, &L);
+  if (rc != RG_OK) return rc;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (!L.noop && !L.zero_only) {
+    // the error word and the tickets this launch uses must start at zero
+    const int64_t clear = rg::kNoallocTicketOff - rg::kNoallocErrOff +
+                          (splits > 1 ? static_cast<int64_t>(L.args.tiles_m) * L.args.tiles_n * 4 * 4 : 0);
+    e = cudaMemsetAsync(d->scratch + rg::kNoallocErrOff, 0, static_cast<size_t>(clear), st);
+    if (e != cudaSuccess) return rg::cuda_fail(e, "rg_gemm_noalloc: clear tickets");
+  }
+  e = rg::launch(&view, L, st);
+  return e == cudaSuccess ? RG_OK : rg::cuda_fail(e, "rg_gemm_noalloc: launch");
+}

@@ -95,6 +95,7 @@ _sigs = {
     "rg_plan_build_ex": (C.c_int, [C.POINTER(rg_grid), _P, _I32, _P, _I32, C.POINTER(_P)]),
     "rg_launch_count": (C.c_int, [_P, C.POINTER(_I64)]),
     "rg_set_test_stall": (C.c_int, [_P, _I32]),
+    "rg_gemm_noalloc": (C.c_int, [_I64, _I64, _I64, _P, _I64, _P, _I64, _P, _I64, _I32, _I32, _P]),
     "rg_plan_free": (None, [_P]),
     "rg_plan_grid": (C.c_int, [_P, C.POINTER(rg_grid)]),
     "rg_plan_tables": (C.c_int, [_P, _P, _P, _P, _P, _P, _P, _P]),
@@ -329,3 +330,14 @@ def rg_sweep(ctx, grid: rg_grid, variant_ids, A, B, Cp, opts: rg_sweep_opts | No
     _check(_lib.rg_sweep(ctx, C.byref(grid), len(vids), vids.ctypes.data, plan, _ptr(A), _ptr(B), _ptr(Cp),
                          C.byref(o), out.ctypes.data, _stream(stream)), "rg_sweep")
     return out
+
+
+RG_NOALLOC_PARTIAL_BYTES = 16 << 20
+RG_NOALLOC_MAX_TILES = 4096
+
+
+def rg_gemm_noalloc(M, N, K, A, lda, B, ldb, Cp, ldc, variant_id, beta=0, stream=None) -> int:
+    """GEMM that allocates no device memory (scratch in a fixed array inside the
+    library); returns the status code.  See include/rg.h for its limits."""
+    return _lib.rg_gemm_noalloc(M, N, K, _ptr(A), lda, _ptr(B), ldb, _ptr(Cp), ldc, variant_id, beta,
+                                _stream(stream))
