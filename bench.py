@@ -508,6 +508,25 @@ def extras(args, rg, ctx, grid, T0v, plan_smooth, A, B, C, flops, Mv, Nv, Kv, de
             ct[rg.variant_name(v)] = {"period_steps": lag, "autocorr": corr, "mean": float(tfl.mean()),
                                       "roughness": float(np.mean(np.abs(np.diff(tfl))))}
         out["cross_tile_N_at_M_K_2048"] = ct
+    # ---- first-principles GB300 landscapes (Sec. 9) and KOL grades (Sec. 10) of the measured surfaces
+    bw = (json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("hbm_gbs", 6800.0)
+          if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 6800.0)
+    ideal = rg.rg_landscape(grid, rg.RG_LANDSCAPE_IDEAL, p_burst, sms, 0.0, [(128, 128)])
+    opt = rg.rg_landscape(grid, rg.RG_LANDSCAPE_OPTIMAL, p_burst, sms, bw, rg.TILES)
+    fp = {}
+    for name, surf in (("ideal_128x128", ideal), ("optimal_six_tiles", opt)):
+        t_eq = np.maximum(1, np.round(flops / (surf * 1e3))).astype(np.int64)   # as integer ns, for the stats call
+        _, r, _ = rg.rg_surface_stats(grid, t_eq)
+        fp[name] = {"mean_tflops": float(surf.mean()), "R_N_slice": r["R_N_slice"], "R_3D": r["R_3D"]}
+    fp["constants"] = {"P_tflops": p_burst, "C_sms": sms, "BW_gbs": bw, "eta_channel": 1.0}
+    out["first_principles"] = fp
+    o = fp["optimal_six_tiles"]
+    out["kol"] = {name: rg.rg_kol(ladder_mean, o["mean_tflops"], ladder_r, o["R_N_slice"])
+                  for name, ladder_mean, ladder_r in (
+                      ("fixed_128x128", ladder["fixed_128x128"]["mean_tflops"], ladder["fixed_128x128"]["R_N_slice"]),
+                      ("best_of_6", ladder["best_of_6"]["mean_tflops"], ladder["best_of_6"]["R_N_slice"]),
+                      ("dp_split_pad_on_best_of_6", ladder["dp_split_pad_on_best_of_6"]["measured"]["mean_tflops"],
+                       ladder["dp_split_pad_on_best_of_6"]["measured"]["R_N_slice"]))}
     # ---- e2e: host buffers through the public API (H2D, plan GEMM, D2H per cell)
     out["e2e"] = e2e(rg, ctx, plan_smooth, a_bits, b_bits, dev, count)
     # ---- CPU oracle baseline on this host

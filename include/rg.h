@@ -197,6 +197,25 @@ int rg_plan_load(const char* path, const rg_ctx* ctx, rg_plan** out);
 int rg_surface_stats(const rg_grid* grid, const int64_t* t_ns, double* tflops_out,
                      double rough_out[5], double* mean_out);
 
+/* ---- first-principles landscapes (Sec. 9.1, 9.2) and kernel grading (Sec. 10; host) ----
+ * out[cell] = achieved TFLOP/s of the analytic landscape on `grid`:
+ *   RG_LANDSCAPE_IDEAL:   P * min(1, W / C), W = ceil(M/BM) ceil(N/BN) for tiles[0]
+ *                         (the compute ceiling with its partial-wave ramp, Sec. 9.1);
+ *   RG_LANDSCAPE_OPTIMAL: 2MNK / min over the n_tiles tiles of max(t_compute, t_memory),
+ *                         t_compute = 2MNK / (P * eta_wave), eta_wave = W / (ceil(W/C) C),
+ *                         t_memory = 2MK/(BW eta_A) + 2KN/(BW eta_B) + 4MN/(BW eta_D)  (Sec. 9.2).
+ * P = p_tflops (TFLOP/s), C = c_units (SMs, or SM pairs for 2-CTA tiles), BW = bw_gbs (GB/s),
+ * tiles = n_tiles (BM, BN) pairs.  channels > 0 selects the paper's interleaved-channel model
+ * for eta (channels, interleave bytes); channels = 0 sets every eta to 1 (HBM, no disclosed hash). */
+#define RG_LANDSCAPE_IDEAL 0
+#define RG_LANDSCAPE_OPTIMAL 1
+int rg_landscape(const rg_grid* grid, int32_t mode, double p_tflops, int32_t c_units, double bw_gbs,
+                 int32_t n_tiles, const int32_t* tiles, int32_t channels, int32_t interleave, double* out);
+/* Kernel Optimality Level (Sec. 10.2-10.3, Table 19): tau = mean_a / mean_o, rho = r_a / r_o;
+ * T band 0..3 at tau 0.50 / 0.75 / 0.95; S band 3 for rho <= 1.25, 2 up to 2, 1 up to 3, else 0;
+ * level = min(T, S).  out = {tau, rho}, bands = {T, S, L}. */
+int rg_kol(double mean_a, double mean_o, double r_a, double r_o, double out[2], int32_t bands[3]);
+
 /* ---- sweep (Sec. 3, Sec. 5.4) ----
  * Times every (variant, cell) pair: for each, `warmup` untimed launches, a
  * short device spin, then `reps` launches between two CUDA events;

@@ -2,6 +2,7 @@
 // Sec. 8.6 / Table 17 slice and 3D conventions) and the library's error
 // plumbing.  Compiled without floating-point contraction so every operation
 // is one IEEE double operation in the stated order.
+#include <algorithm>
 #include <cmath>
 #include <string>
 #include <vector>
@@ -161,5 +162,88 @@ extern "C" int rg_surface_stats(const rg_grid* grid, const int64_t* t_ns, double
     rough_out[3] = (rM + rN + rK) / 3.0;
     rough_out[4] = nn > 1 ? ss.value() / ps : 0.0;
   }
+  return RG_OK;
+}
+
+// ---------------------------------------------------------------- first-principles landscapes
+namespace {
+int64_t gcd64(int64_t a, int64_t b) {
+  while (b) {
+    const int64_t t = a % b;
+    a = b;
+    b = t;
+  }
+  return a;
+}
+int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// Channel utilisation of one tensor under the interleave model of Sec. 9.2.
+double eta_channel(int64_t L, int64_t e, int64_t channels, int64_t interleave) {
+  const int64_t w = std::min(channels, e);
+  const int64_t s = ((L * e) / interleave) % channels;
+  const int64_t g = gcd64(s, channels);
+  const double reach = static_cast<double>(w * channels) / static_cast<double>(g);
+  return std::min(static_cast<double>(channels), reach) / static_cast<double>(channels);
+}
+}  // namespace
+
+extern "C" int rg_landscape(const rg_grid* grid, int32_t mode, double p_tflops, int32_t c_units, double bw_gbs,
+                            int32_t n_tiles, const int32_t* tiles, int32_t channels, int32_t interleave,
+                            double* out) {
+  rg::clear_error();
+  if (!grid || !tiles || !out || n_tiles <= 0 || c_units <= 0 || !(p_tflops > 0.0))
+    return rg::fail(RG_ERR_INVALID, "rg_landscape: bad argument");
+  if (!rg::grid_valid(*grid)) return rg::fail(RG_ERR_INVALID, "rg_landscape: invalid grid");
+  if (mode != RG_LANDSCAPE_IDEAL && mode != RG_LANDSCAPE_OPTIMAL) return rg::fail(RG_ERR_INVALID, "rg_landscape: mode");
+  if (mode == RG_LANDSCAPE_OPTIMAL && !(bw_gbs > 0.0)) return rg::fail(RG_ERR_INVALID, "rg_landscape: bandwidth");
+  if (channels < 0 || (channels > 0 && interleave <= 0)) return rg::fail(RG_ERR_INVALID, "rg_landscape: channels");
+  for (int t = 0; t < n_tiles; ++t)
+    if (tiles[2 * t] <= 0 || tiles[2 * t + 1] <= 0) return rg::fail(RG_ERR_INVALID, "rg_landscape: tile");
+  const int64_t nm = grid->m.count, nn = grid->n.count, nk = grid->k.count;
+  const double C = static_cast<double>(c_units);
+  for (int64_t a = 0; a < nm; ++a)
+    for (int64_t b = 0; b < nn; ++b)
+      for (int64_t c = 0; c < nk; ++c) {
+        const int64_t Mi = rg::axis_value(grid->m, a), Ni = rg::axis_value(grid->n, b), Ki = rg::axis_value(grid->k, c);
+        const double M = static_cast<double>(Mi), N = static_cast<double>(Ni), K = static_cast<double>(Ki);
+        double v;
+        if (mode == RG_LANDSCAPE_IDEAL) {
+          const int64_t W = ceil_div(Mi, tiles[0]) * ceil_div(Ni, tiles[1]);
+          v = p_tflops * std::min(1.0, static_cast<double>(W) / C);
+        } else {
+          const double fl = 2.0 * M * N * K;
+          double eA = 1.0, eB = 1.0, eD = 1.0;
+          if (channels > 0) {
+            eA = eta_channel(Ki, 2, channels, interleave);
+            eB = eta_channel(Ni, 2, channels, interleave);
+            eD = eta_channel(Ni, 4, channels, interleave);
+          }
+          const double bw = bw_gbs * 1e9;
+          const double t_mem = 2.0 * M * K / (bw * eA) + 2.0 * K * N / (bw * eB) + 4.0 * M * N / (bw * eD);
+          double best = INFINITY;
+          for (int t = 0; t < n_tiles; ++t) {
+            const int64_t W = ceil_div(Mi, tiles[2 * t]) * ceil_div(Ni, tiles[2 * t + 1]);
+            const double eta = static_cast<double>(W) / (static_cast<double>(ceil_div(W, c_units)) * C);
+            const double t_comp = fl / (p_tflops * 1e12 * eta);
+            best = std::min(best, std::max(t_comp, t_mem));
+          }
+          v = fl / best / 1e12;
+        }
+        out[(a * nn + b) * nk + c] = v;
+      }
+  return RG_OK;
+}
+
+extern "C" int rg_kol(double mean_a, double mean_o, double r_a, double r_o, double out[2], int32_t bands[3]) {
+  if (!out || !bands || !(mean_o > 0.0) || !(r_o > 0.0)) return rg::fail(RG_ERR_INVALID, "rg_kol: bad argument");
+  const double tau = mean_a / mean_o;
+  const double rho = r_a / r_o;
+  const int32_t T = tau < 0.50 ? 0 : tau < 0.75 ? 1 : tau < 0.95 ? 2 : 3;
+  const int32_t S = rho > 3.0 ? 0 : rho > 2.0 ? 1 : rho > 1.25 ? 2 : 3;
+  out[0] = tau;
+  out[1] = rho;
+  bands[0] = T;
+  bands[1] = S;
+  bands[2] = std::min(T, S);
   return RG_OK;
 }

@@ -95,6 +95,8 @@ _sigs = {
     "rg_plan_build_ex": (C.c_int, [C.POINTER(rg_grid), _P, _I32, _P, _I32, C.POINTER(_P)]),
     "rg_launch_count": (C.c_int, [_P, C.POINTER(_I64)]),
     "rg_set_test_stall": (C.c_int, [_P, _I32]),
+    "rg_landscape": (C.c_int, [C.POINTER(rg_grid), _I32, C.c_double, _I32, C.c_double, _I32, _P, _I32, _I32, _P]),
+    "rg_kol": (C.c_int, [C.c_double, C.c_double, C.c_double, C.c_double, _P, _P]),
     "rg_gemm_noalloc": (C.c_int, [_I64, _I64, _I64, _P, _I64, _P, _I64, _P, _I64, _I32, _I32, _P]),
     "rg_plan_free": (None, [_P]),
     "rg_plan_grid": (C.c_int, [_P, C.POINTER(rg_grid)]),
@@ -330,6 +332,27 @@ def rg_sweep(ctx, grid: rg_grid, variant_ids, A, B, Cp, opts: rg_sweep_opts | No
     _check(_lib.rg_sweep(ctx, C.byref(grid), len(vids), vids.ctypes.data, plan, _ptr(A), _ptr(B), _ptr(Cp),
                          C.byref(o), out.ctypes.data, _stream(stream)), "rg_sweep")
     return out
+
+
+RG_LANDSCAPE_IDEAL = 0
+RG_LANDSCAPE_OPTIMAL = 1
+
+
+def rg_landscape(grid: rg_grid, mode: int, p_tflops: float, c_units: int, bw_gbs: float, tiles,
+                 channels: int = 0, interleave: int = 256) -> np.ndarray:
+    """First-principles TFLOP/s surface [cells] (RG_LANDSCAPE_IDEAL or RG_LANDSCAPE_OPTIMAL)."""
+    t = np.ascontiguousarray(np.asarray(tiles, dtype=np.int32).reshape(-1, 2))
+    out = np.zeros(grid_cells(grid), np.float64)
+    _check(_lib.rg_landscape(C.byref(grid), mode, p_tflops, c_units, bw_gbs, len(t), t.ctypes.data, channels,
+                             interleave, out.ctypes.data), "rg_landscape")
+    return out
+
+
+def rg_kol(mean_a: float, mean_o: float, r_a: float, r_o: float) -> dict:
+    o = np.zeros(2, np.float64)
+    b = np.zeros(3, np.int32)
+    _check(_lib.rg_kol(mean_a, mean_o, r_a, r_o, o.ctypes.data, b.ctypes.data), "rg_kol")
+    return {"tau": float(o[0]), "rho": float(o[1]), "T": int(b[0]), "S": int(b[1]), "L": int(b[2])}
 
 
 RG_NOALLOC_PARTIAL_BYTES = 16 << 20

@@ -188,3 +188,23 @@ def test_plan_build_rejects_bad_input(rg):
     g2 = rg.make_grid((256, 128, 2))
     with pytest.raises(rg.RGError):
         rg.rg_plan_build(g2, np.ones((1, 8), np.int64), [0])          # start != step
+
+
+def test_landscapes_match_oracle_bit_exact(rg):
+    from oracle import landscape as ol
+    grid = ((128, 128, 32), (128, 128, 32), (128, 128, 4))
+    g = rg.make_grid(*grid)
+    ide = rg.rg_landscape(g, rg.RG_LANDSCAPE_IDEAL, 108.2, 20, 0.0, [(256, 256)])
+    assert np.array_equal(ide.reshape(32, 32, 4), ol.ideal_surface(grid, 108.2, 20, (256, 256)))
+    tiles = [(256, 256), (128, 128), (64, 64)]
+    opt = rg.rg_landscape(g, rg.RG_LANDSCAPE_OPTIMAL, 108.2, 20, 451.0, tiles, channels=6, interleave=256)
+    assert np.array_equal(opt.reshape(32, 32, 4), ol.optimal_surface(grid, 108.2, 20, tiles, 451.0, channels=6))
+    gb = [(128, 64), (128, 128), (128, 256), (256, 64), (256, 128), (256, 256)]
+    opt2 = rg.rg_landscape(g, rg.RG_LANDSCAPE_OPTIMAL, 1900.7, 152, 6663.9, gb)
+    assert np.array_equal(opt2.reshape(32, 32, 4), ol.optimal_surface(grid, 1900.7, 152, gb, 6663.9))
+
+
+def test_kol_matches_oracle(rg):
+    from oracle import landscape as ol
+    for args in ((58.7, 96.7, 16.8, 2.23), (76.3, 96.7, 5.0, 2.8), (96.0, 96.7, 2.0, 2.0), (10.0, 96.7, 1.0, 2.0)):
+        assert rg.rg_kol(*args) == ol.kol(*args)
