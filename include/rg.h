@@ -197,6 +197,21 @@ int rg_plan_load(const char* path, const rg_ctx* ctx, rg_plan** out);
 int rg_surface_stats(const rg_grid* grid, const int64_t* t_ns, double* tflops_out,
                      double rough_out[5], double* mean_out);
 
+/* ---- FP8 e4m3 with FP32 scales per 128 x 128 block (precision variant of the GEMM) ----
+ * rg_fp8_quantize: X (rows x cols FP32, ldx) -> Q (e4m3 bytes, ldq) and scales
+ * [ceil(rows/128)][ceil(cols/128)] (row-major, FP32): per block amax, s = amax / 448
+ * (IEEE division; s = 1 for an all-zero block), Q = e4m3(x / s) rounded to nearest
+ * even with saturation to +-448.
+ * rg_gemm_fp8: C (M x N FP32, ldc) = sum over 128-deep K blocks kb of
+ * sA[i/128][kb] * sB[kb][j/128] * (qA * qB restricted to kb), FP32 accumulation;
+ * qA M x K e4m3 (lda), sA [ceil(M/128)][ceil(K/128)], qB K x N e4m3 (ldb),
+ * sB [ceil(K/128)][ceil(N/128)], as produced by rg_fp8_quantize.  qA, qB, C 16-byte
+ * aligned; lda, ldb multiples of 16; ldc a multiple of 4.  Device pointers, stream-ordered. */
+int rg_fp8_quantize(rg_ctx* ctx, const float* X, int64_t rows, int64_t cols, int64_t ldx, uint8_t* Q,
+                    int64_t ldq, float* scales, void* stream);
+int rg_gemm_fp8(rg_ctx* ctx, int64_t M, int64_t N, int64_t K, const uint8_t* qA, int64_t lda, const float* sA,
+                const uint8_t* qB, int64_t ldb, const float* sB, float* C, int64_t ldc, void* stream);
+
 /* ---- first-principles landscapes (Sec. 9.1, 9.2) and kernel grading (Sec. 10; host) ----
  * out[cell] = achieved TFLOP/s of the analytic landscape on `grid`:
  *   RG_LANDSCAPE_IDEAL:   P * min(1, W / C), W = ceil(M/BM) ceil(N/BN) for tiles[0]

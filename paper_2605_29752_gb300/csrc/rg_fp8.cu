@@ -1,0 +1,369 @@
+// FP8 e4m3 GEMM with FP32 scales per 128 x 128 block, FP32 accumulation and
+// output, and the block quantiser that produces its operands.  (The paper
+// measures BF16 only; this is the precision variant of the same NN GEMM.)
+//
+//   A ~ qA (M x K e4m3, row-major) with sA[M/128][K/128],
+//   B ~ qB (K x N e4m3, row-major) with sB[K/128][N/128],
+//   C[i][j] = sum_kb sA[i/128][kb] * sB[kb][j/128] * sum_{k in kb} qA[i][k] qB[k][j].
+//
+// Kernel (one CTA per SM, persistent over 128 x 128 output tiles):
+//   warp 0     TMA producer: A block 128 x 128 bytes (K-major) and B block 128 K-rows
+//              x 128 bytes (N-major), 128-byte swizzle, ring of stages.
+//   warp 1     one thread issues tcgen05.mma kind::f8f6f4 (M = N = 128, K = 32) into
+//              one of four TMEM buffers, a fresh accumulator per 128-deep K block.
+//   warps 2-5  promotion and epilogue: per K block, tcgen05.ld the block product,
+//              multiply by sA * sB (one scalar per tile and K block, since tiles and
+//              scale blocks coincide) and add into FP32 registers (one row per thread);
+//              after the last block, 128B-swizzled staging and TMA store.
+// Every mbarrier wait is bounded; on expiry the kernel records an error code,
+// lets its in-flight copies land, releases TMEM and returns.
+#include <cuda.h>
+#include <cuda_fp8.h>
+#include <cuda_runtime.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <string>
+
+#include "ptx.cuh"
+#include "rg_internal.h"
+
+namespace rg {
+
+namespace fp8 {
+
+constexpr int kThreads = 192;
+constexpr int BM = 128, BN = 128, BK = 128;  // BK: one 128-byte swizzle row of e4m3 = one scale block
+constexpr int STAGES = 6;
+constexpr int A_BYTES = BM * BK;
+constexpr int B_BYTES = BK * BN;
+constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+constexpr int NACC = 4;                       // TMEM buffers of 128 columns
+constexpr int TMEM_COLS = 512;
+constexpr int STAGING_PER_WARP = 2 * 4096;
+constexpr int STAGING_OFF = STAGES * STAGE_BYTES;
+constexpr int BAR_OFF = STAGING_OFF + 4 * STAGING_PER_WARP;
+constexpr int SMEM_BYTES = 1024 + BAR_OFF + 256;
+constexpr uint32_t IDESC = instr_desc(0, 0, 0, 1, 128, BN);  // E4M3 x E4M3, A K-major, B MN-major
+constexpr long long kDrainCycles = 1LL << 30;
+constexpr uint32_t FULL = 0xffffffffu;
+static_assert(SMEM_BYTES <= 232448, "shared memory budget");
+
+struct Args {
+  int32_t M, N;
+  int32_t tiles_m, tiles_n;
+  int32_t kblocks;
+  int32_t sa_ld, sb_ld;  // leading dimensions of the scale arrays (blocks)
+  const float* sA;
+  const float* sB;
+  int32_t* err;
+  long long timeout;
+};
+
+__device__ __forceinline__ void st_shared_v4(uint32_t addr, float a, float b, float c, float d) {
+  asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "f"(a), "f"(b), "f"(c), "f"(d) : "memory");
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+    gemm_fp8_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                    const __grid_constant__ CUtensorMap tmC, const Args args) {
+  extern __shared__ uint8_t smem_raw[];
+  const uint32_t raw_s = smem_u32(smem_raw);
+  uint8_t* smem = smem_raw + ((1024u - (raw_s & 1023u)) & 1023u);
+  const uint32_t sbase = smem_u32(smem);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + BAR_OFF);
+  const uint32_t bar0 = smem_u32(bars);
+  auto full_bar = [&](int i) { return bar0 + 8u * i; };
+  auto empty_bar = [&](int i) { return bar0 + 8u * (STAGES + i); };
+  auto tfull_bar = [&](int b) { return bar0 + 8u * (2 * STAGES + b); };
+  auto tempty_bar = [&](int b) { return bar0 + 8u * (2 * STAGES + NACC + b); };
+  const uint32_t drain_bar = bar0 + 8u * (2 * STAGES + 2 * NACC);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 2 * NACC + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  int never = 0;
+  volatile int* no_abort = &never;
+
+  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+  const int total = args.tiles_m * args.tiles_n;
+
+  if (threadIdx.x == 0) {
+    prefetch_tmap(&tmA);
+    prefetch_tmap(&tmB);
+    prefetch_tmap(&tmC);
+    for (int i = 0; i < STAGES; ++i) {
+      mbar_init(full_bar(i), 1);
+      mbar_init(empty_bar(i), 1);
+    }
+    for (int b = 0; b < NACC; ++b) {
+      mbar_init(tfull_bar(b), 1);
+      mbar_init(tempty_bar(b), 4);
+    }
+    mbar_init(drain_bar, 1);
+    *abort_flag = 0;
+    fence_mbar_init();
+  }
+  if (warp == 1) {
+    tmem_alloc(smem_u32(tmem_slot), TMEM_COLS);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+  grid_dependency_wait();
+  grid_launch_dependents();
+
+  if (warp == 0) {
+    if (lane == 0) {
+      int stage = 0;
+      uint32_t ph = 0, issued_mask = 0, issued_ph = 0;
+      bool ok = true;
+      for (int u = blockIdx.x; ok && u < total; u += gridDim.x) {
+        const int tm = u / args.tiles_n, tn = u % args.tiles_n;
+        for (int kb = 0; kb < args.kblocks; ++kb) {
+          if (!mbar_wait(empty_bar(stage), ph ^ 1u, args.timeout, abort_flag)) {
+            ok = false;
+            break;
+          }
+          const uint32_t sa = sbase + stage * STAGE_BYTES;
+          mbar_arrive_expect_tx(full_bar(stage), STAGE_BYTES);
+          tma_load_2d(sa, &tmA, full_bar(stage), kb * BK, tm * BM);
+          tma_load_2d(sa + A_BYTES, &tmB, full_bar(stage), tn * BN, kb * BK);
+          issued_mask |= 1u << stage;
+          issued_ph = (issued_ph & ~(1u << stage)) | (ph << stage);
+          if (++stage == STAGES) {
+            stage = 0;
+            ph ^= 1u;
+          }
+        }
+      }
+      if (!ok) {
+        atomicExch(args.err, 1);
+        *abort_flag = 1;
+      }
+      for (int i = 0; i < STAGES; ++i)
+        if (issued_mask & (1u << i)) mbar_wait(full_bar(i), (issued_ph >> i) & 1u, kDrainCycles, no_abort);
+    }
+  } else if (warp == 1) {
+    int stage = 0, acc = 0;
+    uint32_t ph = 0, aph = 0;
+    bool ok = true;
+    for (int u = blockIdx.x; ok && u < total; u += gridDim.x) {
+      for (int kb = 0; kb < args.kblocks; ++kb) {
+        ok = __all_sync(FULL, mbar_wait(tempty_bar(acc), aph ^ 1u, args.timeout, abort_flag));
+        if (!ok) break;
+        ok = __all_sync(FULL, mbar_wait(full_bar(stage), ph, args.timeout, abort_flag));
+        if (!ok) break;
+        tc_fence_after();
+        if (lane == 0) {
+          const uint32_t sa = sbase + stage * STAGE_BYTES;
+          const uint32_t sb = sa + A_BYTES;
+          const uint32_t d = tmem_base + static_cast<uint32_t>(acc * BN);
+#pragma unroll
+          for (int k = 0; k < BK / 32; ++k) {
+            const uint64_t adesc = smem_desc_sw128(sa + k * 32, 16, 1024);
+            const uint64_t bdesc = smem_desc_sw128(sb + k * (32 * 128), BK * 128, 1024);
+            mma_f8(d, adesc, bdesc, IDESC, k > 0 ? 1u : 0u);
+          }
+          mma_commit(empty_bar(stage));
+          mma_commit(tfull_bar(acc));
+        }
+        __syncwarp();
+        if (++stage == STAGES) {
+          stage = 0;
+          ph ^= 1u;
+        }
+        if (++acc == NACC) {
+          acc = 0;
+          aph ^= 1u;
+        }
+      }
+    }
+    if (!ok) {
+      if (lane == 0) {
+        atomicExch(args.err, 2);
+        *abort_flag = 1;
+        mma_commit(drain_bar);
+      }
+      __syncwarp();
+      mbar_wait(drain_bar, 0, kDrainCycles, no_abort);
+    }
+  } else {
+    const int q = warp & 3;
+    const uint32_t stg0 = sbase + STAGING_OFF + (warp - 2) * STAGING_PER_WARP;
+    int acc = 0, sbuf = 0;
+    uint32_t aph = 0;
+    bool ok = true;
+    for (int u = blockIdx.x; ok && u < total; u += gridDim.x) {
+      const int tm = u / args.tiles_n, tn = u % args.tiles_n;
+      float r[BN];
+#pragma unroll
+      for (int i = 0; i < BN; ++i) r[i] = 0.f;
+      for (int kb = 0; kb < args.kblocks; ++kb) {
+        const float s = args.sA[static_cast<size_t>(tm) * args.sa_ld + kb] * args.sB[static_cast<size_t>(kb) * args.sb_ld + tn];
+        ok = __all_sync(FULL, mbar_wait(tfull_bar(acc), aph, args.timeout, abort_flag));
+        if (!ok) break;
+        tc_fence_after();
+        const uint32_t t = tmem_base + (static_cast<uint32_t>(q * 32) << 16) + static_cast<uint32_t>(acc * BN);
+#pragma unroll
+        for (int c = 0; c < BN / 32; ++c) {
+          uint32_t p[32];
+          tmem_ld_32x32b_x32(t + c * 32, p);
+          tmem_ld_wait();
+#pragma unroll
+          for (int i = 0; i < 32; ++i) r[c * 32 + i] = fmaf(s, __uint_as_float(p[i]), r[c * 32 + i]);
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(tempty_bar(acc));
+        if (++acc == NACC) {
+          acc = 0;
+          aph ^= 1u;
+        }
+      }
+      if (!ok) break;
+      const int row0 = tm * BM + q * 32;
+#pragma unroll
+      for (int c = 0; c < BN / 32; ++c) {
+        const int col0 = tn * BN + c * 32;
+        if (row0 >= args.M || col0 >= args.N) continue;
+        if (lane == 0) bulk_wait_read<1>();
+        __syncwarp();
+        const uint32_t buf = stg0 + sbuf * 4096;
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+          st_shared_v4(buf + lane * 128 + ((j ^ (lane & 7)) << 4), r[c * 32 + 4 * j], r[c * 32 + 4 * j + 1],
+                       r[c * 32 + 4 * j + 2], r[c * 32 + 4 * j + 3]);
+        fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0) {
+          tma_store_2d(&tmC, buf, col0, row0);
+          bulk_commit();
+        }
+        sbuf ^= 1;
+      }
+    }
+    if (!ok && lane == 0) {
+      atomicExch(args.err, 3);
+      *abort_flag = 1;
+    }
+    if (lane == 0) bulk_wait<0>();
+    __syncwarp();
+  }
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem_base, TMEM_COLS);
+  }
+}
+
+// One CTA per 128 x 128 block: amax, scale = amax / 448 (1 for an all-zero
+// block), codes = e4m3(x / scale) rounded to nearest even with saturation.
+__global__ void __launch_bounds__(256) quantize_kernel(const float* __restrict__ X, int64_t rows, int64_t cols,
+                                                       int64_t ldx, uint8_t* __restrict__ Q, int64_t ldq,
+                                                       float* __restrict__ scales, int64_t s_ld) {
+  __shared__ float red[8];
+  const int64_t r0 = static_cast<int64_t>(blockIdx.y) * 128, c0 = static_cast<int64_t>(blockIdx.x) * 128;
+  const int tid = threadIdx.x;
+  float amax = 0.f;
+  for (int i = tid; i < 128 * 128; i += 256) {
+    const int64_t r = r0 + i / 128, c = c0 + i % 128;
+    if (r < rows && c < cols) amax = fmaxf(amax, fabsf(X[r * ldx + c]));
+  }
+  for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+  if ((tid & 31) == 0) red[tid >> 5] = amax;
+  __syncthreads();
+  float m = red[0];
+  for (int w = 1; w < 8; ++w) m = fmaxf(m, red[w]);
+  const float s = m > 0.f ? __fdiv_rn(m, 448.0f) : 1.0f;
+  if (tid == 0) scales[static_cast<int64_t>(blockIdx.y) * s_ld + blockIdx.x] = s;
+  for (int i = tid; i < 128 * 128; i += 256) {
+    const int64_t r = r0 + i / 128, c = c0 + i % 128;
+    if (r < rows && c < cols) {
+      const float v = __fdiv_rn(X[r * ldx + c], s);
+      Q[r * ldq + c] = static_cast<uint8_t>(__nv_cvt_float_to_fp8(v, __NV_SATFINITE, __NV_E4M3));
+    }
+  }
+}
+
+}  // namespace fp8
+
+int fp8_make_map(CUtensorMap* m, CUtensorMapDataType dt, const void* base, uint64_t inner, uint64_t outer,
+                 uint64_t row_bytes, uint32_t box_inner, uint32_t box_outer);
+cudaError_t fp8_launch_pdl(const void* fn, dim3 grid, int threads, int smem, cudaStream_t st, void** params);
+int ctx_fp8_info(rg_ctx* ctx, int32_t** err, long long* timeout, int* sms);
+
+}  // namespace rg
+
+extern "C" int rg_fp8_quantize(rg_ctx* ctx, const float* X, int64_t rows, int64_t cols, int64_t ldx, uint8_t* Q,
+                               int64_t ldq, float* scales, void* stream) {
+  rg::clear_error();
+  if (!ctx) return rg::fail(RG_ERR_INVALID, "rg_fp8_quantize: null context");
+  if (rows < 0 || cols < 0 || ldx < cols || ldq < cols) return rg::fail(RG_ERR_INVALID, "rg_fp8_quantize: sizes");
+  if (rows == 0 || cols == 0) return RG_OK;
+  if (!X || !Q || !scales) return rg::fail(RG_ERR_INVALID, "rg_fp8_quantize: null pointer");
+  const int64_t br = (rows + 127) / 128, bc = (cols + 127) / 128;
+  if (br > 65535 || bc > (1LL << 31) - 1) return rg::fail(RG_ERR_SHAPE, "rg_fp8_quantize: too many blocks");
+  rg::fp8::quantize_kernel<<<dim3(static_cast<unsigned>(bc), static_cast<unsigned>(br)), 256, 0,
+                             static_cast<cudaStream_t>(stream)>>>(X, rows, cols, ldx, Q, ldq, scales, bc);
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? RG_OK : rg::fail(RG_ERR_CUDA, std::string("rg_fp8_quantize: ") + cudaGetErrorString(e));
+}
+
+extern "C" int rg_gemm_fp8(rg_ctx* ctx, int64_t M, int64_t N, int64_t K, const uint8_t* qA, int64_t lda,
+                           const float* sA, const uint8_t* qB, int64_t ldb, const float* sB, float* C, int64_t ldc,
+                           void* stream) {
+  rg::clear_error();
+  using namespace rg::fp8;
+  if (!ctx) return rg::fail(RG_ERR_INVALID, "rg_gemm_fp8: null context");
+  if (M < 0 || N < 0 || K < 0) return rg::fail(RG_ERR_INVALID, "rg_gemm_fp8: negative size");
+  if (M == 0 || N == 0) return RG_OK;
+  if (K == 0) {
+    const cudaError_t e = cudaMemset2DAsync(C, ldc * 4, 0, N * 4, M, static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? RG_OK : rg::fail(RG_ERR_CUDA, "rg_gemm_fp8: memset");
+  }
+  if (!qA || !qB || !sA || !sB || !C) return rg::fail(RG_ERR_INVALID, "rg_gemm_fp8: null pointer");
+  if (lda < K || ldb < N || ldc < N) return rg::fail(RG_ERR_INVALID, "rg_gemm_fp8: leading dimensions");
+  if ((reinterpret_cast<uintptr_t>(qA) & 15) || (reinterpret_cast<uintptr_t>(qB) & 15) ||
+      (reinterpret_cast<uintptr_t>(C) & 15) || (lda % 16) || (ldb % 16) || (ldc % 4))
+    return rg::fail(RG_ERR_ALIGN, "rg_gemm_fp8: 16-byte aligned operands, lda and ldb multiples of 16, ldc of 4");
+  if (M > (1 << 30) || N > (1 << 30) || K > (1 << 30)) return rg::fail(RG_ERR_SHAPE, "rg_gemm_fp8: size beyond 2^30");
+  int32_t* err = nullptr;
+  long long timeout = 0;
+  int sms = 0;
+  int rc = rg::ctx_fp8_info(ctx, &err, &timeout, &sms);
+  if (rc != RG_OK) return rc;
+  CUtensorMap a, b, c;
+  rc = rg::fp8_make_map(&a, CU_TENSOR_MAP_DATA_TYPE_UINT8, qA, K, M, lda, BK, BM);
+  if (rc == RG_OK) rc = rg::fp8_make_map(&b, CU_TENSOR_MAP_DATA_TYPE_UINT8, qB, N, K, ldb, BN, BK);
+  if (rc == RG_OK) rc = rg::fp8_make_map(&c, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, C, N, M, ldc * 4, 32, 32);
+  if (rc != RG_OK) return rc;
+  Args args{};
+  args.M = static_cast<int32_t>(M);
+  args.N = static_cast<int32_t>(N);
+  args.tiles_m = static_cast<int32_t>((M + BM - 1) / BM);
+  args.tiles_n = static_cast<int32_t>((N + BN - 1) / BN);
+  args.kblocks = static_cast<int32_t>((K + BK - 1) / BK);
+  args.sa_ld = args.kblocks;
+  args.sb_ld = args.tiles_n;
+  args.sA = sA;
+  args.sB = sB;
+  args.err = err;
+  args.timeout = timeout;
+  static bool attr_done[64] = {false};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev >= 0 && dev < 64 && !attr_done[dev]) {
+    const cudaError_t e = cudaFuncSetAttribute(reinterpret_cast<const void*>(gemm_fp8_kernel),
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    if (e != cudaSuccess) return rg::fail(RG_ERR_CUDA, "rg_gemm_fp8: shared-memory attribute");
+    attr_done[dev] = true;
+  }
+  const int64_t units = static_cast<int64_t>(args.tiles_m) * args.tiles_n;
+  dim3 grid(static_cast<unsigned>(std::min<int64_t>(units, sms)));
+  void* params[4] = {&a, &b, &c, &args};
+  const cudaError_t e = rg::fp8_launch_pdl(reinterpret_cast<const void*>(gemm_fp8_kernel), grid, kThreads, SMEM_BYTES,
+                                           static_cast<cudaStream_t>(stream), params);
+  return e == cudaSuccess ? RG_OK : rg::fail(RG_ERR_CUDA, std::string("rg_gemm_fp8: launch: ") + cudaGetErrorString(e));
+}

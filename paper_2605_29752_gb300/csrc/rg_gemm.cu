@@ -625,6 +625,45 @@ static int plan_launches(rg_ctx* ctx, const rg_plan* plan, int64_t M, int64_t N,
 
 }  // namespace rg
 
+// ------------------------------------------------------------------ shared with the FP8 and grouped kernels
+namespace rg {
+
+int fp8_make_map(CUtensorMap* m, CUtensorMapDataType dt, const void* base, uint64_t inner, uint64_t outer,
+                 uint64_t row_bytes, uint32_t box_inner, uint32_t box_outer) {
+  const int rc = get_encode();
+  if (rc != RG_OK) return rc;
+  return make_map(m, dt, base, inner, outer, row_bytes, box_inner, box_outer);
+}
+
+// Launch with programmatic dependent launch allowed (the kernel waits on
+// griddepcontrol before touching global memory).
+cudaError_t fp8_launch_pdl(const void* fn, dim3 grid, int threads, int smem, cudaStream_t st, void** params) {
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = dim3(threads);
+  cfg.dynamicSmemBytes = static_cast<size_t>(smem);
+  cfg.stream = st;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelExC(&cfg, fn, params);
+}
+
+// The context's error word, wait budget and SM count for kernels of other
+// translation units; counts one launch.
+int ctx_fp8_info(rg_ctx* ctx, int32_t** err, long long* timeout, int* sms) {
+  if (!ctx) return fail(RG_ERR_INVALID, "null context");
+  *err = ctx->err;
+  *timeout = ctx->timeout;
+  *sms = ctx->sm_count;
+  ++ctx->launches;
+  return RG_OK;
+}
+
+}  // namespace rg
+
 // ------------------------------------------------------------------ C ABI
 
 extern "C" int rg_init(int device, int64_t workspace_bytes, rg_ctx** out) {

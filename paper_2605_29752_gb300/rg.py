@@ -95,6 +95,8 @@ _sigs = {
     "rg_plan_build_ex": (C.c_int, [C.POINTER(rg_grid), _P, _I32, _P, _I32, C.POINTER(_P)]),
     "rg_launch_count": (C.c_int, [_P, C.POINTER(_I64)]),
     "rg_set_test_stall": (C.c_int, [_P, _I32]),
+    "rg_fp8_quantize": (C.c_int, [_P, _P, _I64, _I64, _I64, _P, _I64, _P, _P]),
+    "rg_gemm_fp8": (C.c_int, [_P, _I64, _I64, _I64, _P, _I64, _P, _P, _I64, _P, _P, _I64, _P]),
     "rg_landscape": (C.c_int, [C.POINTER(rg_grid), _I32, C.c_double, _I32, C.c_double, _I32, _P, _I32, _I32, _P]),
     "rg_kol": (C.c_int, [C.c_double, C.c_double, C.c_double, C.c_double, _P, _P]),
     "rg_gemm_noalloc": (C.c_int, [_I64, _I64, _I64, _P, _I64, _P, _I64, _P, _I64, _I32, _I32, _P]),
@@ -332,6 +334,16 @@ def rg_sweep(ctx, grid: rg_grid, variant_ids, A, B, Cp, opts: rg_sweep_opts | No
     _check(_lib.rg_sweep(ctx, C.byref(grid), len(vids), vids.ctypes.data, plan, _ptr(A), _ptr(B), _ptr(Cp),
                          C.byref(o), out.ctypes.data, _stream(stream)), "rg_sweep")
     return out
+
+
+def rg_fp8_quantize(ctx, X, rows, cols, ldx, Q, ldq, scales, stream=None) -> None:
+    _check(_lib.rg_fp8_quantize(ctx, _ptr(X), rows, cols, ldx, _ptr(Q), ldq, _ptr(scales), _stream(stream)),
+           "rg_fp8_quantize")
+
+
+def rg_gemm_fp8(ctx, M, N, K, qA, lda, sA, qB, ldb, sB, Cp, ldc, stream=None) -> None:
+    _check(_lib.rg_gemm_fp8(ctx, M, N, K, _ptr(qA), lda, _ptr(sA), _ptr(qB), ldb, _ptr(sB), _ptr(Cp), ldc,
+                            _stream(stream)), "rg_gemm_fp8")
 
 
 RG_LANDSCAPE_IDEAL = 0
