@@ -197,6 +197,38 @@ int rg_plan_load(const char* path, const rg_ctx* ctx, rg_plan** out);
 int rg_surface_stats(const rg_grid* grid, const int64_t* t_ns, double* tflops_out,
                      double rough_out[5], double* mean_out);
 
+/* ---- grouped GEMM under CUDA graphs (many problems, one persistent launch) ----
+ * A group runs a list of independent NN GEMMs with one tile shape in one
+ * persistent launch over all SMs: the launch's work units are the
+ * concatenation of every problem's output tiles.  Each problem has its own
+ * sizes, operands, leading dimensions, beta and padded launch extents
+ * (pm, pn, pk as in rg_gemm; 0 = no padding); split-K is not used.  Problems of
+ * one call must not write overlapping parts of C unless ordered by beta-free
+ * semantics (their tiles run concurrently).
+ * rg_group_create allocates, per group, kGroupSlots = 4 slots of work lists
+ * (pinned host + device, for max_items problems each) and instantiates one CUDA
+ * graph per slot: [copy the host list to the device list, grouped kernel].
+ * rg_gemm_grouped fills the next slot (waiting first until that slot's replay
+ * from 4 calls ago has finished), then replays its graph on `stream`;
+ * the call returns without waiting for the GEMMs.  Operand conventions and
+ * alignment are those of rg_gemm; K == 0 problems are rejected. */
+typedef struct {
+  int64_t M, N, K;
+  const void* A;
+  int64_t lda;
+  const void* B;
+  int64_t ldb;
+  float* C;
+  int64_t ldc;
+  int64_t pm, pn, pk;
+  int32_t beta;
+  int32_t reserved;
+} rg_group_problem;
+typedef struct rg_group rg_group;
+int rg_group_create(rg_ctx* ctx, int32_t tile, int32_t max_items, rg_group** out);
+void rg_group_destroy(rg_group* group);
+int rg_gemm_grouped(rg_group* group, const rg_group_problem* problems, int32_t n, void* stream);
+
 /* ---- FP8 e4m3 with FP32 scales per 128 x 128 block (precision variant of the GEMM) ----
  * rg_fp8_quantize: X (rows x cols FP32, ldx) -> Q (e4m3 bytes, ldq) and scales
  * [ceil(rows/128)][ceil(cols/128)] (row-major, FP32): per block amax, s = amax / 448

@@ -31,6 +31,7 @@
 #include <cstring>
 #include <mutex>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "ptx.cuh"
@@ -124,10 +125,96 @@ __device__ __forceinline__ void store_block(const CUtensorMap* tmC, const float 
   sbuf ^= 1;
 }
 
-template <int BM, int BN, int STAGES>
-__global__ void __launch_bounds__(kThreads, 1)
-    gemm_bf16_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                     const __grid_constant__ CUtensorMap tmC, const GemmArgs args) {
+// One work unit: which output tile of which problem, which K blocks, and where
+// its operands and output live.
+struct Unit {
+  const CUtensorMap* a;
+  const CUtensorMap* b;
+  const CUtensorMap* c;
+  int tm, tn;     // tile coordinates in the problem
+  int s, splits;  // K split index and count
+  int kb0, kb1;   // K blocks [kb0, kb1) of this unit
+  int M, N;       // logical output extents of the problem
+  int beta;
+  int tile, ntiles;  // tile id / tile count of the problem (split-K workspace and tickets)
+};
+
+__device__ __forceinline__ Unit split_unit(const CUtensorMap* a, const CUtensorMap* b, const CUtensorMap* c, int u,
+                                           int tiles_m, int tiles_n, int splits, int kblocks, int M, int N, int beta) {
+  Unit x;
+  x.a = a;
+  x.b = b;
+  x.c = c;
+  x.tile = u / splits;
+  x.s = u % splits;
+  x.splits = splits;
+  x.tm = x.tile / tiles_n;
+  x.tn = x.tile % tiles_n;
+  x.kb0 = static_cast<int>(static_cast<long long>(x.s) * kblocks / splits);
+  x.kb1 = static_cast<int>(static_cast<long long>(x.s + 1) * kblocks / splits);
+  x.M = M;
+  x.N = N;
+  x.beta = beta;
+  x.ntiles = tiles_m * tiles_n;
+  return x;
+}
+
+// One problem whose tensor maps are kernel parameters (rg_gemm).
+struct SingleSched {
+  static constexpr bool kMapsInGlobal = false;
+  const CUtensorMap* a;
+  const CUtensorMap* b;
+  const CUtensorMap* c;
+  int tiles_m, tiles_n, splits, kblocks, M, N, beta;
+  __device__ __forceinline__ void prefetch() const {
+    prefetch_tmap(a);
+    prefetch_tmap(b);
+    prefetch_tmap(c);
+  }
+  __device__ __forceinline__ int total() const { return tiles_m * tiles_n * splits; }
+  __device__ __forceinline__ Unit unit(int u) const {
+    return split_unit(a, b, c, u, tiles_m, tiles_n, splits, kblocks, M, N, beta);
+  }
+};
+
+// Many problems in one launch (rg_gemm_grouped): a device-resident work list
+// whose header gives the item count and the total tile count; the units are the
+// concatenation of every item's tiles (item i owns units [tile_start, tile_start
+// + tiles_m * tiles_n)).  Each item carries its own tensor maps (in global
+// memory), launch extents and beta; no split-K.
+struct alignas(64) GroupItem {
+  CUtensorMap a, b, c;
+  int32_t M, N, beta, tiles_m;
+  int32_t tiles_n, kblocks, tile_start, reserved;
+};
+struct alignas(64) GroupHeader {
+  int32_t n_items;
+  int32_t total_tiles;
+  int32_t reserved[14];
+};
+
+struct GroupSched {
+  static constexpr bool kMapsInGlobal = true;
+  const GroupHeader* h;
+  const GroupItem* items;
+  int n_items, total_tiles;  // read after the grid dependency wait
+  __device__ __forceinline__ void prefetch() const {}
+  __device__ __forceinline__ int total() const { return total_tiles; }
+  __device__ __forceinline__ Unit unit(int u) const {
+    int lo = 0, hi = n_items - 1;  // last item whose tile_start <= u
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (items[mid].tile_start <= u) lo = mid; else hi = mid - 1;
+    }
+    const GroupItem& it = items[lo];
+    return split_unit(&it.a, &it.b, &it.c, u - it.tile_start, it.tiles_m, it.tiles_n, 1, it.kblocks, it.M, it.N,
+                      it.beta);
+  }
+};
+
+template <int BM, int BN, int STAGES, class Sched>
+__device__ __forceinline__ void gemm_body(Sched& sched, float* ws, int32_t* tickets, int32_t* err, long long timeout,
+                                          int stall) {
   using C = KCfg<BM, BN, STAGES>;
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw_s = smem_u32(smem_raw);
@@ -147,12 +234,9 @@ __global__ void __launch_bounds__(kThreads, 1)
 
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
-  const int total = args.tiles_m * args.tiles_n * args.splits;
 
   if (threadIdx.x == 0) {
-    prefetch_tmap(&tmA);
-    prefetch_tmap(&tmB);
-    prefetch_tmap(&tmC);
+    sched.prefetch();
     for (int i = 0; i < STAGES; ++i) {
       mbar_init(full_bar(i), 1);
       mbar_init(empty_bar(i), 1);
@@ -177,6 +261,11 @@ __global__ void __launch_bounds__(kThreads, 1)
   // touches global memory before that grid has completed.
   grid_dependency_wait();
   grid_launch_dependents();
+  if constexpr (std::is_same<Sched, GroupSched>::value) {
+    sched.n_items = sched.h->n_items;
+    sched.total_tiles = sched.h->total_tiles;
+  }
+  const int total = sched.total();
 
   if (warp == 0) {
     // ------------------------------------------------ TMA producer (one thread)
@@ -186,22 +275,23 @@ __global__ void __launch_bounds__(kThreads, 1)
       uint32_t issued_mask = 0, issued_ph = 0;
       bool ok = true;
       for (int u = blockIdx.x; ok && u < total; u += gridDim.x) {
-        const int tile = u / args.splits, s = u % args.splits;
-        const int tm = tile / args.tiles_n, tn = tile % args.tiles_n;
-        const int kb0 = static_cast<int>(static_cast<long long>(s) * args.kblocks / args.splits);
-        const int kb1 = static_cast<int>(static_cast<long long>(s + 1) * args.kblocks / args.splits);
-        for (int kb = kb0; kb < kb1; ++kb) {
-          if (!mbar_wait(empty_bar(stage), ph ^ 1u, args.timeout, abort_flag)) {
+        const Unit w = sched.unit(u);
+        if constexpr (Sched::kMapsInGlobal) {
+          tensormap_fence_acquire(w.a);
+          tensormap_fence_acquire(w.b);
+        }
+        for (int kb = w.kb0; kb < w.kb1; ++kb) {
+          if (!mbar_wait(empty_bar(stage), ph ^ 1u, timeout, abort_flag)) {
             ok = false;
             break;
           }
           const uint32_t sa = sbase + stage * C::STAGE_BYTES;
           const uint32_t sb = sa + C::A_BYTES;
           mbar_arrive_expect_tx(full_bar(stage), C::STAGE_BYTES);
-          tma_load_2d(sa, &tmA, full_bar(stage), kb * kBK, tm * BM);
+          tma_load_2d(sa, w.a, full_bar(stage), kb * kBK, w.tm * BM);
 #pragma unroll
           for (int j = 0; j < BN / 64; ++j)
-            tma_load_2d(sb + j * (kBK * 128), &tmB, full_bar(stage), tn * BN + j * 64, kb * kBK);
+            tma_load_2d(sb + j * (kBK * 128), w.b, full_bar(stage), w.tn * BN + j * 64, kb * kBK);
           issued_mask |= 1u << stage;
           issued_ph = (issued_ph & ~(1u << stage)) | (ph << stage);
           if (++stage == STAGES) {
@@ -211,7 +301,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
       }
       if (!ok) {
-        atomicExch(args.err, kErrProducer);
+        atomicExch(err, kErrProducer);
         *abort_flag = 1;
       }
       // no TMA write may still be landing when the CTA exits
@@ -223,17 +313,16 @@ __global__ void __launch_bounds__(kThreads, 1)
     int stage = 0, acc = 0;
     uint32_t ph = 0, aph = 0;
     bool ok = true;
-    if (args.stall) ok = __all_sync(FULL, mbar_wait(drain_bar, 0, args.timeout, abort_flag));
+    if (stall) ok = __all_sync(FULL, mbar_wait(drain_bar, 0, timeout, abort_flag));
     for (int u = blockIdx.x; ok && u < total; u += gridDim.x) {
-      const int s = u % args.splits;
-      const int kb0 = static_cast<int>(static_cast<long long>(s) * args.kblocks / args.splits);
-      const int kb1 = static_cast<int>(static_cast<long long>(s + 1) * args.kblocks / args.splits);
-      ok = __all_sync(FULL, mbar_wait(tempty_bar(acc), aph ^ 1u, args.timeout, abort_flag));
+      const Unit w = sched.unit(u);
+      const int kb0 = w.kb0, kb1 = w.kb1;
+      ok = __all_sync(FULL, mbar_wait(tempty_bar(acc), aph ^ 1u, timeout, abort_flag));
       if (!ok) break;
       tc_fence_after();
       const uint32_t d0 = tmem_base + static_cast<uint32_t>(acc * C::ACC_COLS);
       for (int kb = kb0; kb < kb1; ++kb) {
-        ok = __all_sync(FULL, mbar_wait(full_bar(stage), ph, args.timeout, abort_flag));
+        ok = __all_sync(FULL, mbar_wait(full_bar(stage), ph, timeout, abort_flag));
         if (!ok) break;
         tc_fence_after();
         if (lane == 0) {
@@ -266,7 +355,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     if (!ok) {
       if (lane == 0) {
-        atomicExch(args.err, kErrMma);
+        atomicExch(err, kErrMma);
         *abort_flag = 1;
         mma_commit(drain_bar);  // completes once every issued MMA has finished
       }
@@ -277,33 +366,33 @@ __global__ void __launch_bounds__(kThreads, 1)
     // ------------------------------------------------ epilogue (warps 2-5)
     const int q = warp & 3;  // TMEM lanes 32q..32q+31 are the ones this warp may read
     const uint32_t stg0 = sbase + C::STAGING_OFF + (warp - 2) * kStagingPerWarp;
-    const int ntiles = args.tiles_m * args.tiles_n;
     int acc = 0, sbuf = 0;
     uint32_t aph = 0;
     bool ok = true;
     for (int u = blockIdx.x; u < total; u += gridDim.x) {
-      const int tile = u / args.splits, s = u % args.splits;
-      const int tm = tile / args.tiles_n, tn = tile % args.tiles_n;
-      const int kb0 = static_cast<int>(static_cast<long long>(s) * args.kblocks / args.splits);
-      const int kb1 = static_cast<int>(static_cast<long long>(s + 1) * args.kblocks / args.splits);
-      ok = __all_sync(FULL, mbar_wait(tfull_bar(acc), aph, args.timeout, abort_flag));
+      const Unit w = sched.unit(u);
+      const int tile = w.tile, s = w.s, tm = w.tm, tn = w.tn, kb0 = w.kb0, kb1 = w.kb1, ntiles = w.ntiles;
+      if constexpr (Sched::kMapsInGlobal) {
+        if (lane == 0) tensormap_fence_acquire(w.c);
+      }
+      ok = __all_sync(FULL, mbar_wait(tfull_bar(acc), aph, timeout, abort_flag));
       if (!ok) break;
       tc_fence_after();
       const bool have = kb1 > kb0;
       const uint32_t tacc = tmem_base + (static_cast<uint32_t>(q * 32) << 16) + static_cast<uint32_t>(acc * C::ACC_COLS);
-      if (args.splits == 1) {
+      if (w.splits == 1) {
 #pragma unroll 1
         for (int h = 0; h < C::HALVES; ++h)
 #pragma unroll 1
           for (int c = 0; c < BN / 32; ++c) {
             float v[32];
             load_acc(tacc + h * BN + c * 32, have, v);
-            store_block(&tmC, v, tm * BM + h * 128 + q * 32, tn * BN + c * 32, args.M, args.N, args.beta, stg0,
-                        sbuf, lane);
+            store_block(w.c, v, tm * BM + h * 128 + q * 32, tn * BN + c * 32, w.M, w.N, w.beta, stg0, sbuf,
+                        lane);
           }
       } else {
         const size_t tile_elems = static_cast<size_t>(BM) * BN;
-        float* own_ws = args.ws + (static_cast<size_t>(s) * ntiles + tile) * tile_elems;
+        float* own_ws = ws + (static_cast<size_t>(s) * ntiles + tile) * tile_elems;
 #pragma unroll 1
         for (int h = 0; h < C::HALVES; ++h)
 #pragma unroll 1
@@ -320,9 +409,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         __syncwarp();
         int last = 0;
         if (lane == 0) {
-          int32_t* t = args.tickets + static_cast<size_t>(tile) * 4 + q;
+          int32_t* t = tickets + static_cast<size_t>(tile) * 4 + q;
           const int old = atom_add_acq_rel_gpu(t, 1);
-          last = (old == args.splits - 1);
+          last = (old == w.splits - 1);
           if (last) *t = 0;
         }
         last = __shfl_sync(FULL, last, 0);
@@ -339,14 +428,14 @@ __global__ void __launch_bounds__(kThreads, 1)
               load_acc(tacc + h * BN + c * 32, have, own);
               const size_t roff = static_cast<size_t>(h * 128 + q * 32 + lane) * BN + c * 32;
               int t = 0;
-              for (int base = 0; base < args.splits; base += kBatch) {
+              for (int base = 0; base < w.splits; base += kBatch) {
                 float4 x[kBatch][8];
 #pragma unroll
                 for (int b = 0; b < kBatch; ++b) {
                   const int tb = base + b;
-                  if (tb < args.splits && tb != s) {
+                  if (tb < w.splits && tb != s) {
                     const float4* src = reinterpret_cast<const float4*>(
-                        args.ws + (static_cast<size_t>(tb) * ntiles + tile) * tile_elems + roff);
+                        ws + (static_cast<size_t>(tb) * ntiles + tile) * tile_elems + roff);
 #pragma unroll
                     for (int j = 0; j < 8; ++j) x[b][j] = __ldcg(src + j);
                   }
@@ -354,7 +443,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
                 for (int b = 0; b < kBatch; ++b) {
                   const int tb = base + b;
-                  if (tb < args.splits) {
+                  if (tb < w.splits) {
 #pragma unroll
                     for (int j = 0; j < 8; ++j) {
                       const float4 p = (tb == s) ? make_float4(own[4 * j], own[4 * j + 1], own[4 * j + 2], own[4 * j + 3])
@@ -369,8 +458,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                   }
                 }
               }
-              store_block(&tmC, v, tm * BM + h * 128 + q * 32, tn * BN + c * 32, args.M, args.N, args.beta,
-                          stg0, sbuf, lane);
+              store_block(w.c, v, tm * BM + h * 128 + q * 32, tn * BN + c * 32, w.M, w.N, w.beta, stg0, sbuf,
+                          lane);
             }
         }
       }
@@ -383,7 +472,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
     }
     if (!ok && lane == 0) {
-      atomicExch(args.err, kErrEpilogue);
+      atomicExch(err, kErrEpilogue);
       *abort_flag = 1;
     }
     if (lane == 0) bulk_wait<0>();
@@ -395,6 +484,23 @@ __global__ void __launch_bounds__(kThreads, 1)
     tc_fence_after();
     tmem_dealloc(tmem_base, C::TMEM_COLS);
   }
+}
+
+
+template <int BM, int BN, int STAGES>
+__global__ void __launch_bounds__(kThreads, 1)
+    gemm_bf16_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                     const __grid_constant__ CUtensorMap tmC, const GemmArgs args) {
+  SingleSched sched{&tmA, &tmB, &tmC, args.tiles_m, args.tiles_n, args.splits, args.kblocks, args.M, args.N, args.beta};
+  gemm_body<BM, BN, STAGES>(sched, args.ws, args.tickets, args.err, args.timeout, args.stall);
+}
+
+template <int BM, int BN, int STAGES>
+__global__ void __launch_bounds__(kThreads, 1)
+    gemm_bf16_grouped_kernel(const GroupHeader* __restrict__ hdr, const GroupItem* __restrict__ items, int32_t* err,
+                             long long timeout) {
+  GroupSched sched{hdr, items, 0, 0};
+  gemm_body<BM, BN, STAGES>(sched, nullptr, nullptr, err, timeout, 0);
 }
 
 // Device-side spin of about `ns` nanoseconds (global timer), so that launches
@@ -420,6 +526,17 @@ struct TileKernel {
 template <int BM, int BN, int ST>
 TileKernel make_tile_kernel() {
   return TileKernel{gemm_bf16_kernel<BM, BN, ST>, BM, BN, KCfg<BM, BN, ST>::SMEM_BYTES};
+}
+
+using GroupedFn = void (*)(const GroupHeader*, const GroupItem*, int32_t*, long long);
+
+static GroupedFn grouped_kernel(int tile) {
+  static const GroupedFn table[RG_NUM_TILES] = {
+      gemm_bf16_grouped_kernel<128, 64, 8>, gemm_bf16_grouped_kernel<128, 128, 6>,
+      gemm_bf16_grouped_kernel<128, 256, 4>, gemm_bf16_grouped_kernel<256, 64, 4>,
+      gemm_bf16_grouped_kernel<256, 128, 4>, gemm_bf16_grouped_kernel<256, 256, 3>,
+  };
+  return table[tile];
 }
 
 static const TileKernel& tile_kernel(int tile) {
@@ -694,7 +811,9 @@ extern "C" int rg_init(int device, int64_t workspace_bytes, rg_ctx** out) {
   for (int t = 0; t < RG_NUM_TILES; ++t) {
     const rg::TileKernel& tk = rg::tile_kernel(t);
     if ((e = cudaFuncSetAttribute(reinterpret_cast<const void*>(tk.fn), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  tk.smem)) != cudaSuccess) {
+                                  tk.smem)) != cudaSuccess ||
+        (e = cudaFuncSetAttribute(reinterpret_cast<const void*>(rg::grouped_kernel(t)),
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, tk.smem)) != cudaSuccess) {
       delete ctx;
       return rg::cuda_fail(e, "rg_init: shared-memory attribute");
     }
@@ -919,6 +1038,172 @@ extern "C" int rg_sweep(rg_ctx* ctx, const rg_grid* grid, int32_t n_variants, co
     }
   }
   return rg_check(ctx, stream);
+}
+
+// ------------------------------------------------------------------ grouped GEMM under CUDA graphs
+//
+// A group object owns kGroupSlots slots.  Each slot: a pinned host work list, a
+// device work list (header + items), a CUDA graph [copy host list -> device list,
+// persistent grouped kernel over all SMs] instantiated once, and an event marking
+// the slot's last replay.  A call takes the next slot, waits until that slot's
+// previous replay has finished (so its lists may be rewritten), encodes the
+// problems' tensor maps into the pinned list, sets the copy size to the used
+// part, and replays the graph on the caller's stream.  The graph's topology
+// never changes; only the list contents do.
+namespace rg {
+constexpr int kGroupSlots = 4;
+}
+
+struct rg_group {
+  rg_ctx* ctx = nullptr;
+  int tile = 0;
+  int max_items = 0;
+  struct Slot {
+    unsigned char* host = nullptr;  // pinned: header + items
+    unsigned char* dev = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaGraphNode_t copy_node = nullptr;
+    cudaEvent_t done = nullptr;
+    bool used = false;
+  } slot[rg::kGroupSlots];
+  int next = 0;
+};
+
+namespace rg {
+static size_t group_bytes(int n) { return sizeof(GroupHeader) + static_cast<size_t>(n) * sizeof(GroupItem); }
+
+static void group_free(rg_group* g) {
+  if (!g) return;
+  for (auto& sl : g->slot) {
+    if (sl.exec) cudaGraphExecDestroy(sl.exec);
+    if (sl.graph) cudaGraphDestroy(sl.graph);
+    if (sl.done) cudaEventDestroy(sl.done);
+    if (sl.host) cudaFreeHost(sl.host);
+    if (sl.dev) cudaFree(sl.dev);
+  }
+  delete g;
+}
+
+static int group_build_graph(rg_group* g, rg_group::Slot& sl) {
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaGraphCreate(&graph, 0);
+  if (e != cudaSuccess) return cuda_fail(e, "rg_group: graph");
+  cudaGraphNode_t copy = nullptr, kern = nullptr;
+  e = cudaGraphAddMemcpyNode1D(&copy, graph, nullptr, 0, sl.dev, sl.host, group_bytes(g->max_items),
+                               cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) {
+    const TileKernel& tk = tile_kernel(g->tile);
+    const GroupHeader* hdr = reinterpret_cast<const GroupHeader*>(sl.dev);
+    const GroupItem* items = reinterpret_cast<const GroupItem*>(sl.dev + sizeof(GroupHeader));
+    int32_t* err = g->ctx->err;
+    long long timeout = g->ctx->timeout;
+    void* params[4] = {&hdr, &items, &err, &timeout};
+    cudaKernelNodeParams kp = {};
+    kp.func = reinterpret_cast<void*>(grouped_kernel(g->tile));
+    kp.gridDim = dim3(static_cast<unsigned>(g->ctx->sm_count));
+    kp.blockDim = dim3(kThreads);
+    kp.sharedMemBytes = static_cast<unsigned>(tk.smem);
+    kp.kernelParams = params;
+    e = cudaGraphAddKernelNode(&kern, graph, &copy, 1, &kp);
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&sl.exec, graph, 0);
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(graph);
+    return cuda_fail(e, "rg_group: build graph");
+  }
+  sl.graph = graph;
+  sl.copy_node = copy;
+  return RG_OK;
+}
+}  // namespace rg
+
+extern "C" int rg_group_create(rg_ctx* ctx, int32_t tile, int32_t max_items, rg_group** out) {
+  rg::clear_error();
+  if (!ctx || !out || tile < 0 || tile >= RG_NUM_TILES || max_items <= 0 || max_items > (1 << 20))
+    return rg::fail(RG_ERR_INVALID, "rg_group_create: bad argument");
+  auto* g = new (std::nothrow) rg_group();
+  if (!g) return rg::fail(RG_ERR_OOM, "rg_group_create: host allocation");
+  g->ctx = ctx;
+  g->tile = tile;
+  g->max_items = max_items;
+  const size_t bytes = rg::group_bytes(max_items);
+  for (auto& sl : g->slot) {
+    cudaError_t e = cudaMallocHost(&sl.host, bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&sl.dev, bytes);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+      rg::group_free(g);
+      cudaGetLastError();
+      return rg::fail(RG_ERR_OOM, std::string("rg_group_create: ") + cudaGetErrorString(e));
+    }
+    std::memset(sl.host, 0, bytes);
+    const int rc = rg::group_build_graph(g, sl);
+    if (rc != RG_OK) {
+      rg::group_free(g);
+      return rc;
+    }
+  }
+  *out = g;
+  return RG_OK;
+}
+
+extern "C" void rg_group_destroy(rg_group* g) {
+  if (!g) return;
+  for (auto& sl : g->slot)
+    if (sl.used) cudaEventSynchronize(sl.done);
+  rg::group_free(g);
+}
+
+extern "C" int rg_gemm_grouped(rg_group* g, const rg_group_problem* probs, int32_t n, void* stream) {
+  rg::clear_error();
+  if (!g || (n > 0 && !probs) || n < 0) return rg::fail(RG_ERR_INVALID, "rg_gemm_grouped: bad argument");
+  if (n > g->max_items) return rg::fail(RG_ERR_SHAPE, "rg_gemm_grouped: more problems than the group holds");
+  if (n == 0) return RG_OK;
+  rg_group::Slot& sl = g->slot[g->next];
+  g->next = (g->next + 1) % rg::kGroupSlots;
+  cudaError_t e;
+  if (sl.used && (e = cudaEventSynchronize(sl.done)) != cudaSuccess) return rg::cuda_fail(e, "rg_gemm_grouped: slot");
+  auto* hdr = reinterpret_cast<rg::GroupHeader*>(sl.host);
+  auto* items = reinterpret_cast<rg::GroupItem*>(sl.host + sizeof(rg::GroupHeader));
+  const rg::TileShape ts = rg::tile_shape(g->tile);
+  int64_t tiles = 0;
+  int32_t count = 0;
+  for (int32_t i = 0; i < n; ++i) {
+    const rg_group_problem& p = probs[i];
+    rg::Launch L;
+    const int rc = rg::prepare(g->ctx, p.M, p.N, p.K, p.A, p.lda, p.B, p.ldb, p.C, p.ldc, RG_VARIANT(g->tile, 0),
+                               p.beta, p.pm, p.pn, p.pk, &L);
+    if (rc != RG_OK) return rc;
+    if (L.noop) continue;
+    if (L.zero_only) return rg::fail(RG_ERR_INVALID, "rg_gemm_grouped: K == 0 problems are not grouped");
+    rg::GroupItem& it = items[count++];
+    it.a = L.a;
+    it.b = L.b;
+    it.c = L.c;
+    it.M = L.args.M;
+    it.N = L.args.N;
+    it.beta = L.args.beta;
+    it.tiles_m = L.args.tiles_m;
+    it.tiles_n = L.args.tiles_n;
+    it.kblocks = L.args.kblocks;
+    it.tile_start = static_cast<int32_t>(tiles);
+    it.reserved = 0;
+    tiles += static_cast<int64_t>(L.args.tiles_m) * L.args.tiles_n;
+    if (tiles > (1LL << 30)) return rg::fail(RG_ERR_SHAPE, "rg_gemm_grouped: too many tiles");
+  }
+  (void)ts;
+  if (count == 0) return RG_OK;
+  hdr->n_items = count;
+  hdr->total_tiles = static_cast<int32_t>(tiles);
+  e = cudaGraphExecMemcpyNodeSetParams1D(sl.exec, sl.copy_node, sl.dev, sl.host, rg::group_bytes(count),
+                                         cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaGraphLaunch(sl.exec, static_cast<cudaStream_t>(stream));
+  if (e == cudaSuccess) e = cudaEventRecord(sl.done, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return rg::cuda_fail(e, "rg_gemm_grouped: replay");
+  sl.used = true;
+  g->ctx->launches += 1;
+  return RG_OK;
 }
 
 // ------------------------------------------------------------------ entry point without allocation

@@ -66,6 +66,13 @@ class rg_sweep_opts(C.Structure):
                 ("prune_splits", C.c_int32), ("reserved", C.c_int32)]
 
 
+class rg_group_problem(C.Structure):
+    _fields_ = [("M", C.c_int64), ("N", C.c_int64), ("K", C.c_int64), ("A", C.c_void_p), ("lda", C.c_int64),
+                ("B", C.c_void_p), ("ldb", C.c_int64), ("C", C.c_void_p), ("ldc", C.c_int64),
+                ("pm", C.c_int64), ("pn", C.c_int64), ("pk", C.c_int64), ("beta", C.c_int32),
+                ("reserved", C.c_int32)]
+
+
 class RGError(RuntimeError):
     def __init__(self, code: int, where: str, msg: str):
         super().__init__(f"{where}: {msg} (status {code})")
@@ -95,6 +102,9 @@ _sigs = {
     "rg_plan_build_ex": (C.c_int, [C.POINTER(rg_grid), _P, _I32, _P, _I32, C.POINTER(_P)]),
     "rg_launch_count": (C.c_int, [_P, C.POINTER(_I64)]),
     "rg_set_test_stall": (C.c_int, [_P, _I32]),
+    "rg_group_create": (C.c_int, [_P, _I32, _I32, C.POINTER(_P)]),
+    "rg_group_destroy": (None, [_P]),
+    "rg_gemm_grouped": (C.c_int, [_P, C.POINTER(rg_group_problem), _I32, _P]),
     "rg_fp8_quantize": (C.c_int, [_P, _P, _I64, _I64, _I64, _P, _I64, _P, _P]),
     "rg_gemm_fp8": (C.c_int, [_P, _I64, _I64, _I64, _P, _I64, _P, _P, _I64, _P, _P, _I64, _P]),
     "rg_landscape": (C.c_int, [C.POINTER(rg_grid), _I32, C.c_double, _I32, C.c_double, _I32, _P, _I32, _I32, _P]),
@@ -334,6 +344,33 @@ def rg_sweep(ctx, grid: rg_grid, variant_ids, A, B, Cp, opts: rg_sweep_opts | No
     _check(_lib.rg_sweep(ctx, C.byref(grid), len(vids), vids.ctypes.data, plan, _ptr(A), _ptr(B), _ptr(Cp),
                          C.byref(o), out.ctypes.data, _stream(stream)), "rg_sweep")
     return out
+
+
+def rg_group_create(ctx: int, tile: int, max_items: int) -> int:
+    h = _P()
+    _check(_lib.rg_group_create(ctx, tile, max_items, C.byref(h)), "rg_group_create")
+    return h.value
+
+
+def rg_group_destroy(group: int) -> None:
+    _lib.rg_group_destroy(group)
+
+
+def group_problems(items) -> "C.Array":
+    """items: iterables (M, N, K, A, lda, B, ldb, C, ldc[, beta[, pm, pn, pk]]) with pointers or tensors."""
+    arr = (rg_group_problem * max(1, len(items)))()
+    for i, it in enumerate(items):
+        M, N, K, A, lda, B, ldb, Cp, ldc = it[:9]
+        beta = it[9] if len(it) > 9 else 0
+        pm, pn, pk = it[10:13] if len(it) > 12 else (0, 0, 0)
+        arr[i] = rg_group_problem(M, N, K, _ptr(A), lda, _ptr(B), ldb, _ptr(Cp), ldc, pm, pn, pk, beta, 0)
+    return arr
+
+
+def rg_gemm_grouped(group: int, problems, n: int | None = None, stream=None) -> None:
+    arr = problems if isinstance(problems, C.Array) else group_problems(problems)
+    count = len(problems) if n is None else n
+    _check(_lib.rg_gemm_grouped(group, arr, count, _stream(stream)), "rg_gemm_grouped")
 
 
 def rg_fp8_quantize(ctx, X, rows, cols, ldx, Q, ldq, scales, stream=None) -> None:
