@@ -229,6 +229,54 @@ int rg_group_create(rg_ctx* ctx, int32_t tile, int32_t max_items, rg_group** out
 void rg_group_destroy(rg_group* group);
 int rg_gemm_grouped(rg_group* group, const rg_group_problem* problems, int32_t n, void* stream);
 
+/* ---- serving: continuous batching over the grouped GEMM ----
+ * rg_serve runs one trace of requests on the calling thread and returns when
+ * every request has finished or been rejected.  Requests are admitted in
+ * arrival order once arrived and once their operand bytes (2MK + 2KN + 4MN)
+ * fit under hbm_budget_bytes next to the admitted, unfinished requests; one
+ * that can never fit is rejected with RG_ERR_ADMISSION in its result.  Each
+ * request goes through rg_plan_lookup (plan may be NULL): a single-leaf cell
+ * lends its padded launch extents, a split cell runs as-is.  Whenever one of
+ * max_inflight slots is free, up to max_batch admitted requests form one
+ * grouped launch (rg_gemm_grouped, CUDA graph replay) on that slot's stream, so
+ * batches formed while others run overlap them on the device; finished batches
+ * release budget and admit waiting requests.  A request with C == NULL gets its
+ * output (ldc = N) from an arena of hbm_budget_bytes allocated for the run and
+ * released at completion (its values are then gone: for load tests).  Times in
+ * results are nanoseconds from the start of the run on the host's steady clock;
+ * arrival_ns must be non-decreasing.  A, B and (non-NULL) C are device memory
+ * the caller keeps valid for the whole call. */
+typedef struct {
+  int64_t hbm_budget_bytes;   /* default 64 GiB */
+  int32_t max_batch;          /* requests per grouped launch; default 64 */
+  int32_t max_inflight;       /* grouped launches on the GPU at once, 1..16; default 2 */
+  int32_t tile;               /* tile of the grouped kernel; default RG_TILE_128x128 */
+  int32_t reserved;
+} rg_serve_opts;
+typedef struct {
+  int64_t M, N, K;
+  const void* A;
+  int64_t lda;
+  const void* B;
+  int64_t ldb;
+  float* C;
+  int64_t ldc;
+  int64_t arrival_ns;
+} rg_serve_request;
+typedef struct {
+  int64_t admitted_ns, launched_ns, done_ns;
+  int32_t batch;              /* index of the grouped launch that ran it, -1 if none */
+  int32_t status;             /* RG_OK, RG_ERR_ADMISSION or RG_ERR_INVALID */
+} rg_serve_result;
+typedef struct {
+  int64_t requests, batches, admission_stalls;
+  double wall_s, p50_latency_us, p99_latency_us, mean_latency_us;
+  double tflops;              /* useful 2MNK of served requests / (last completion - first arrival) */
+} rg_serve_stats;
+void rg_serve_opts_default(rg_serve_opts* opts);
+int rg_serve(rg_ctx* ctx, const rg_plan* plan, const rg_serve_opts* opts, const rg_serve_request* requests,
+             int32_t n, rg_serve_result* results, rg_serve_stats* stats);
+
 /* ---- FP8 e4m3 with FP32 scales per 128 x 128 block (precision variant of the GEMM) ----
  * rg_fp8_quantize: X (rows x cols FP32, ldx) -> Q (e4m3 bytes, ldq) and scales
  * [ceil(rows/128)][ceil(cols/128)] (row-major, FP32): per block amax, s = amax / 448

@@ -73,6 +73,28 @@ class rg_group_problem(C.Structure):
                 ("reserved", C.c_int32)]
 
 
+class rg_serve_opts(C.Structure):
+    _fields_ = [("hbm_budget_bytes", C.c_int64), ("max_batch", C.c_int32), ("max_inflight", C.c_int32),
+                ("tile", C.c_int32), ("reserved", C.c_int32)]
+
+
+class rg_serve_request(C.Structure):
+    _fields_ = [("M", C.c_int64), ("N", C.c_int64), ("K", C.c_int64), ("A", C.c_void_p), ("lda", C.c_int64),
+                ("B", C.c_void_p), ("ldb", C.c_int64), ("C", C.c_void_p), ("ldc", C.c_int64),
+                ("arrival_ns", C.c_int64)]
+
+
+class rg_serve_result(C.Structure):
+    _fields_ = [("admitted_ns", C.c_int64), ("launched_ns", C.c_int64), ("done_ns", C.c_int64),
+                ("batch", C.c_int32), ("status", C.c_int32)]
+
+
+class rg_serve_stats(C.Structure):
+    _fields_ = [("requests", C.c_int64), ("batches", C.c_int64), ("admission_stalls", C.c_int64),
+                ("wall_s", C.c_double), ("p50_latency_us", C.c_double), ("p99_latency_us", C.c_double),
+                ("mean_latency_us", C.c_double), ("tflops", C.c_double)]
+
+
 class RGError(RuntimeError):
     def __init__(self, code: int, where: str, msg: str):
         super().__init__(f"{where}: {msg} (status {code})")
@@ -105,6 +127,9 @@ _sigs = {
     "rg_group_create": (C.c_int, [_P, _I32, _I32, C.POINTER(_P)]),
     "rg_group_destroy": (None, [_P]),
     "rg_gemm_grouped": (C.c_int, [_P, C.POINTER(rg_group_problem), _I32, _P]),
+    "rg_serve_opts_default": (None, [C.POINTER(rg_serve_opts)]),
+    "rg_serve": (C.c_int, [_P, _P, C.POINTER(rg_serve_opts), C.POINTER(rg_serve_request), _I32,
+                           C.POINTER(rg_serve_result), C.POINTER(rg_serve_stats)]),
     "rg_fp8_quantize": (C.c_int, [_P, _P, _I64, _I64, _I64, _P, _I64, _P, _P]),
     "rg_gemm_fp8": (C.c_int, [_P, _I64, _I64, _I64, _P, _I64, _P, _P, _I64, _P, _P, _I64, _P]),
     "rg_landscape": (C.c_int, [C.POINTER(rg_grid), _I32, C.c_double, _I32, C.c_double, _I32, _P, _I32, _I32, _P]),
@@ -371,6 +396,28 @@ def rg_gemm_grouped(group: int, problems, n: int | None = None, stream=None) -> 
     arr = problems if isinstance(problems, C.Array) else group_problems(problems)
     count = len(problems) if n is None else n
     _check(_lib.rg_gemm_grouped(group, arr, count, _stream(stream)), "rg_gemm_grouped")
+
+
+def rg_serve_opts_default() -> rg_serve_opts:
+    o = rg_serve_opts()
+    _lib.rg_serve_opts_default(C.byref(o))
+    return o
+
+
+def rg_serve(ctx, plan, opts: rg_serve_opts, requests):
+    """requests: iterables (M, N, K, A, lda, B, ldb, C or None, ldc, arrival_ns).
+    Returns (list of result dicts, stats dict)."""
+    n = len(requests)
+    arr = (rg_serve_request * max(1, n))()
+    for i, (M, N, K, A, lda, B, ldb, Cp, ldc, t) in enumerate(requests):
+        arr[i] = rg_serve_request(M, N, K, _ptr(A), lda, _ptr(B), ldb, _ptr(Cp), ldc, int(t))
+    res = (rg_serve_result * max(1, n))()
+    st = rg_serve_stats()
+    _check(_lib.rg_serve(ctx, plan, C.byref(opts), arr, n, res, C.byref(st)), "rg_serve")
+    results = [{"admitted_ns": r.admitted_ns, "launched_ns": r.launched_ns, "done_ns": r.done_ns,
+                "batch": r.batch, "status": r.status} for r in res[:n]]
+    stats = {k: getattr(st, k) for k, _ in rg_serve_stats._fields_}
+    return results, stats
 
 
 def rg_fp8_quantize(ctx, X, rows, cols, ldx, Q, ldq, scales, stream=None) -> None:
