@@ -291,6 +291,14 @@ int rg_fp8_quantize(rg_ctx* ctx, const float* X, int64_t rows, int64_t cols, int
                     int64_t ldq, float* scales, void* stream);
 int rg_gemm_fp8(rg_ctx* ctx, int64_t M, int64_t N, int64_t K, const uint8_t* qA, int64_t lda, const float* sA,
                 const uint8_t* qB, int64_t ldb, const float* sB, float* C, int64_t ldc, void* stream);
+/* Times rg_gemm_fp8 on every cell of `grid` with the sweep protocol of rg_sweep
+ * (same options; split pruning does not apply).  Cell (M, N, K) uses the
+ * contiguous prefixes qA[0 : M*K] (lda = K) and qB[0 : K*N] (ldb = N) with
+ * compact scale arrays read from sA and sB (they must hold the largest cell's
+ * blocks); C holds max M * max N floats.  Grid sizes must be multiples of 16.
+ * t_ns_out[cell] as in rg_sweep. */
+int rg_sweep_fp8(rg_ctx* ctx, const rg_grid* grid, const uint8_t* qA, const float* sA, const uint8_t* qB,
+                 const float* sB, float* C, const rg_sweep_opts* opts, int64_t* t_ns_out, void* stream);
 
 /* ---- first-principles landscapes (Sec. 9.1, 9.2) and kernel grading (Sec. 10; host) ----
  * out[cell] = achieved TFLOP/s of the analytic landscape on `grid`:

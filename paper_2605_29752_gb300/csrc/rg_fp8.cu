@@ -367,3 +367,77 @@ extern "C" int rg_gemm_fp8(rg_ctx* ctx, int64_t M, int64_t N, int64_t K, const u
                                            static_cast<cudaStream_t>(stream), params);
   return e == cudaSuccess ? RG_OK : rg::fail(RG_ERR_CUDA, std::string("rg_gemm_fp8: launch: ") + cudaGetErrorString(e));
 }
+
+namespace {
+uint64_t splitmix_next_fp8(uint64_t& s) {
+  uint64_t z = (s += 0x9E3779B97F4A7C15ull);
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+}  // namespace
+
+extern "C" int rg_sweep_fp8(rg_ctx* ctx, const rg_grid* grid, const uint8_t* qA, const float* sA, const uint8_t* qB,
+                            const float* sB, float* C, const rg_sweep_opts* opts, int64_t* t_ns_out, void* stream) {
+  rg::clear_error();
+  using namespace rg::fp8;
+  if (!ctx || !grid || !qA || !sA || !qB || !sB || !C || !t_ns_out)
+    return rg::fail(RG_ERR_INVALID, "rg_sweep_fp8: null argument");
+  if (!rg::grid_valid(*grid)) return rg::fail(RG_ERR_INVALID, "rg_sweep_fp8: invalid grid");
+  rg_sweep_opts o;
+  rg_sweep_opts_default(&o);
+  if (opts) o = *opts;
+  if (o.reps <= 0 || o.warmup < 0 || o.global_warmup < 0 || o.spin_ns < 0)
+    return rg::fail(RG_ERR_INVALID, "rg_sweep_fp8: options");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int64_t cells = rg::cells_of(*grid);
+  const int64_t nk = grid->k.count, nn = grid->n.count;
+  std::vector<int64_t> order(static_cast<size_t>(cells));
+  for (size_t i = 0; i < order.size(); ++i) order[i] = static_cast<int64_t>(i);
+  if (o.shuffle) {
+    uint64_t s = o.seed;
+    for (size_t i = order.size() - 1; i > 0; --i) std::swap(order[i], order[splitmix_next_fp8(s) % (i + 1)]);
+  }
+  int32_t* err = nullptr;
+  long long timeout = 0;
+  int sms = 0;
+  int rc = rg::ctx_fp8_info(ctx, &err, &timeout, &sms);
+  if (rc != RG_OK) return rc;
+  if (cudaFuncSetAttribute(reinterpret_cast<const void*>(gemm_fp8_kernel), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           SMEM_BYTES) != cudaSuccess)
+    return rg::fail(RG_ERR_CUDA, "rg_sweep_fp8: shared-memory attribute");
+  CUtensorMap ma, mb, mc;
+  Args args{};
+  dim3 grid_dim;
+  auto prep = [&](int64_t cell, int* launches) -> int {
+    const int64_t a = cell / (nn * nk), b = (cell / nk) % nn, c = cell % nk;
+    const int64_t M = rg::axis_value(grid->m, a), N = rg::axis_value(grid->n, b), K = rg::axis_value(grid->k, c);
+    if ((K % 16) || (N % 16)) return rg::fail(RG_ERR_ALIGN, "rg_sweep_fp8: grid sizes must be multiples of 16");
+    int r = rg::fp8_make_map(&ma, CU_TENSOR_MAP_DATA_TYPE_UINT8, qA, K, M, K, BK, BM);
+    if (r == RG_OK) r = rg::fp8_make_map(&mb, CU_TENSOR_MAP_DATA_TYPE_UINT8, qB, N, K, N, BN, BK);
+    if (r == RG_OK) r = rg::fp8_make_map(&mc, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, C, N, M, N * 4, 32, 32);
+    if (r != RG_OK) return r;
+    args.M = static_cast<int32_t>(M);
+    args.N = static_cast<int32_t>(N);
+    args.tiles_m = static_cast<int32_t>((M + BM - 1) / BM);
+    args.tiles_n = static_cast<int32_t>((N + BN - 1) / BN);
+    args.kblocks = static_cast<int32_t>((K + BK - 1) / BK);
+    args.sa_ld = args.kblocks;
+    args.sb_ld = args.tiles_n;
+    args.sA = sA;
+    args.sB = sB;
+    args.err = err;
+    args.timeout = timeout;
+    grid_dim = dim3(static_cast<unsigned>(std::min<int64_t>(static_cast<int64_t>(args.tiles_m) * args.tiles_n, sms)));
+    *launches = 1;
+    return RG_OK;
+  };
+  auto run = [&]() -> cudaError_t {
+    void* params[4] = {&ma, &mb, &mc, &args};
+    return rg::fp8_launch_pdl(reinterpret_cast<const void*>(gemm_fp8_kernel), grid_dim, kThreads, SMEM_BYTES, st,
+                              params);
+  };
+  rc = rg::timed_sweep(ctx, order, o, st, t_ns_out, prep, run);
+  if (rc != RG_OK) return rc;
+  return rg_check(ctx, stream);
+}

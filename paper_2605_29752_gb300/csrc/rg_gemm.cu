@@ -29,6 +29,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <functional>
 #include <mutex>
 #include <string>
 #include <type_traits>
@@ -768,6 +769,59 @@ cudaError_t fp8_launch_pdl(const void* fn, dim3 grid, int threads, int smem, cud
   return cudaLaunchKernelExC(&cfg, fn, params);
 }
 
+// The sweep protocol (Sec. 3: one discarded warm-up launch, then the mean of
+// `reps` launches; Sec. 5.4: items in the given, randomised order): for each
+// item, `prep` readies its launches and reports how many one repetition makes,
+// `run` enqueues one repetition.  A device spin before the timed group lets the
+// host enqueue the whole group, so the events time back-to-back device work.
+// Events are recorded in batches of 256 items and read after one synchronise.
+int timed_sweep(rg_ctx* ctx, const std::vector<int64_t>& order, const rg_sweep_opts& o, cudaStream_t st,
+                int64_t* t_ns_out, const std::function<int(int64_t, int*)>& prep,
+                const std::function<cudaError_t()>& run) {
+  const int kBatch = 256;
+  while (ctx->events.size() < 2 * kBatch) {
+    cudaEvent_t ev;
+    cudaError_t e = cudaEventCreate(&ev);
+    if (e != cudaSuccess) return cuda_fail(e, "sweep: event");
+    ctx->events.push_back(ev);
+  }
+  int nl = 1;
+  if (!order.empty() && o.global_warmup > 0) {
+    int rc = prep(order[0], &nl);
+    if (rc != RG_OK) return rc;
+    for (int i = 0; i < o.global_warmup; ++i)
+      if (cudaError_t e = run(); e != cudaSuccess) return cuda_fail(e, "sweep: warm-up");
+  }
+  for (size_t base = 0; base < order.size(); base += kBatch) {
+    const size_t nb = std::min<size_t>(kBatch, order.size() - base);
+    for (size_t i = 0; i < nb; ++i) {
+      int rc = prep(order[base + i], &nl);
+      if (rc != RG_OK) return rc;
+      cudaError_t e = cudaSuccess;
+      for (int w = 0; w < o.warmup && e == cudaSuccess; ++w) e = run();
+      if (e == cudaSuccess && o.spin_ns > 0) {
+        spin_kernel<<<1, 1, 0, st>>>(o.spin_ns * o.reps * static_cast<long long>(nl));
+        ++ctx->launches;
+        e = cudaGetLastError();
+      }
+      if (e == cudaSuccess) e = cudaEventRecord(ctx->events[2 * i], st);
+      for (int r = 0; r < o.reps && e == cudaSuccess; ++r) e = run();
+      if (e == cudaSuccess) e = cudaEventRecord(ctx->events[2 * i + 1], st);
+      if (e != cudaSuccess) return cuda_fail(e, "sweep: launch");
+    }
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "sweep: synchronize");
+    for (size_t i = 0; i < nb; ++i) {
+      float ms = 0.f;
+      e = cudaEventElapsedTime(&ms, ctx->events[2 * i], ctx->events[2 * i + 1]);
+      if (e != cudaSuccess) return cuda_fail(e, "sweep: event time");
+      const int64_t t = std::llround(static_cast<double>(ms) * 1e6 / o.reps);
+      t_ns_out[order[base + i]] = t > 0 ? t : 1;
+    }
+  }
+  return RG_OK;
+}
+
 // The context's error word, wait budget and SM count for kernels of other
 // translation units; counts one launch.
 int ctx_fp8_info(rg_ctx* ctx, int32_t** err, long long* timeout, int* sms) {
@@ -948,15 +1002,6 @@ extern "C" int rg_sweep(rg_ctx* ctx, const rg_grid* grid, int32_t n_variants, co
       std::swap(order[i], order[j]);
     }
   }
-  const int kBatch = 256;
-  if (ctx->events.size() < 2 * kBatch) {
-    while (ctx->events.size() < 2 * kBatch) {
-      cudaEvent_t ev;
-      cudaError_t e = cudaEventCreate(&ev);
-      if (e != cudaSuccess) return rg::cuda_fail(e, "rg_sweep: event");
-      ctx->events.push_back(ev);
-    }
-  }
   std::vector<rg::Launch> ls;
   auto dims = [&](int64_t item, int64_t* M, int64_t* N, int64_t* K) {
     const int64_t cell = item % cells;
@@ -979,20 +1024,6 @@ extern "C" int rg_sweep(rg_ctx* ctx, const rg_grid* grid, int32_t n_variants, co
     const int64_t kblocks = (K + rg::kBK - 1) / rg::kBK;
     return tiles >= ctx->sm_count || kblocks < 2 * S;
   };
-  auto build = [&](int64_t item, std::vector<rg::Launch>& out) -> int {
-    int64_t M, N, K;
-    dims(item, &M, &N, &K);
-    if (plan) return rg::plan_launches(ctx, plan, M, N, K, A, K, B, N, C, N, out);
-    out.resize(1);
-    return rg::prepare(ctx, M, N, K, A, K, B, N, C, N, variant_ids[item / cells], 0, 0, 0, 0, &out[0]);
-  };
-  auto run = [&](const std::vector<rg::Launch>& v) -> cudaError_t {
-    for (const auto& L : v) {
-      cudaError_t e = rg::launch(ctx, L, st);
-      if (e != cudaSuccess) return e;
-    }
-    return cudaSuccess;
-  };
   if (o.prune_splits && !plan) {  // timed items first, pruned ones marked
     std::vector<int64_t> keep;
     keep.reserve(order.size());
@@ -1004,39 +1035,28 @@ extern "C" int rg_sweep(rg_ctx* ctx, const rg_grid* grid, int32_t n_variants, co
     }
     order.swap(keep);
   }
-  if (!order.empty() && o.global_warmup > 0) {
-    int rc = build(order[0], ls);
-    if (rc != RG_OK) return rc;
-    for (int i = 0; i < o.global_warmup; ++i)
-      if (cudaError_t e = run(ls); e != cudaSuccess) return rg::cuda_fail(e, "rg_sweep: warmup");
-  }
-  for (size_t base = 0; base < order.size(); base += kBatch) {
-    const size_t nb = std::min<size_t>(kBatch, order.size() - base);
-    for (size_t i = 0; i < nb; ++i) {
-      int rc = build(order[base + i], ls);
-      if (rc != RG_OK) return rc;
-      cudaError_t e = cudaSuccess;
-      for (int w = 0; w < o.warmup && e == cudaSuccess; ++w) e = run(ls);
-      if (e == cudaSuccess && o.spin_ns > 0) {
-        rg::spin_kernel<<<1, 1, 0, st>>>(o.spin_ns * o.reps * static_cast<long long>(ls.size()));
-        ++ctx->launches;
-        e = cudaGetLastError();
-      }
-      if (e == cudaSuccess) e = cudaEventRecord(ctx->events[2 * i], st);
-      for (int r = 0; r < o.reps && e == cudaSuccess; ++r) e = run(ls);
-      if (e == cudaSuccess) e = cudaEventRecord(ctx->events[2 * i + 1], st);
-      if (e != cudaSuccess) return rg::cuda_fail(e, "rg_sweep: launch");
+  auto prep = [&](int64_t item, int* launches) -> int {
+    int64_t M, N, K;
+    dims(item, &M, &N, &K);
+    int rc;
+    if (plan) {
+      rc = rg::plan_launches(ctx, plan, M, N, K, A, K, B, N, C, N, ls);
+    } else {
+      ls.resize(1);
+      rc = rg::prepare(ctx, M, N, K, A, K, B, N, C, N, variant_ids[item / cells], 0, 0, 0, 0, &ls[0]);
     }
-    cudaError_t e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess) return rg::cuda_fail(e, "rg_sweep: synchronize");
-    for (size_t i = 0; i < nb; ++i) {
-      float ms = 0.f;
-      e = cudaEventElapsedTime(&ms, ctx->events[2 * i], ctx->events[2 * i + 1]);
-      if (e != cudaSuccess) return rg::cuda_fail(e, "rg_sweep: event time");
-      const int64_t t = std::llround(static_cast<double>(ms) * 1e6 / o.reps);
-      t_ns_out[order[base + i]] = t > 0 ? t : 1;
+    *launches = static_cast<int>(ls.size());
+    return rc;
+  };
+  auto run = [&]() -> cudaError_t {
+    for (const auto& L : ls) {
+      cudaError_t e = rg::launch(ctx, L, st);
+      if (e != cudaSuccess) return e;
     }
-  }
+    return cudaSuccess;
+  };
+  const int rc = rg::timed_sweep(ctx, order, o, st, t_ns_out, prep, run);
+  if (rc != RG_OK) return rc;
   return rg_check(ctx, stream);
 }
 

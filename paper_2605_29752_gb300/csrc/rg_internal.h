@@ -43,6 +43,17 @@ inline int variant_split(int v) { return 1 << (v % RG_NUM_SPLITS); }
 
 }  // namespace rg
 
+#ifdef __CUDACC__
+#include <cuda_runtime.h>
+
+#include <functional>
+namespace rg {
+int timed_sweep(rg_ctx* ctx, const std::vector<int64_t>& order, const rg_sweep_opts& o, cudaStream_t st,
+                int64_t* t_ns_out, const std::function<int(int64_t, int*)>& prep,
+                const std::function<cudaError_t()>& run);
+}
+#endif
+
 struct rg_plan {
   rg::Plan p;
 };

@@ -132,6 +132,7 @@ _sigs = {
                            C.POINTER(rg_serve_result), C.POINTER(rg_serve_stats)]),
     "rg_fp8_quantize": (C.c_int, [_P, _P, _I64, _I64, _I64, _P, _I64, _P, _P]),
     "rg_gemm_fp8": (C.c_int, [_P, _I64, _I64, _I64, _P, _I64, _P, _P, _I64, _P, _P, _I64, _P]),
+    "rg_sweep_fp8": (C.c_int, [_P, C.POINTER(rg_grid), _P, _P, _P, _P, _P, C.POINTER(rg_sweep_opts), _P, _P]),
     "rg_landscape": (C.c_int, [C.POINTER(rg_grid), _I32, C.c_double, _I32, C.c_double, _I32, _P, _I32, _I32, _P]),
     "rg_kol": (C.c_int, [C.c_double, C.c_double, C.c_double, C.c_double, _P, _P]),
     "rg_gemm_noalloc": (C.c_int, [_I64, _I64, _I64, _P, _I64, _P, _I64, _P, _I64, _I32, _I32, _P]),
@@ -428,6 +429,14 @@ def rg_fp8_quantize(ctx, X, rows, cols, ldx, Q, ldq, scales, stream=None) -> Non
 def rg_gemm_fp8(ctx, M, N, K, qA, lda, sA, qB, ldb, sB, Cp, ldc, stream=None) -> None:
     _check(_lib.rg_gemm_fp8(ctx, M, N, K, _ptr(qA), lda, _ptr(sA), _ptr(qB), ldb, _ptr(sB), _ptr(Cp), ldc,
                             _stream(stream)), "rg_gemm_fp8")
+
+
+def rg_sweep_fp8(ctx, grid: rg_grid, qA, sA, qB, sB, Cp, opts: rg_sweep_opts | None = None, stream=None) -> np.ndarray:
+    out = np.zeros(grid_cells(grid), np.int64)
+    o = opts or rg_sweep_opts_default()
+    _check(_lib.rg_sweep_fp8(ctx, C.byref(grid), _ptr(qA), _ptr(sA), _ptr(qB), _ptr(sB), _ptr(Cp), C.byref(o),
+                             out.ctypes.data, _stream(stream)), "rg_sweep_fp8")
+    return out
 
 
 RG_LANDSCAPE_IDEAL = 0
