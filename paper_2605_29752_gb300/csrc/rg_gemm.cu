@@ -27,6 +27,7 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstring>
 #include <functional>
@@ -132,6 +133,7 @@ struct Unit {
   const CUtensorMap* a;
   const CUtensorMap* b;
   const CUtensorMap* c;
+  const CUtensorMap* w;  // split-K workspace [split][tile][BM rows] x BN, FP32 (split-K only)
   int tm, tn;     // tile coordinates in the problem
   int s, splits;  // K split index and count
   int kb0, kb1;   // K blocks [kb0, kb1) of this unit
@@ -140,12 +142,14 @@ struct Unit {
   int tile, ntiles;  // tile id / tile count of the problem (split-K workspace and tickets)
 };
 
-__device__ __forceinline__ Unit split_unit(const CUtensorMap* a, const CUtensorMap* b, const CUtensorMap* c, int u,
-                                           int tiles_m, int tiles_n, int splits, int kblocks, int M, int N, int beta) {
+__device__ __forceinline__ Unit split_unit(const CUtensorMap* a, const CUtensorMap* b, const CUtensorMap* c,
+                                           const CUtensorMap* w, int u, int tiles_m, int tiles_n, int splits,
+                                           int kblocks, int M, int N, int beta) {
   Unit x;
   x.a = a;
   x.b = b;
   x.c = c;
+  x.w = w;
   x.tile = u / splits;
   x.s = u % splits;
   x.splits = splits;
@@ -166,6 +170,7 @@ struct SingleSched {
   const CUtensorMap* a;
   const CUtensorMap* b;
   const CUtensorMap* c;
+  const CUtensorMap* w;
   int tiles_m, tiles_n, splits, kblocks, M, N, beta;
   __device__ __forceinline__ void prefetch() const {
     prefetch_tmap(a);
@@ -174,7 +179,7 @@ struct SingleSched {
   }
   __device__ __forceinline__ int total() const { return tiles_m * tiles_n * splits; }
   __device__ __forceinline__ Unit unit(int u) const {
-    return split_unit(a, b, c, u, tiles_m, tiles_n, splits, kblocks, M, N, beta);
+    return split_unit(a, b, c, w, u, tiles_m, tiles_n, splits, kblocks, M, N, beta);
   }
 };
 
@@ -208,8 +213,8 @@ struct GroupSched {
       if (items[mid].tile_start <= u) lo = mid; else hi = mid - 1;
     }
     const GroupItem& it = items[lo];
-    return split_unit(&it.a, &it.b, &it.c, u - it.tile_start, it.tiles_m, it.tiles_n, 1, it.kblocks, it.M, it.N,
-                      it.beta);
+    return split_unit(&it.a, &it.b, &it.c, nullptr, u - it.tile_start, it.tiles_m, it.tiles_n, 1, it.kblocks, it.M,
+                      it.N, it.beta);
   }
 };
 
@@ -392,21 +397,23 @@ __device__ __forceinline__ void gemm_body(Sched& sched, float* ws, int32_t* tick
                         lane);
           }
       } else {
-        const size_t tile_elems = static_cast<size_t>(BM) * BN;
-        float* own_ws = ws + (static_cast<size_t>(s) * ntiles + tile) * tile_elems;
+        // Split-K.  Publish this split's FP32 partial tile: TMEM -> swizzled staging ->
+        // TMA store into the workspace (rows (s * ntiles + tile) * BM ..), then wait
+        // for the stores, fence them against the generic proxy and take the ticket
+        // of this (tile, warp) row block with an acquire-release atomic.
+        const int wrow = (s * ntiles + tile) * BM;
 #pragma unroll 1
         for (int h = 0; h < C::HALVES; ++h)
 #pragma unroll 1
           for (int c = 0; c < BN / 32; ++c) {
             float v[32];
             load_acc(tacc + h * BN + c * 32, have, v);
-            float4* dst = reinterpret_cast<float4*>(own_ws + static_cast<size_t>(h * 128 + q * 32 + lane) * BN + c * 32);
-#pragma unroll
-            for (int j = 0; j < 8; ++j) dst[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+            store_block(w.w, v, wrow + h * 128 + q * 32, c * 32, INT_MAX, INT_MAX, 0, stg0, sbuf, lane);
           }
-        // Publish this warp's partial rows: the warp barrier orders every lane's
-        // stores before lane 0's release; the last arriver's acquire (then the
-        // warp barrier) orders the other splits' rows before its loads.
+        if (lane == 0) {
+          bulk_wait<0>();
+          fence_proxy_async_global();
+        }
         __syncwarp();
         int last = 0;
         if (lane == 0) {
@@ -417,17 +424,33 @@ __device__ __forceinline__ void gemm_body(Sched& sched, float* ws, int32_t* tick
         }
         last = __shfl_sync(FULL, last, 0);
         if (last) {
-          // Sum the S partials of each 32 x 32 block in the fixed order 0..S-1.
-          // Partials are loaded in batches of up to kBatch so that their L2 round
-          // trips overlap (the latency of one batch, not of each partial).
+          // The last arriver sums the S partials of each 32 x 32 block in the fixed
+          // order 0..S-1.  Lane l holds block rows 4j + l/8 (j = 0..7), columns
+          // 4(l%8)..4(l%8)+3, so each warp load reads four whole 128-byte rows;
+          // partials are loaded kBatch at a time.  Its own partial (still in TMEM,
+          // one row per lane) is brought into that layout through the staging buffer.
           constexpr int kBatch = 3;
+          const int rsub = lane >> 3, g = lane & 7;
 #pragma unroll 1
           for (int h = 0; h < C::HALVES; ++h)
 #pragma unroll 1
             for (int c = 0; c < BN / 32; ++c) {
-              float own[32], v[32];
+              float own[32];
               load_acc(tacc + h * BN + c * 32, have, own);
-              const size_t roff = static_cast<size_t>(h * 128 + q * 32 + lane) * BN + c * 32;
+              if (lane == 0) bulk_wait_read<1>();
+              __syncwarp();
+              const uint32_t buf = stg0 + sbuf * 4096;
+#pragma unroll
+              for (int j = 0; j < 8; ++j)
+                st_shared_v4(buf + lane * 128 + ((j ^ (lane & 7)) << 4), own[4 * j], own[4 * j + 1], own[4 * j + 2],
+                             own[4 * j + 3]);
+              __syncwarp();
+              float4 o[8], sum[8];
+#pragma unroll
+              for (int j = 0; j < 8; ++j) {
+                const int r = 4 * j + rsub;
+                o[j] = ld_shared_v4(buf + r * 128 + ((g ^ (r & 7)) << 4));
+              }
               int t = 0;
               for (int base = 0; base < w.splits; base += kBatch) {
                 float4 x[kBatch][8];
@@ -435,10 +458,11 @@ __device__ __forceinline__ void gemm_body(Sched& sched, float* ws, int32_t* tick
                 for (int b = 0; b < kBatch; ++b) {
                   const int tb = base + b;
                   if (tb < w.splits && tb != s) {
-                    const float4* src = reinterpret_cast<const float4*>(
-                        ws + (static_cast<size_t>(tb) * ntiles + tile) * tile_elems + roff);
+                    const float* src = ws + static_cast<size_t>((tb * ntiles + tile) * BM + h * 128 + q * 32) * BN +
+                                       c * 32 + 4 * g;
 #pragma unroll
-                    for (int j = 0; j < 8; ++j) x[b][j] = __ldcg(src + j);
+                    for (int j = 0; j < 8; ++j)
+                      x[b][j] = __ldcg(reinterpret_cast<const float4*>(src + static_cast<size_t>(4 * j + rsub) * BN));
                   }
                 }
 #pragma unroll
@@ -447,20 +471,36 @@ __device__ __forceinline__ void gemm_body(Sched& sched, float* ws, int32_t* tick
                   if (tb < w.splits) {
 #pragma unroll
                     for (int j = 0; j < 8; ++j) {
-                      const float4 p = (tb == s) ? make_float4(own[4 * j], own[4 * j + 1], own[4 * j + 2], own[4 * j + 3])
-                                                 : x[b][j];
+                      const float4 p = (tb == s) ? o[j] : x[b][j];
                       if (t == 0) {
-                        v[4 * j] = p.x; v[4 * j + 1] = p.y; v[4 * j + 2] = p.z; v[4 * j + 3] = p.w;
+                        sum[j] = p;
                       } else {
-                        v[4 * j] += p.x; v[4 * j + 1] += p.y; v[4 * j + 2] += p.z; v[4 * j + 3] += p.w;
+                        sum[j].x += p.x; sum[j].y += p.y; sum[j].z += p.z; sum[j].w += p.w;
                       }
                     }
                     ++t;
                   }
                 }
               }
-              store_block(w.c, v, tm * BM + h * 128 + q * 32, tn * BN + c * 32, w.M, w.N, w.beta, stg0, sbuf,
-                          lane);
+              __syncwarp();
+#pragma unroll
+              for (int j = 0; j < 8; ++j) {
+                const int r = 4 * j + rsub;
+                st_shared_v4(buf + r * 128 + ((g ^ (r & 7)) << 4), sum[j].x, sum[j].y, sum[j].z, sum[j].w);
+              }
+              fence_proxy_async_smem();
+              __syncwarp();
+              const int row0 = tm * BM + h * 128 + q * 32, col0 = tn * BN + c * 32;
+              if (row0 < w.M && col0 < w.N) {
+                if (lane == 0) {
+                  if (w.beta)
+                    tma_reduce_add_2d(w.c, buf, col0, row0);
+                  else
+                    tma_store_2d(w.c, buf, col0, row0);
+                  bulk_commit();
+                }
+                sbuf ^= 1;
+              }
             }
         }
       }
@@ -491,8 +531,10 @@ __device__ __forceinline__ void gemm_body(Sched& sched, float* ws, int32_t* tick
 template <int BM, int BN, int STAGES>
 __global__ void __launch_bounds__(kThreads, 1)
     gemm_bf16_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                     const __grid_constant__ CUtensorMap tmC, const GemmArgs args) {
-  SingleSched sched{&tmA, &tmB, &tmC, args.tiles_m, args.tiles_n, args.splits, args.kblocks, args.M, args.N, args.beta};
+                     const __grid_constant__ CUtensorMap tmC, const __grid_constant__ CUtensorMap tmW,
+                     const GemmArgs args) {
+  SingleSched sched{&tmA,        &tmB,          &tmC,   &tmW,  args.tiles_m, args.tiles_n,
+                    args.splits, args.kblocks, args.M, args.N, args.beta};
   gemm_body<BM, BN, STAGES>(sched, args.ws, args.tickets, args.err, args.timeout, args.stall);
 }
 
@@ -517,7 +559,7 @@ __global__ void spin_kernel(long long ns) {
 
 // ------------------------------------------------------------------ host side
 
-using KernFn = void (*)(const CUtensorMap, const CUtensorMap, const CUtensorMap, const GemmArgs);
+using KernFn = void (*)(const CUtensorMap, const CUtensorMap, const CUtensorMap, const CUtensorMap, const GemmArgs);
 
 struct TileKernel {
   KernFn fn;
@@ -604,7 +646,7 @@ static int make_map(CUtensorMap* m, CUtensorMapDataType dt, const void* base, ui
 
 struct Launch {
   KernFn fn = nullptr;
-  CUtensorMap a, b, c;
+  CUtensorMap a, b, c, w;
   GemmArgs args{};
   dim3 grid;
   int smem = 0;
@@ -664,6 +706,13 @@ static int prepare(rg_ctx* ctx, int64_t M, int64_t N, int64_t K, const void* A, 
   rc = make_map(&L->a, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, A, K, M, lda * 2, kBK, tk.bm);
   if (rc == RG_OK) rc = make_map(&L->b, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, B, N, K, ldb * 2, 64, kBK);
   if (rc == RG_OK) rc = make_map(&L->c, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, C, N, M, ldc * 4, 32, 32);
+  if (rc == RG_OK) {
+    if (splits > 1)  // workspace rows: [split][tile][BM], BN floats each
+      rc = make_map(&L->w, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, ctx->ws, tk.bn,
+                    static_cast<uint64_t>(splits) * tiles_m * tiles_n * tk.bm, static_cast<uint64_t>(tk.bn) * 4, 32, 32);
+    else
+      L->w = L->c;  // unused without split-K
+  }
   if (rc != RG_OK) return rc;
   L->fn = tk.fn;
   L->smem = tk.smem;
@@ -689,8 +738,8 @@ static cudaError_t launch(rg_ctx* ctx, const Launch& L, cudaStream_t st) {
   if (L.noop) return cudaSuccess;
   if (L.zero_only) return cudaMemset2DAsync(L.C, L.ldc * 4, 0, L.N * 4, L.M, st);
   ++ctx->launches;
-  void* params[4] = {const_cast<CUtensorMap*>(&L.a), const_cast<CUtensorMap*>(&L.b), const_cast<CUtensorMap*>(&L.c),
-                     const_cast<GemmArgs*>(&L.args)};
+  void* params[5] = {const_cast<CUtensorMap*>(&L.a), const_cast<CUtensorMap*>(&L.b), const_cast<CUtensorMap*>(&L.c),
+                     const_cast<CUtensorMap*>(&L.w), const_cast<GemmArgs*>(&L.args)};
   // Programmatic dependent launch: the grid may be scheduled while the previous
   // grid in the stream finishes; the kernel waits (griddepcontrol.wait) before
   // its first global memory access.
