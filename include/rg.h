@@ -55,8 +55,8 @@ enum {
 
 /* ---- kernel variants ----
  * Six output tiles (BM x BN), each with an in-kernel split-K factor S in
- * {1, 2, 4, 8}.  variant id = tile * RG_NUM_SPLITS + log2(S).  Variant ids
- * are ordered tile-major, then by S; ties in best-of selection go to the
+ * {1, 2, 4, 8} (id = tile * RG_NUM_SPLITS + log2(S)) and a stream-K
+ * schedule (id = RG_VARIANT_SK(tile)).  Ties in best-of selection go to the
  * lowest id.                                                   (Sec. 6.1, 6.4) */
 enum {
   RG_TILE_128x64 = 0, RG_TILE_128x128 = 1, RG_TILE_128x256 = 2,
@@ -64,8 +64,13 @@ enum {
   RG_NUM_TILES = 6
 };
 #define RG_NUM_SPLITS 4
-#define RG_NUM_VARIANTS (RG_NUM_TILES * RG_NUM_SPLITS)
 #define RG_VARIANT(tile, log2_split) ((tile) * RG_NUM_SPLITS + (log2_split))
+/* Stream-K variant of a tile (ids 24..29, after the split-K ids): the launch's
+ * tiles x K-blocks iterations are divided evenly among at most one CTA per SM
+ * (each CTA at least 4 K blocks); a tile whose iterations span several CTAs is
+ * summed by its last arriving piece in the fixed order of their K ranges. */
+#define RG_VARIANT_SK(tile) (RG_NUM_TILES * RG_NUM_SPLITS + (tile))
+#define RG_NUM_VARIANTS (RG_NUM_TILES * RG_NUM_SPLITS + RG_NUM_TILES)
 
 typedef struct rg_ctx rg_ctx;
 typedef struct rg_plan rg_plan;

@@ -60,6 +60,8 @@ struct GemmArgs {
   int32_t kblocks;          // ceil(padded K / 64)
   int32_t beta;
   int32_t stall;            // test hook: the MMA warp first waits on a barrier nothing arrives on
+  int32_t dp_tiles;         // stream-K: tiles run whole before the shared tail
+  int32_t reserved_;
   float* ws;                // split-K partials [split][tile][BM][BN]
   int32_t* tickets;         // [tile][4], zero between launches
   int32_t* err;
@@ -177,9 +179,99 @@ struct SingleSched {
     prefetch_tmap(b);
     prefetch_tmap(c);
   }
-  __device__ __forceinline__ int total() const { return tiles_m * tiles_n * splits; }
-  __device__ __forceinline__ Unit unit(int u) const {
-    return split_unit(a, b, c, w, u, tiles_m, tiles_n, splits, kblocks, M, N, beta);
+  __device__ __forceinline__ void init() {}
+  // units u = blockIdx.x + i * gridDim.x of the (tile, split) space
+  __device__ __forceinline__ int count() const {
+    const int t = tiles_m * tiles_n * splits;
+    return static_cast<int>(blockIdx.x) < t ? (t - 1 - static_cast<int>(blockIdx.x)) / static_cast<int>(gridDim.x) + 1
+                                            : 0;
+  }
+  __device__ __forceinline__ Unit unit(int i) const {
+    return split_unit(a, b, c, w, static_cast<int>(blockIdx.x) + i * static_cast<int>(gridDim.x), tiles_m, tiles_n,
+                      splits, kblocks, M, N, beta);
+  }
+};
+
+// Stream-K (hybrid): whole waves of tiles run data-parallel, one tile per CTA
+// per wave (tile g + i * G on CTA g, for tiles below dp_tiles = G * floor(T / G));
+// the remaining tiles' K iterations are divided evenly among the first tail CTAs:
+// CTA h owns tail iterations [h I / tail, (h+1) I / tail), processed as one
+// segment per tile it touches.  A tail tile covered by one segment is stored
+// directly; one split over several CTAs is summed by its last arriving segment
+// in the fixed order of the segments' K ranges (through the split-K workspace,
+// slot = segment * ntiles + tile).  So no wave is left partly idle.
+struct StreamKSched {
+  static constexpr bool kMapsInGlobal = false;
+  const CUtensorMap* a;
+  const CUtensorMap* b;
+  const CUtensorMap* c;
+  const CUtensorMap* w;
+  int tiles_m, tiles_n, kblocks, M, N, beta;
+  int tail = 0;      // CTAs sharing the tail tiles (from the launcher)
+  int dp_tiles = 0;  // tiles run whole (from the launcher)
+  long long iters = 0, begin = 0, end = 0;
+  int G = 1, g = 0, T = 0, n_dp = 0, t0 = 0, n_sk = 0;
+  __device__ __forceinline__ void prefetch() const {
+    prefetch_tmap(a);
+    prefetch_tmap(b);
+    prefetch_tmap(c);
+  }
+  __device__ __forceinline__ long long cta_begin(int h) const { return static_cast<long long>(h) * iters / tail; }
+  // the tail CTA whose range holds tail iteration x
+  __device__ __forceinline__ int cta_of(long long x) const {
+    int h = static_cast<int>((x * tail) / iters);
+    while (h + 1 < tail && cta_begin(h + 1) <= x) ++h;
+    while (h > 0 && cta_begin(h) > x) --h;
+    return h;
+  }
+  __device__ __forceinline__ void init() {
+    G = static_cast<int>(gridDim.x);
+    g = static_cast<int>(blockIdx.x);
+    T = tiles_m * tiles_n;
+    n_dp = g < dp_tiles ? (dp_tiles - 1 - g) / G + 1 : 0;
+    iters = static_cast<long long>(T - dp_tiles) * kblocks;
+    if (tail > 0 && g < tail && iters > 0) {
+      begin = cta_begin(g);
+      end = cta_begin(g + 1);
+      if (end > begin) {
+        t0 = static_cast<int>(begin / kblocks);
+        n_sk = static_cast<int>((end - 1) / kblocks) - t0 + 1;
+      }
+    }
+  }
+  __device__ __forceinline__ int count() const { return n_dp + n_sk; }
+  __device__ __forceinline__ Unit unit(int i) const {
+    Unit x;
+    x.a = a;
+    x.b = b;
+    x.c = c;
+    x.w = w;
+    x.M = M;
+    x.N = N;
+    x.beta = beta;
+    x.ntiles = T;
+    if (i < n_dp) {  // a whole tile of the data-parallel waves
+      x.tile = g + i * G;
+      x.kb0 = 0;
+      x.kb1 = kblocks;
+      x.splits = 1;
+      x.s = 0;
+    } else {  // a segment of a tail tile
+      const int j = i - n_dp;
+      const int lt = t0 + j;  // index among the tail tiles
+      x.tile = dp_tiles + lt;
+      const long long tb = static_cast<long long>(lt) * kblocks;
+      const long long lo = begin > tb ? begin : tb;
+      const long long hi = end < tb + kblocks ? end : tb + kblocks;
+      x.kb0 = static_cast<int>(lo - tb);
+      x.kb1 = static_cast<int>(hi - tb);
+      const int first = cta_of(tb), last = cta_of(tb + kblocks - 1);
+      x.splits = last - first + 1;
+      x.s = g - first;
+    }
+    x.tm = x.tile / tiles_n;
+    x.tn = x.tile % tiles_n;
+    return x;
   }
 };
 
@@ -205,8 +297,17 @@ struct GroupSched {
   const GroupItem* items;
   int n_items, total_tiles;  // read after the grid dependency wait
   __device__ __forceinline__ void prefetch() const {}
-  __device__ __forceinline__ int total() const { return total_tiles; }
-  __device__ __forceinline__ Unit unit(int u) const {
+  __device__ __forceinline__ void init() {
+    n_items = h->n_items;
+    total_tiles = h->total_tiles;
+  }
+  __device__ __forceinline__ int count() const {
+    return static_cast<int>(blockIdx.x) < total_tiles
+               ? (total_tiles - 1 - static_cast<int>(blockIdx.x)) / static_cast<int>(gridDim.x) + 1
+               : 0;
+  }
+  __device__ __forceinline__ Unit unit(int i) const {
+    const int u = static_cast<int>(blockIdx.x) + i * static_cast<int>(gridDim.x);
     int lo = 0, hi = n_items - 1;  // last item whose tile_start <= u
     while (lo < hi) {
       const int mid = (lo + hi + 1) >> 1;
@@ -267,11 +368,8 @@ __device__ __forceinline__ void gemm_body(Sched& sched, float* ws, int32_t* tick
   // touches global memory before that grid has completed.
   grid_dependency_wait();
   grid_launch_dependents();
-  if constexpr (std::is_same<Sched, GroupSched>::value) {
-    sched.n_items = sched.h->n_items;
-    sched.total_tiles = sched.h->total_tiles;
-  }
-  const int total = sched.total();
+  sched.init();
+  const int nunits = sched.count();
 
   if (warp == 0) {
     // ------------------------------------------------ TMA producer (one thread)
@@ -280,8 +378,8 @@ __device__ __forceinline__ void gemm_body(Sched& sched, float* ws, int32_t* tick
       uint32_t ph = 0;
       uint32_t issued_mask = 0, issued_ph = 0;
       bool ok = true;
-      for (int u = blockIdx.x; ok && u < total; u += gridDim.x) {
-        const Unit w = sched.unit(u);
+      for (int i = 0; ok && i < nunits; ++i) {
+        const Unit w = sched.unit(i);
         if constexpr (Sched::kMapsInGlobal) {
           tensormap_fence_acquire(w.a);
           tensormap_fence_acquire(w.b);
@@ -320,8 +418,8 @@ __device__ __forceinline__ void gemm_body(Sched& sched, float* ws, int32_t* tick
     uint32_t ph = 0, aph = 0;
     bool ok = true;
     if (stall) ok = __all_sync(FULL, mbar_wait(drain_bar, 0, timeout, abort_flag));
-    for (int u = blockIdx.x; ok && u < total; u += gridDim.x) {
-      const Unit w = sched.unit(u);
+    for (int i = 0; ok && i < nunits; ++i) {
+      const Unit w = sched.unit(i);
       const int kb0 = w.kb0, kb1 = w.kb1;
       ok = __all_sync(FULL, mbar_wait(tempty_bar(acc), aph ^ 1u, timeout, abort_flag));
       if (!ok) break;
@@ -375,8 +473,8 @@ __device__ __forceinline__ void gemm_body(Sched& sched, float* ws, int32_t* tick
     int acc = 0, sbuf = 0;
     uint32_t aph = 0;
     bool ok = true;
-    for (int u = blockIdx.x; u < total; u += gridDim.x) {
-      const Unit w = sched.unit(u);
+    for (int i = 0; i < nunits; ++i) {
+      const Unit w = sched.unit(i);
       const int tile = w.tile, s = w.s, tm = w.tm, tn = w.tn, kb0 = w.kb0, kb1 = w.kb1, ntiles = w.ntiles;
       if constexpr (Sched::kMapsInGlobal) {
         if (lane == 0) tensormap_fence_acquire(w.c);
@@ -540,6 +638,16 @@ __global__ void __launch_bounds__(kThreads, 1)
 
 template <int BM, int BN, int STAGES>
 __global__ void __launch_bounds__(kThreads, 1)
+    gemm_bf16_streamk_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                             const __grid_constant__ CUtensorMap tmC, const __grid_constant__ CUtensorMap tmW,
+                             const GemmArgs args) {
+  StreamKSched sched{&tmA,        &tmB,   &tmC,   &tmW,      args.tiles_m, args.tiles_n, args.kblocks,
+                     args.M,      args.N, args.beta, args.splits /* CTAs sharing the tail */, args.dp_tiles};
+  gemm_body<BM, BN, STAGES>(sched, args.ws, args.tickets, args.err, args.timeout, args.stall);
+}
+
+template <int BM, int BN, int STAGES>
+__global__ void __launch_bounds__(kThreads, 1)
     gemm_bf16_grouped_kernel(const GroupHeader* __restrict__ hdr, const GroupItem* __restrict__ items, int32_t* err,
                              long long timeout) {
   GroupSched sched{hdr, items, 0, 0};
@@ -563,12 +671,14 @@ using KernFn = void (*)(const CUtensorMap, const CUtensorMap, const CUtensorMap,
 
 struct TileKernel {
   KernFn fn;
+  KernFn sk;  // stream-K instance of the same tile
   int bm, bn, smem;
 };
 
 template <int BM, int BN, int ST>
 TileKernel make_tile_kernel() {
-  return TileKernel{gemm_bf16_kernel<BM, BN, ST>, BM, BN, KCfg<BM, BN, ST>::SMEM_BYTES};
+  return TileKernel{gemm_bf16_kernel<BM, BN, ST>, gemm_bf16_streamk_kernel<BM, BN, ST>, BM, BN,
+                    KCfg<BM, BN, ST>::SMEM_BYTES};
 }
 
 using GroupedFn = void (*)(const GroupHeader*, const GroupItem*, int32_t*, long long);
@@ -652,6 +762,7 @@ struct Launch {
   int smem = 0;
   bool zero_only = false;  // K == 0 with beta == 0: C = 0
   bool noop = false;
+  int64_t ws_slots = 1;  // > 1: the launch uses the split-K workspace and tickets
   float* C = nullptr;
   int64_t M = 0, N = 0, ldc = 0;
 };
@@ -693,13 +804,22 @@ static int prepare(rg_ctx* ctx, int64_t M, int64_t N, int64_t K, const void* A, 
   int rc = get_encode();
   if (rc != RG_OK) return rc;
   const int tile = variant_tile(variant);
+  const bool sk = variant_streamk(variant);
   const int splits = variant_split(variant);
   const TileKernel& tk = tile_kernel(tile);
   const int64_t tiles_m = (pm + tk.bm - 1) / tk.bm;
   const int64_t tiles_n = (pn + tk.bn - 1) / tk.bn;
   const int64_t kblocks = (pk + kBK - 1) / kBK;
-  if (splits > 1) {
-    const int64_t need = static_cast<int64_t>(splits) * tiles_m * tiles_n * tk.bm * tk.bn * 4;
+  // workspace slots per tile: the split count, or stream-K's most segments on one tile
+  int64_t slots = splits;
+  SkGeometry skg{};
+  if (sk) {
+    skg = sk_geometry(tiles_m * tiles_n, kblocks, ctx->sm_count);
+    slots = skg.max_pieces;
+  }
+  const bool uses_ws = slots > 1;
+  if (uses_ws) {
+    const int64_t need = slots * tiles_m * tiles_n * tk.bm * tk.bn * 4;
     if (need > ctx->ws_bytes || tiles_m * tiles_n * 4 > kMaxTickets)
       return fail(RG_ERR_SHAPE, "split-K workspace too small for this shape");
   }
@@ -707,21 +827,23 @@ static int prepare(rg_ctx* ctx, int64_t M, int64_t N, int64_t K, const void* A, 
   if (rc == RG_OK) rc = make_map(&L->b, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, B, N, K, ldb * 2, 64, kBK);
   if (rc == RG_OK) rc = make_map(&L->c, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, C, N, M, ldc * 4, 32, 32);
   if (rc == RG_OK) {
-    if (splits > 1)  // workspace rows: [split][tile][BM], BN floats each
+    if (uses_ws)  // workspace rows: [slot][tile][BM], BN floats each
       rc = make_map(&L->w, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, ctx->ws, tk.bn,
-                    static_cast<uint64_t>(splits) * tiles_m * tiles_n * tk.bm, static_cast<uint64_t>(tk.bn) * 4, 32, 32);
+                    static_cast<uint64_t>(slots) * tiles_m * tiles_n * tk.bm, static_cast<uint64_t>(tk.bn) * 4, 32, 32);
     else
       L->w = L->c;  // unused without split-K
   }
   if (rc != RG_OK) return rc;
-  L->fn = tk.fn;
+  L->fn = sk ? tk.sk : tk.fn;
   L->smem = tk.smem;
+  L->ws_slots = slots;
   GemmArgs& g = L->args;
   g.M = static_cast<int32_t>(M);
   g.N = static_cast<int32_t>(N);
   g.tiles_m = static_cast<int32_t>(tiles_m);
   g.tiles_n = static_cast<int32_t>(tiles_n);
-  g.splits = splits;
+  g.splits = sk ? static_cast<int32_t>(skg.tail_ctas) : splits;  // stream-K: CTAs sharing the tail tiles
+  g.dp_tiles = sk ? static_cast<int32_t>(skg.dp_tiles) : 0;
   g.kblocks = static_cast<int32_t>(kblocks);
   g.beta = beta;
   g.ws = ctx->ws;
@@ -730,7 +852,7 @@ static int prepare(rg_ctx* ctx, int64_t M, int64_t N, int64_t K, const void* A, 
   g.timeout = ctx->timeout;
   g.stall = ctx->stall;
   const int64_t units = tiles_m * tiles_n * splits;
-  L->grid = dim3(static_cast<unsigned>(std::min<int64_t>(units, ctx->sm_count)));
+  L->grid = dim3(static_cast<unsigned>(sk ? skg.grid : std::min<int64_t>(units, ctx->sm_count)));
   return RG_OK;
 }
 
@@ -915,6 +1037,8 @@ extern "C" int rg_init(int device, int64_t workspace_bytes, rg_ctx** out) {
     const rg::TileKernel& tk = rg::tile_kernel(t);
     if ((e = cudaFuncSetAttribute(reinterpret_cast<const void*>(tk.fn), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   tk.smem)) != cudaSuccess ||
+        (e = cudaFuncSetAttribute(reinterpret_cast<const void*>(tk.sk), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  tk.smem)) != cudaSuccess ||
         (e = cudaFuncSetAttribute(reinterpret_cast<const void*>(rg::grouped_kernel(t)),
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, tk.smem)) != cudaSuccess) {
       delete ctx;
@@ -1065,12 +1189,17 @@ extern "C" int rg_sweep(rg_ctx* ctx, const rg_grid* grid, int32_t n_variants, co
     if (plan || !o.prune_splits) return false;
     const int32_t v = variant_ids[item / cells];
     const int S = rg::variant_split(v);
-    if (S == 1) return false;
+    const bool sk = rg::variant_streamk(v);
+    if (S == 1 && !sk) return false;
     int64_t M, N, K;
     dims(item, &M, &N, &K);
     const rg::TileShape ts = rg::tile_shape(rg::variant_tile(v));
     const int64_t tiles = ((M + ts.bm - 1) / ts.bm) * ((N + ts.bn - 1) / ts.bn);
     const int64_t kblocks = (K + rg::kBK - 1) / rg::kBK;
+    if (sk) {  // stream-K changes something only where whole waves leave a remainder spread over several CTAs
+      const rg::SkGeometry gsk = rg::sk_geometry(tiles, kblocks, ctx->sm_count);
+      return tiles < ctx->sm_count || gsk.tail_ctas <= tiles - gsk.dp_tiles;
+    }
     return tiles >= ctx->sm_count || kblocks < 2 * S;
   };
   if (o.prune_splits && !plan) {  // timed items first, pruned ones marked
@@ -1350,11 +1479,16 @@ extern "C" int rg_gemm_noalloc(int64_t M, int64_t N, int64_t K, const void* A, i
   if (rc != RG_OK) return rc;
   if (variant < 0 || variant >= RG_NUM_VARIANTS) return rg::fail(RG_ERR_INVALID, "rg_gemm_noalloc: variant id out of range");
   const int splits = rg::variant_split(variant);
-  if (splits > 1 && M > 0 && N > 0) {
+  if ((splits > 1 || rg::variant_streamk(variant)) && M > 0 && N > 0 && K > 0) {
     const rg::TileShape ts = rg::tile_shape(rg::variant_tile(variant));
     const int64_t tiles = ((M + ts.bm - 1) / ts.bm) * ((N + ts.bn - 1) / ts.bn);
-    const int64_t need = static_cast<int64_t>(splits) * tiles * ts.bm * ts.bn * 4;
-    if (need > rg::kNoallocPartialBytes || tiles > RG_NOALLOC_MAX_TILES)
+    int64_t slots = splits;
+    if (rg::variant_streamk(variant)) {
+      const int64_t kb = (K + rg::kBK - 1) / rg::kBK;
+      slots = rg::sk_geometry(tiles, kb, d->sm_count).max_pieces;
+    }
+    const int64_t need = slots > 1 ? slots * tiles * ts.bm * ts.bn * 4 : 0;
+    if (need > rg::kNoallocPartialBytes || (slots > 1 && tiles > RG_NOALLOC_MAX_TILES))
       return rg::fail(RG_ERR_SHAPE, "rg_gemm_noalloc: split-K needs " + std::to_string(need) +
                                         " scratch bytes and " + std::to_string(tiles) + " tiles; the fixed scratch holds " +
                                         std::to_string(rg::kNoallocPartialBytes) + " bytes and " +
@@ -1376,7 +1510,7 @@ extern "C" int rg_gemm_noalloc(int64_t M, int64_t N, int64_t K, const void* A, i
   if (!L.noop && !L.zero_only) {
     // the error word and the tickets this launch uses must start at zero
     const int64_t clear = rg::kNoallocTicketOff - rg::kNoallocErrOff +
-                          (splits > 1 ? static_cast<int64_t>(L.args.tiles_m) * L.args.tiles_n * 4 * 4 : 0);
+                          (L.ws_slots > 1 ? static_cast<int64_t>(L.args.tiles_m) * L.args.tiles_n * 4 * 4 : 0);
     e = cudaMemsetAsync(d->scratch + rg::kNoallocErrOff, 0, static_cast<size_t>(clear), st);
     if (e != cudaSuccess) return rg::cuda_fail(e, "rg_gemm_noalloc: clear tickets");
   }

@@ -38,8 +38,52 @@ struct TileShape {
   int bm, bn;
 };
 TileShape tile_shape(int tile);
-inline int variant_tile(int v) { return v / RG_NUM_SPLITS; }
-inline int variant_split(int v) { return 1 << (v % RG_NUM_SPLITS); }
+// Variant ids: tile * RG_NUM_SPLITS + log2(split) for the split-K variants, then
+// RG_VARIANT_SK(tile) for the stream-K variants.
+constexpr int kClassicVariants = RG_NUM_TILES * RG_NUM_SPLITS;
+inline bool variant_streamk(int v) { return v >= kClassicVariants; }
+inline int variant_tile(int v) { return v >= kClassicVariants ? v - kClassicVariants : v / RG_NUM_SPLITS; }
+inline int variant_split(int v) { return v >= kClassicVariants ? 1 : 1 << (v % RG_NUM_SPLITS); }
+// Stream-K geometry shared by the launcher, the sweep's pruning and the kernel:
+// whole waves of tiles run data-parallel (one tile per CTA per wave); only the
+// remainder tiles are divided among tail_ctas CTAs by K iterations (each at
+// least kSkMinIters K blocks, at most kSkMaxPieces CTAs per tile).
+constexpr int64_t kSkMinIters = 4;
+constexpr int64_t kSkMaxPieces = 4;
+struct SkGeometry {
+  int64_t grid;       // CTAs launched
+  int64_t dp_tiles;   // tiles [0, dp_tiles) run whole, tile g + i * grid on CTA g
+  int64_t tail_ctas;  // CTAs 0..tail_ctas-1 share the iterations of tiles [dp_tiles, tiles)
+  int64_t max_pieces; // most CTAs touching one tail tile (workspace slots per tile)
+};
+inline SkGeometry sk_geometry(int64_t tiles, int64_t kblocks, int64_t sms) {
+  SkGeometry g{};
+  g.dp_tiles = (tiles / sms) * sms;
+  const int64_t tail = tiles - g.dp_tiles;
+  g.grid = g.dp_tiles > 0 ? sms : 1;
+  g.max_pieces = 1;
+  g.tail_ctas = 0;
+  if (tail == 0) return g;
+  const int64_t iters = tail * kblocks;
+  int64_t c = iters / kSkMinIters;
+  if (c > tail * kSkMaxPieces) c = tail * kSkMaxPieces;
+  if (c > sms) c = sms;
+  if (c < 1) c = 1;
+  g.tail_ctas = c;
+  if (g.grid < c) g.grid = c;
+  auto begin = [&](int64_t h) { return h * iters / c; };
+  auto cta_of = [&](int64_t x) {
+    int64_t h = (x * c) / iters;
+    while (h + 1 < c && begin(h + 1) <= x) ++h;
+    while (h > 0 && begin(h) > x) --h;
+    return h;
+  };
+  for (int64_t t = 0; t < tail; ++t) {
+    const int64_t p = cta_of((t + 1) * kblocks - 1) - cta_of(t * kblocks) + 1;
+    if (p > g.max_pieces) g.max_pieces = p;
+  }
+  return g;
+}
 
 }  // namespace rg
 

@@ -31,16 +31,23 @@ RG_ERR_NO_DEVICE = -9
 RG_T_UNMEASURED = 1 << 60
 RG_NUM_TILES = 6
 RG_NUM_SPLITS = 4
-RG_NUM_VARIANTS = RG_NUM_TILES * RG_NUM_SPLITS
+RG_NUM_VARIANTS = RG_NUM_TILES * RG_NUM_SPLITS + RG_NUM_TILES
 TILES = [(128, 64), (128, 128), (128, 256), (256, 64), (256, 128), (256, 256)]
 SPLITS = [1, 2, 4, 8]
+SK = "SK"
 
 
-def variant(tile: int, split: int = 1) -> int:
+def variant(tile: int, split=1) -> int:
+    """Variant id of a tile with split factor 1/2/4/8, or split="SK" for stream-K."""
+    if split == SK:
+        return RG_NUM_TILES * RG_NUM_SPLITS + tile
     return tile * RG_NUM_SPLITS + SPLITS.index(split)
 
 
 def variant_name(v: int) -> str:
+    if v >= RG_NUM_TILES * RG_NUM_SPLITS:
+        bm, bn = TILES[v - RG_NUM_TILES * RG_NUM_SPLITS]
+        return f"{bm}x{bn}/SK"
     bm, bn = TILES[v // RG_NUM_SPLITS]
     return f"{bm}x{bn}/S{SPLITS[v % RG_NUM_SPLITS]}"
 

@@ -11,7 +11,7 @@ from oracle import gemm as og
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-ALL_VARIANTS = list(range(24))
+ALL_VARIANTS = list(range(30))          # 24 split-K variants, then 6 stream-K
 
 
 @pytest.fixture(scope="module")
@@ -126,7 +126,7 @@ def test_beta_one_accumulates(rg, ctx, v):
     check(run(rg, ctx, a, b, v, beta=1, c0=c0), a, b, c0=c0)
 
 
-@pytest.mark.parametrize("v", [1, 2, 3, 7, 11, 15, 19, 23])
+@pytest.mark.parametrize("v", [1, 2, 3, 7, 11, 15, 19, 23, 24, 25, 26, 27, 28, 29])
 def test_split_k_deterministic(rg, ctx, v):
     M, N, K = 512, 384, 2048
     a, b = synthetic.operands_bf16(M, N, K, seed=7)
@@ -180,3 +180,24 @@ def test_alignment_and_argument_errors(rg, ctx):
     assert rg.rg_gemm_status(ctx, 64, 64, 64, A, 64, A, 64, C, 64, 1, 0, 32) == rg.RG_ERR_INVALID
     assert rg.rg_gemm_status(ctx, 64, 64, 64, A, 32, A, 64, C, 64, 1) == rg.RG_ERR_INVALID
     rg.rg_check(ctx)
+
+
+@pytest.mark.parametrize("tile", range(6))
+@pytest.mark.parametrize("shape", [(1664, 1664, 2048), (2176, 1920, 1152), (128, 128, 4096), (256, 512, 640)])
+def test_stream_k_uneven_waves(rg, ctx, tile, shape):
+    """Stream-K on shapes whose tile count is just above a wave, or far below the SM count: every tile
+    spans one or several CTAs' iteration ranges; the result is within the bound and deterministic."""
+    M, N, K = shape
+    a, b = synthetic.operands_bf16(M, N, K, seed=12)
+    v = rg.variant(tile, rg.SK)
+    c1 = run(rg, ctx, a, b, v)
+    check(c1, a, b)
+    assert np.array_equal(c1, run(rg, ctx, a, b, v))
+
+
+@pytest.mark.parametrize("v", [24, 27, 29])
+def test_stream_k_beta_one(rg, ctx, v):
+    M, N, K = 640, 384, 1536
+    a, b = synthetic.operands_bf16(M, N, K, seed=13)
+    c0 = synthetic.normal_stream_f32(13, 5, M * N).reshape(M, N)
+    check(run(rg, ctx, a, b, v, beta=1, c0=c0), a, b, c0=c0)

@@ -33,6 +33,7 @@ def _dev_bf16(bits):
     ((300, 200, 328), 21, 0),        # 256x256, split 2, ragged
     ((384, 512, 1024), 14, 1),       # 256x64, split 4, beta = 1
     ((2048, 1536, 1024), 8, 0),      # 128x256, split 1
+    ((640, 512, 2048), 25, 0),       # 128x128, stream-K
 ])
 def test_matches_rg_gemm_twice(rg, shape, v, beta):
     M, N, K = shape
