@@ -154,6 +154,27 @@ def dist_setup():
     return world, rank, local
 
 
+def max_over_ranks(value: float, dist=None, device=None) -> float:
+    """The maximum of a per-rank value over all ranks (the slowest replica's step time); the
+    value itself without a process group."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def mean_over_ranks(value: float, dist=None, device=None) -> float:
+    """The mean of a per-rank value over all ranks (replicas each measure the whole landscape)."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item()) / dist.get_world_size()
+
+
 def stats_of(rg, grid, t_ns):
     tf, r, mean = rg.rg_surface_stats(grid, t_ns)
     return tf, r, mean
@@ -325,15 +346,11 @@ def main():
     if dist:
         dist.barrier()
     n_launch = rg.rg_launch_count(ctx) - n_launch0
-    step_ms = ev0.elapsed_time(ev1) / args.steps
-    if dist:
-        t = torch.tensor([step_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        step_ms = float(t.item())
+    step_ms = max_over_ranks(ev0.elapsed_time(ev1) / args.steps, dist, dev)
 
     plain = [summarize(*stats_of(rg, grid, tp)) for tp, _ in results]
     smooth = [summarize(*stats_of(rg, grid, ts)) for _, ts in results]
-    value = float(np.mean([s["mean_tflops"] for s in smooth]))
+    value = mean_over_ranks(float(np.mean([s["mean_tflops"] for s in smooth])), dist, dev)
     last_p, last_s = results[-1]
     agg_flops = float(flops.sum())
     agg_smooth = agg_flops / (last_s.astype(np.float64).sum() * 1e-9) / 1e12
