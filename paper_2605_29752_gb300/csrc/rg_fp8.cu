@@ -6,15 +6,16 @@
 //   B ~ qB (K x N e4m3, row-major) with sB[K/128][N/128],
 //   C[i][j] = sum_kb sA[i/128][kb] * sB[kb][j/128] * sum_{k in kb} qA[i][k] qB[k][j].
 //
-// Kernel (one CTA per SM, persistent over 128 x 128 output tiles):
+// Kernel (one CTA per SM, persistent over 128 x 256 output tiles):
 //   warp 0     TMA producer: A block 128 x 128 bytes (K-major) and B block 128 K-rows
-//              x 128 bytes (N-major), 128-byte swizzle, ring of stages.
-//   warp 1     one thread issues tcgen05.mma kind::f8f6f4 (M = N = 128, K = 32) into
-//              one of four TMEM buffers, a fresh accumulator per 128-deep K block.
-//   warps 2-5  promotion and epilogue: per K block, tcgen05.ld the block product,
-//              multiply by sA * sB (one scalar per tile and K block, since tiles and
-//              scale blocks coincide) and add into FP32 registers (one row per thread);
-//              after the last block, 128B-swizzled staging and TMA store.
+//              x 256 bytes (N-major, two 128-byte-wide halves), 128-byte swizzle.
+//   warp 1     one thread issues tcgen05.mma kind::f8f6f4 (M = 128, N = 256, K = 32) into
+//              one of two TMEM buffers, a fresh accumulator per 128-deep K block.
+//   warps 2-9  promotion and epilogue, two warps per TMEM lane quarter, each owning one
+//              128-column half (= one scale block column): per K block, tcgen05.ld the
+//              block product, multiply by sA * sB (one scalar per warp and K block) and
+//              add into FP32 registers (half a row per thread); after the last block,
+//              128B-swizzled staging and TMA store.
 // Every mbarrier wait is bounded; on expiry the kernel records an error code,
 // lets its in-flight copies land, releases TMEM and returns.
 #include <cuda.h>
@@ -32,17 +33,19 @@ namespace rg {
 
 namespace fp8 {
 
-constexpr int kThreads = 192;
-constexpr int BM = 128, BN = 128, BK = 128;  // BK: one 128-byte swizzle row of e4m3 = one scale block
-constexpr int STAGES = 6;
+constexpr int kEpiWarps = 8;                  // two promotion warps per TMEM lane quarter
+constexpr int kThreads = 32 * (2 + kEpiWarps);
+constexpr int BM = 128, BN = 256, BK = 128;  // BK: one 128-byte swizzle row of e4m3 = one scale block
+constexpr int SB = 128;                      // scale block edge
+constexpr int STAGES = 3;
 constexpr int A_BYTES = BM * BK;
-constexpr int B_BYTES = BK * BN;
+constexpr int B_BYTES = BK * BN;             // two 128-column N-major halves of BK rows
 constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
-constexpr int NACC = 4;                       // TMEM buffers of 128 columns
+constexpr int NACC = 2;                       // TMEM buffers of BN columns
 constexpr int TMEM_COLS = 512;
 constexpr int STAGING_PER_WARP = 2 * 4096;
 constexpr int STAGING_OFF = STAGES * STAGE_BYTES;
-constexpr int BAR_OFF = STAGING_OFF + 4 * STAGING_PER_WARP;
+constexpr int BAR_OFF = STAGING_OFF + kEpiWarps * STAGING_PER_WARP;
 constexpr int SMEM_BYTES = 1024 + BAR_OFF + 256;
 constexpr uint32_t IDESC = instr_desc(0, 0, 0, 1, 128, BN);  // E4M3 x E4M3, A K-major, B MN-major
 constexpr long long kDrainCycles = 1LL << 30;
@@ -97,7 +100,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     for (int b = 0; b < NACC; ++b) {
       mbar_init(tfull_bar(b), 1);
-      mbar_init(tempty_bar(b), 4);
+      mbar_init(tempty_bar(b), kEpiWarps);
     }
     mbar_init(drain_bar, 1);
     *abort_flag = 0;
@@ -129,7 +132,9 @@ __global__ void __launch_bounds__(kThreads, 1)
           const uint32_t sa = sbase + stage * STAGE_BYTES;
           mbar_arrive_expect_tx(full_bar(stage), STAGE_BYTES);
           tma_load_2d(sa, &tmA, full_bar(stage), kb * BK, tm * BM);
-          tma_load_2d(sa + A_BYTES, &tmB, full_bar(stage), tn * BN, kb * BK);
+#pragma unroll
+          for (int j = 0; j < BN / 128; ++j)
+            tma_load_2d(sa + A_BYTES + j * (BK * 128), &tmB, full_bar(stage), tn * BN + j * 128, kb * BK);
           issued_mask |= 1u << stage;
           issued_ph = (issued_ph & ~(1u << stage)) | (ph << stage);
           if (++stage == STAGES) {
@@ -163,7 +168,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
           for (int k = 0; k < BK / 32; ++k) {
             const uint64_t adesc = smem_desc_sw128(sa + k * 32, 16, 1024);
-            const uint64_t bdesc = smem_desc_sw128(sb + k * (32 * 128), BK * 128, 1024);
+            const uint64_t bdesc = smem_desc_sw128(sb + k * (32 * 128), BK * 128, 1024);  // halves BK*128 apart
             mma_f8(d, adesc, bdesc, IDESC, k > 0 ? 1u : 0u);
           }
           mma_commit(empty_bar(stage));
@@ -190,24 +195,30 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_wait(drain_bar, 0, kDrainCycles, no_abort);
     }
   } else {
+    // promotion warps 2..9: lane quarter q (the TMEM lanes this warp may read), column half hc
+    const int e = warp - 2;
     const int q = warp & 3;
-    const uint32_t stg0 = sbase + STAGING_OFF + (warp - 2) * STAGING_PER_WARP;
+    const int hc = e / 4;
+    const uint32_t stg0 = sbase + STAGING_OFF + e * STAGING_PER_WARP;
     int acc = 0, sbuf = 0;
     uint32_t aph = 0;
     bool ok = true;
     for (int u = blockIdx.x; ok && u < total; u += gridDim.x) {
       const int tm = u / args.tiles_n, tn = u % args.tiles_n;
-      float r[BN];
+      const int nb = tn * (BN / SB) + hc;  // this half's scale block column
+      float r[BN / 2];
 #pragma unroll
-      for (int i = 0; i < BN; ++i) r[i] = 0.f;
+      for (int i = 0; i < BN / 2; ++i) r[i] = 0.f;
       for (int kb = 0; kb < args.kblocks; ++kb) {
-        const float s = args.sA[static_cast<size_t>(tm) * args.sa_ld + kb] * args.sB[static_cast<size_t>(kb) * args.sb_ld + tn];
+        const float s = nb < args.sb_ld ? args.sA[static_cast<size_t>(tm) * args.sa_ld + kb] *
+                                              args.sB[static_cast<size_t>(kb) * args.sb_ld + nb]
+                                        : 0.f;
         ok = __all_sync(FULL, mbar_wait(tfull_bar(acc), aph, args.timeout, abort_flag));
         if (!ok) break;
         tc_fence_after();
-        const uint32_t t = tmem_base + (static_cast<uint32_t>(q * 32) << 16) + static_cast<uint32_t>(acc * BN);
+        const uint32_t t = tmem_base + (static_cast<uint32_t>(q * 32) << 16) + static_cast<uint32_t>(acc * BN + hc * 128);
 #pragma unroll
-        for (int c = 0; c < BN / 32; ++c) {
+        for (int c = 0; c < 4; ++c) {
           uint32_t p[32];
           tmem_ld_32x32b_x32(t + c * 32, p);
           tmem_ld_wait();
@@ -225,8 +236,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (!ok) break;
       const int row0 = tm * BM + q * 32;
 #pragma unroll
-      for (int c = 0; c < BN / 32; ++c) {
-        const int col0 = tn * BN + c * 32;
+      for (int c = 0; c < 4; ++c) {
+        const int col0 = tn * BN + hc * 128 + c * 32;
         if (row0 >= args.M || col0 >= args.N) continue;
         if (lane == 0) bulk_wait_read<1>();
         __syncwarp();
@@ -248,7 +259,9 @@ __global__ void __launch_bounds__(kThreads, 1)
       atomicExch(args.err, 3);
       *abort_flag = 1;
     }
-    if (lane == 0) bulk_wait<0>();
+    // the staging buffers must have been read before the CTA exits; the global writes
+    // themselves complete with the grid (a dependent grid's griddepcontrol.wait sees them)
+    if (lane == 0) bulk_wait_read<0>();
     __syncwarp();
   }
   __syncthreads();
@@ -336,7 +349,7 @@ extern "C" int rg_gemm_fp8(rg_ctx* ctx, int64_t M, int64_t N, int64_t K, const u
   if (rc != RG_OK) return rc;
   CUtensorMap a, b, c;
   rc = rg::fp8_make_map(&a, CU_TENSOR_MAP_DATA_TYPE_UINT8, qA, K, M, lda, BK, BM);
-  if (rc == RG_OK) rc = rg::fp8_make_map(&b, CU_TENSOR_MAP_DATA_TYPE_UINT8, qB, N, K, ldb, BN, BK);
+  if (rc == RG_OK) rc = rg::fp8_make_map(&b, CU_TENSOR_MAP_DATA_TYPE_UINT8, qB, N, K, ldb, 128, BK);
   if (rc == RG_OK) rc = rg::fp8_make_map(&c, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, C, N, M, ldc * 4, 32, 32);
   if (rc != RG_OK) return rc;
   Args args{};
@@ -346,7 +359,7 @@ extern "C" int rg_gemm_fp8(rg_ctx* ctx, int64_t M, int64_t N, int64_t K, const u
   args.tiles_n = static_cast<int32_t>((N + BN - 1) / BN);
   args.kblocks = static_cast<int32_t>((K + BK - 1) / BK);
   args.sa_ld = args.kblocks;
-  args.sb_ld = args.tiles_n;
+  args.sb_ld = static_cast<int32_t>((N + SB - 1) / SB);
   args.sA = sA;
   args.sB = sB;
   args.err = err;
@@ -414,7 +427,7 @@ extern "C" int rg_sweep_fp8(rg_ctx* ctx, const rg_grid* grid, const uint8_t* qA,
     const int64_t M = rg::axis_value(grid->m, a), N = rg::axis_value(grid->n, b), K = rg::axis_value(grid->k, c);
     if ((K % 16) || (N % 16)) return rg::fail(RG_ERR_ALIGN, "rg_sweep_fp8: grid sizes must be multiples of 16");
     int r = rg::fp8_make_map(&ma, CU_TENSOR_MAP_DATA_TYPE_UINT8, qA, K, M, K, BK, BM);
-    if (r == RG_OK) r = rg::fp8_make_map(&mb, CU_TENSOR_MAP_DATA_TYPE_UINT8, qB, N, K, N, BN, BK);
+    if (r == RG_OK) r = rg::fp8_make_map(&mb, CU_TENSOR_MAP_DATA_TYPE_UINT8, qB, N, K, N, 128, BK);
     if (r == RG_OK) r = rg::fp8_make_map(&mc, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, C, N, M, N * 4, 32, 32);
     if (r != RG_OK) return r;
     args.M = static_cast<int32_t>(M);
@@ -423,7 +436,7 @@ extern "C" int rg_sweep_fp8(rg_ctx* ctx, const rg_grid* grid, const uint8_t* qA,
     args.tiles_n = static_cast<int32_t>((N + BN - 1) / BN);
     args.kblocks = static_cast<int32_t>((K + BK - 1) / BK);
     args.sa_ld = args.kblocks;
-    args.sb_ld = args.tiles_n;
+    args.sb_ld = static_cast<int32_t>((N + SB - 1) / SB);
     args.sA = sA;
     args.sB = sB;
     args.err = err;

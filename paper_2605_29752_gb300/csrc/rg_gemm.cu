@@ -614,7 +614,9 @@ __device__ __forceinline__ void gemm_body(Sched& sched, float* ws, int32_t* tick
       atomicExch(err, kErrEpilogue);
       *abort_flag = 1;
     }
-    if (lane == 0) bulk_wait<0>();
+    // the staging buffers must have been read before the CTA exits; the global writes
+    // themselves complete with the grid (a dependent grid's griddepcontrol.wait sees them)
+    if (lane == 0) bulk_wait_read<0>();
     __syncwarp();
   }
 

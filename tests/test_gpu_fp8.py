@@ -126,3 +126,19 @@ def test_gemm_fp8_alignment_errors(rg, ctx):
     with pytest.raises(rg.RGError) as e:
         rg.rg_gemm_fp8(ctx, 64, 64, 40, q, 40, s, q, 64, s, C, 64)
     assert e.value.code == rg.RG_ERR_ALIGN
+
+
+def test_fp8_sweep_small_grid(rg, ctx):
+    """rg_sweep_fp8 times every cell of a grid (here {256, 512}^3) and the surface statistics accept it."""
+    Mx = 512
+    x = synthetic.normal_stream_f32(0, 1, Mx * Mx).reshape(Mx, Mx)
+    qa, sa = quantize(rg, ctx, x)
+    qb, sb = quantize(rg, ctx, x)
+    C = torch.zeros(Mx * Mx, device="cuda")
+    g = rg.make_grid((256, 256, 2))
+    opts = rg.rg_sweep_opts_default()
+    opts.reps = 2
+    t = rg.rg_sweep_fp8(ctx, g, qa, sa, qb, sb, C, opts)
+    assert t.shape == (8,) and np.all(t > 0) and np.all(t < 10 ** 8)
+    tf, r, mean = rg.rg_surface_stats(g, t)
+    assert mean > 0 and np.all(tf > 0)
