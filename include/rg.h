@@ -55,8 +55,9 @@ enum {
 
 /* ---- kernel variants ----
  * Six output tiles (BM x BN), each with an in-kernel split-K factor S in
- * {1, 2, 4, 8} (id = tile * RG_NUM_SPLITS + log2(S)) and a stream-K
- * schedule (id = RG_VARIANT_SK(tile)).  Ties in best-of selection go to the
+ * {1, 2, 4, 8} (id = tile * RG_NUM_SPLITS + log2(S)), a stream-K
+ * schedule (id = RG_VARIANT_SK(tile)) and a 2-CTA multicast pair
+ * (id = RG_VARIANT_PAIR(tile)).  Ties in best-of selection go to the
  * lowest id.                                                   (Sec. 6.1, 6.4) */
 enum {
   RG_TILE_128x64 = 0, RG_TILE_128x128 = 1, RG_TILE_128x256 = 2,
@@ -70,7 +71,12 @@ enum {
  * (each CTA at least 4 K blocks); a tile whose iterations span several CTAs is
  * summed by its last arriving piece in the fixed order of their K ranges. */
 #define RG_VARIANT_SK(tile) (RG_NUM_TILES * RG_NUM_SPLITS + (tile))
-#define RG_NUM_VARIANTS (RG_NUM_TILES * RG_NUM_SPLITS + RG_NUM_TILES)
+/* Pair variant of a tile (ids 30..35): 2-CTA clusters on neighbouring output
+ * tiles that share one operand tile (B for tiles with BN >= BM, pairs along M;
+ * A otherwise, pairs along N); each CTA loads half of the shared tile and TMA
+ * multicasts it to both, halving that operand's L2 reads. */
+#define RG_VARIANT_PAIR(tile) (RG_NUM_TILES * RG_NUM_SPLITS + RG_NUM_TILES + (tile))
+#define RG_NUM_VARIANTS (RG_NUM_TILES * RG_NUM_SPLITS + 2 * RG_NUM_TILES)
 
 typedef struct rg_ctx rg_ctx;
 typedef struct rg_plan rg_plan;

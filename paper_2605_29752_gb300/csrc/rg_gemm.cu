@@ -169,6 +169,8 @@ __device__ __forceinline__ Unit split_unit(const CUtensorMap* a, const CUtensorM
 // One problem whose tensor maps are kernel parameters (rg_gemm).
 struct SingleSched {
   static constexpr bool kMapsInGlobal = false;
+  static constexpr int kMulticast = 0;
+  static constexpr int rank = 0;
   const CUtensorMap* a;
   const CUtensorMap* b;
   const CUtensorMap* c;
@@ -202,6 +204,8 @@ struct SingleSched {
 // slot = segment * ntiles + tile).  So no wave is left partly idle.
 struct StreamKSched {
   static constexpr bool kMapsInGlobal = false;
+  static constexpr int kMulticast = 0;
+  static constexpr int rank = 0;
   const CUtensorMap* a;
   const CUtensorMap* b;
   const CUtensorMap* c;
@@ -275,6 +279,63 @@ struct StreamKSched {
   }
 };
 
+// Pairs of CTAs (2-CTA clusters) on neighbouring output tiles that share one
+// operand: MODE 1 pairs tiles (2p, n) and (2p+1, n), which read the same B
+// tile; MODE 2 pairs tiles (m, 2p) and (m, 2p+1), which read the same A tile.
+// Each CTA of the pair loads half of the shared tile (half of its rows) and
+// multicasts it to both, so the pair reads that operand from L2 once.  A CTA
+// whose tile falls outside the problem still loads and computes (zero-filled
+// reads) so that its partner's pipeline is fed; its stores are dropped.
+template <int MODE>
+struct PairSched {
+  static constexpr bool kMapsInGlobal = false;
+  static constexpr int kMulticast = MODE;
+  const CUtensorMap* a;
+  const CUtensorMap* b;
+  const CUtensorMap* c;
+  const CUtensorMap* w;
+  int tiles_m, tiles_n, kblocks, M, N, beta;
+  int rank = 0, cid = 0, ncl = 1, pairs = 0, pn_count = 1;
+  __device__ __forceinline__ void prefetch() const {
+    prefetch_tmap(a);
+    prefetch_tmap(b);
+    prefetch_tmap(c);
+  }
+  __device__ __forceinline__ void init() {
+    rank = static_cast<int>(cluster_ctarank());
+    cid = static_cast<int>(blockIdx.x) / 2;
+    ncl = static_cast<int>(gridDim.x) / 2;
+    pn_count = MODE == 1 ? tiles_n : (tiles_n + 1) / 2;
+    pairs = (MODE == 1 ? (tiles_m + 1) / 2 : tiles_m) * pn_count;
+  }
+  __device__ __forceinline__ int count() const { return cid < pairs ? (pairs - 1 - cid) / ncl + 1 : 0; }
+  __device__ __forceinline__ Unit unit(int i) const {
+    const int p = cid + i * ncl;
+    Unit x;
+    x.a = a;
+    x.b = b;
+    x.c = c;
+    x.w = w;
+    if (MODE == 1) {
+      x.tm = 2 * (p / pn_count) + rank;
+      x.tn = p % pn_count;
+    } else {
+      x.tm = p / pn_count;
+      x.tn = 2 * (p % pn_count) + rank;
+    }
+    x.kb0 = 0;
+    x.kb1 = kblocks;
+    x.splits = 1;
+    x.s = 0;
+    x.M = M;
+    x.N = N;
+    x.beta = beta;
+    x.ntiles = tiles_m * tiles_n;
+    x.tile = x.tm * tiles_n + x.tn;
+    return x;
+  }
+};
+
 // Many problems in one launch (rg_gemm_grouped): a device-resident work list
 // whose header gives the item count and the total tile count; the units are the
 // concatenation of every item's tiles (item i owns units [tile_start, tile_start
@@ -293,6 +354,8 @@ struct alignas(64) GroupHeader {
 
 struct GroupSched {
   static constexpr bool kMapsInGlobal = true;
+  static constexpr int kMulticast = 0;
+  static constexpr int rank = 0;
   const GroupHeader* h;
   const GroupItem* items;
   int n_items, total_tiles;  // read after the grid dependency wait
@@ -346,7 +409,8 @@ __device__ __forceinline__ void gemm_body(Sched& sched, float* ws, int32_t* tick
     sched.prefetch();
     for (int i = 0; i < STAGES; ++i) {
       mbar_init(full_bar(i), 1);
-      mbar_init(empty_bar(i), 1);
+      // a stage is free once every CTA that writes into it (multicast) has consumed it
+      mbar_init(empty_bar(i), Sched::kMulticast ? 2 : 1);
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(tfull_bar(b), 1);
@@ -362,6 +426,7 @@ __device__ __forceinline__ void gemm_body(Sched& sched, float* ws, int32_t* tick
   }
   tc_fence_before();
   __syncthreads();
+  if constexpr (Sched::kMulticast != 0) cluster_sync();  // the partner's barriers are initialised
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
   // Everything above overlaps the previous grid in the stream; nothing below
@@ -392,10 +457,21 @@ __device__ __forceinline__ void gemm_body(Sched& sched, float* ws, int32_t* tick
           const uint32_t sa = sbase + stage * C::STAGE_BYTES;
           const uint32_t sb = sa + C::A_BYTES;
           mbar_arrive_expect_tx(full_bar(stage), C::STAGE_BYTES);
-          tma_load_2d(sa, w.a, full_bar(stage), kb * kBK, w.tm * BM);
+          if constexpr (Sched::kMulticast == 2) {  // A shared: this CTA's half of the rows, to both
+            tma_load_2d_multicast(sa + sched.rank * (BM / 2) * 128, w.a, full_bar(stage), kb * kBK,
+                                  w.tm * BM + sched.rank * (BM / 2), 3);
+          } else {
+            tma_load_2d(sa, w.a, full_bar(stage), kb * kBK, w.tm * BM);
+          }
 #pragma unroll
-          for (int j = 0; j < BN / 64; ++j)
-            tma_load_2d(sb + j * (kBK * 128), w.b, full_bar(stage), w.tn * BN + j * 64, kb * kBK);
+          for (int j = 0; j < BN / 64; ++j) {
+            if constexpr (Sched::kMulticast == 1) {  // B shared: this CTA's half of the K rows, to both
+              tma_load_2d_multicast(sb + j * (kBK * 128) + sched.rank * (kBK / 2) * 128, w.b, full_bar(stage),
+                                    w.tn * BN + j * 64, kb * kBK + sched.rank * (kBK / 2), 3);
+            } else {
+              tma_load_2d(sb + j * (kBK * 128), w.b, full_bar(stage), w.tn * BN + j * 64, kb * kBK);
+            }
+          }
           issued_mask |= 1u << stage;
           issued_ph = (issued_ph & ~(1u << stage)) | (ph << stage);
           if (++stage == STAGES) {
@@ -441,7 +517,10 @@ __device__ __forceinline__ void gemm_body(Sched& sched, float* ws, int32_t* tick
               mma_f16(d0 + h * BN, adesc, bdesc, C::IDESC, (kb > kb0 || k > 0) ? 1u : 0u);
             }
           }
-          mma_commit(empty_bar(stage));
+          if constexpr (Sched::kMulticast != 0)
+            mma_commit_multicast(empty_bar(stage), 3);  // releases the stage in both CTAs of the pair
+          else
+            mma_commit(empty_bar(stage));
         }
         __syncwarp();
         if (++stage == STAGES) {
@@ -621,6 +700,8 @@ __device__ __forceinline__ void gemm_body(Sched& sched, float* ws, int32_t* tick
   }
 
   __syncthreads();
+  // no CTA of a pair exits while its partner may still multicast into it or arrive on its barriers
+  if constexpr (Sched::kMulticast != 0) cluster_sync();
   if (warp == 1) {
     tc_fence_after();
     tmem_dealloc(tmem_base, C::TMEM_COLS);
@@ -645,6 +726,15 @@ __global__ void __launch_bounds__(kThreads, 1)
                              const GemmArgs args) {
   StreamKSched sched{&tmA,        &tmB,   &tmC,   &tmW,      args.tiles_m, args.tiles_n, args.kblocks,
                      args.M,      args.N, args.beta, args.splits /* CTAs sharing the tail */, args.dp_tiles};
+  gemm_body<BM, BN, STAGES>(sched, args.ws, args.tickets, args.err, args.timeout, args.stall);
+}
+
+template <int BM, int BN, int STAGES, int MODE>
+__global__ void __launch_bounds__(kThreads, 1)
+    gemm_bf16_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                          const __grid_constant__ CUtensorMap tmC, const __grid_constant__ CUtensorMap tmW,
+                          const GemmArgs args) {
+  PairSched<MODE> sched{&tmA, &tmB, &tmC, &tmW, args.tiles_m, args.tiles_n, args.kblocks, args.M, args.N, args.beta};
   gemm_body<BM, BN, STAGES>(sched, args.ws, args.tickets, args.err, args.timeout, args.stall);
 }
 
@@ -673,14 +763,18 @@ using KernFn = void (*)(const CUtensorMap, const CUtensorMap, const CUtensorMap,
 
 struct TileKernel {
   KernFn fn;
-  KernFn sk;  // stream-K instance of the same tile
+  KernFn sk;    // stream-K instance of the same tile
+  KernFn pair;  // 2-CTA cluster instance sharing one operand by multicast
+  int pair_mode;  // 1: pairs along M share B; 2: pairs along N share A
   int bm, bn, smem;
 };
 
+// The pair shares whichever operand tile is larger per K block (B when BN >= BM).
 template <int BM, int BN, int ST>
 TileKernel make_tile_kernel() {
-  return TileKernel{gemm_bf16_kernel<BM, BN, ST>, gemm_bf16_streamk_kernel<BM, BN, ST>, BM, BN,
-                    KCfg<BM, BN, ST>::SMEM_BYTES};
+  constexpr int mode = BN >= BM ? 1 : 2;
+  return TileKernel{gemm_bf16_kernel<BM, BN, ST>, gemm_bf16_streamk_kernel<BM, BN, ST>,
+                    gemm_bf16_pair_kernel<BM, BN, ST, mode>, mode, BM, BN, KCfg<BM, BN, ST>::SMEM_BYTES};
 }
 
 using GroupedFn = void (*)(const GroupHeader*, const GroupItem*, int32_t*, long long);
@@ -765,6 +859,7 @@ struct Launch {
   bool zero_only = false;  // K == 0 with beta == 0: C = 0
   bool noop = false;
   int64_t ws_slots = 1;  // > 1: the launch uses the split-K workspace and tickets
+  int cluster = 1;       // 2: launched as 2-CTA clusters
   float* C = nullptr;
   int64_t M = 0, N = 0, ldc = 0;
 };
@@ -807,6 +902,7 @@ static int prepare(rg_ctx* ctx, int64_t M, int64_t N, int64_t K, const void* A, 
   if (rc != RG_OK) return rc;
   const int tile = variant_tile(variant);
   const bool sk = variant_streamk(variant);
+  const bool pair = variant_pair(variant);
   const int splits = variant_split(variant);
   const TileKernel& tk = tile_kernel(tile);
   const int64_t tiles_m = (pm + tk.bm - 1) / tk.bm;
@@ -825,8 +921,11 @@ static int prepare(rg_ctx* ctx, int64_t M, int64_t N, int64_t K, const void* A, 
     if (need > ctx->ws_bytes || tiles_m * tiles_n * 4 > kMaxTickets)
       return fail(RG_ERR_SHAPE, "split-K workspace too small for this shape");
   }
-  rc = make_map(&L->a, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, A, K, M, lda * 2, kBK, tk.bm);
-  if (rc == RG_OK) rc = make_map(&L->b, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, B, N, K, ldb * 2, 64, kBK);
+  // pairs load the shared operand as two half boxes (half its rows each)
+  const bool half_a = pair && tk.pair_mode == 2, half_b = pair && tk.pair_mode == 1;
+  rc = make_map(&L->a, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, A, K, M, lda * 2, kBK, half_a ? tk.bm / 2 : tk.bm);
+  if (rc == RG_OK)
+    rc = make_map(&L->b, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, B, N, K, ldb * 2, 64, half_b ? kBK / 2 : kBK);
   if (rc == RG_OK) rc = make_map(&L->c, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, C, N, M, ldc * 4, 32, 32);
   if (rc == RG_OK) {
     if (uses_ws)  // workspace rows: [slot][tile][BM], BN floats each
@@ -836,7 +935,8 @@ static int prepare(rg_ctx* ctx, int64_t M, int64_t N, int64_t K, const void* A, 
       L->w = L->c;  // unused without split-K
   }
   if (rc != RG_OK) return rc;
-  L->fn = sk ? tk.sk : tk.fn;
+  L->fn = sk ? tk.sk : pair ? tk.pair : tk.fn;
+  L->cluster = pair ? 2 : 1;
   L->smem = tk.smem;
   L->ws_slots = slots;
   GemmArgs& g = L->args;
@@ -854,7 +954,12 @@ static int prepare(rg_ctx* ctx, int64_t M, int64_t N, int64_t K, const void* A, 
   g.timeout = ctx->timeout;
   g.stall = ctx->stall;
   const int64_t units = tiles_m * tiles_n * splits;
-  L->grid = dim3(static_cast<unsigned>(sk ? skg.grid : std::min<int64_t>(units, ctx->sm_count)));
+  if (pair) {  // 2-CTA clusters, one per pair of tiles, at most one CTA per SM
+    const int64_t pairs = tk.pair_mode == 1 ? ((tiles_m + 1) / 2) * tiles_n : tiles_m * ((tiles_n + 1) / 2);
+    L->grid = dim3(static_cast<unsigned>(2 * std::min<int64_t>(pairs, ctx->sm_count / 2)));
+  } else {
+    L->grid = dim3(static_cast<unsigned>(sk ? skg.grid : std::min<int64_t>(units, ctx->sm_count)));
+  }
   return RG_OK;
 }
 
@@ -867,16 +972,20 @@ static cudaError_t launch(rg_ctx* ctx, const Launch& L, cudaStream_t st) {
   // Programmatic dependent launch: the grid may be scheduled while the previous
   // grid in the stream finishes; the kernel waits (griddepcontrol.wait) before
   // its first global memory access.
-  cudaLaunchAttribute attr[1];
+  cudaLaunchAttribute attr[2];
   attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
   attr[0].val.programmaticStreamSerializationAllowed = 1;
+  attr[1].id = cudaLaunchAttributeClusterDimension;
+  attr[1].val.clusterDim.x = static_cast<unsigned>(L.cluster);
+  attr[1].val.clusterDim.y = 1;
+  attr[1].val.clusterDim.z = 1;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = L.grid;
   cfg.blockDim = dim3(kThreads);
   cfg.dynamicSmemBytes = static_cast<size_t>(L.smem);
   cfg.stream = st;
   cfg.attrs = attr;
-  cfg.numAttrs = 1;
+  cfg.numAttrs = L.cluster > 1 ? 2 : 1;
   return cudaLaunchKernelExC(&cfg, reinterpret_cast<const void*>(L.fn), params);
 }
 
@@ -1041,6 +1150,8 @@ extern "C" int rg_init(int device, int64_t workspace_bytes, rg_ctx** out) {
                                   tk.smem)) != cudaSuccess ||
         (e = cudaFuncSetAttribute(reinterpret_cast<const void*>(tk.sk), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   tk.smem)) != cudaSuccess ||
+        (e = cudaFuncSetAttribute(reinterpret_cast<const void*>(tk.pair), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  tk.smem)) != cudaSuccess ||
         (e = cudaFuncSetAttribute(reinterpret_cast<const void*>(rg::grouped_kernel(t)),
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, tk.smem)) != cudaSuccess) {
       delete ctx;
@@ -1192,6 +1303,12 @@ extern "C" int rg_sweep(rg_ctx* ctx, const rg_grid* grid, int32_t n_variants, co
     const int32_t v = variant_ids[item / cells];
     const int S = rg::variant_split(v);
     const bool sk = rg::variant_streamk(v);
+    if (rg::variant_pair(v)) {  // a pair needs a partner tile
+      int64_t M, N, K;
+      dims(item, &M, &N, &K);
+      const rg::TileShape ts = rg::tile_shape(rg::variant_tile(v));
+      return ((M + ts.bm - 1) / ts.bm) * ((N + ts.bn - 1) / ts.bn) < 2;
+    }
     if (S == 1 && !sk) return false;
     int64_t M, N, K;
     dims(item, &M, &N, &K);
@@ -1454,8 +1571,10 @@ static int noalloc_setup(int dev, NoallocDevice** out) {
     if (rc != RG_OK) return rc;
     for (int t = 0; t < RG_NUM_TILES; ++t) {
       const TileKernel& tk = tile_kernel(t);
-      e = cudaFuncSetAttribute(reinterpret_cast<const void*>(tk.fn), cudaFuncAttributeMaxDynamicSharedMemorySize, tk.smem);
-      if (e != cudaSuccess) return cuda_fail(e, "rg_gemm_noalloc: shared-memory attribute");
+      for (KernFn fn : {tk.fn, tk.sk, tk.pair}) {
+        e = cudaFuncSetAttribute(reinterpret_cast<const void*>(fn), cudaFuncAttributeMaxDynamicSharedMemorySize, tk.smem);
+        if (e != cudaSuccess) return cuda_fail(e, "rg_gemm_noalloc: shared-memory attribute");
+      }
     }
     void* ptr = nullptr;
     e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);

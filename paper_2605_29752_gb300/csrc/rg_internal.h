@@ -41,8 +41,12 @@ TileShape tile_shape(int tile);
 // Variant ids: tile * RG_NUM_SPLITS + log2(split) for the split-K variants, then
 // RG_VARIANT_SK(tile) for the stream-K variants.
 constexpr int kClassicVariants = RG_NUM_TILES * RG_NUM_SPLITS;
-inline bool variant_streamk(int v) { return v >= kClassicVariants; }
-inline int variant_tile(int v) { return v >= kClassicVariants ? v - kClassicVariants : v / RG_NUM_SPLITS; }
+constexpr int kPairVariants = kClassicVariants + RG_NUM_TILES;
+inline bool variant_streamk(int v) { return v >= kClassicVariants && v < kPairVariants; }
+inline bool variant_pair(int v) { return v >= kPairVariants; }
+inline int variant_tile(int v) {
+  return v >= kPairVariants ? v - kPairVariants : v >= kClassicVariants ? v - kClassicVariants : v / RG_NUM_SPLITS;
+}
 inline int variant_split(int v) { return v >= kClassicVariants ? 1 : 1 << (v % RG_NUM_SPLITS); }
 // Stream-K geometry shared by the launcher, the sweep's pruning and the kernel:
 // whole waves of tiles run data-parallel (one tile per CTA per wave); only the

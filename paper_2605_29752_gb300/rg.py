@@ -31,20 +31,27 @@ RG_ERR_NO_DEVICE = -9
 RG_T_UNMEASURED = 1 << 60
 RG_NUM_TILES = 6
 RG_NUM_SPLITS = 4
-RG_NUM_VARIANTS = RG_NUM_TILES * RG_NUM_SPLITS + RG_NUM_TILES
+RG_NUM_VARIANTS = RG_NUM_TILES * RG_NUM_SPLITS + 2 * RG_NUM_TILES
 TILES = [(128, 64), (128, 128), (128, 256), (256, 64), (256, 128), (256, 256)]
 SPLITS = [1, 2, 4, 8]
 SK = "SK"
+PAIR = "PR"
 
 
 def variant(tile: int, split=1) -> int:
-    """Variant id of a tile with split factor 1/2/4/8, or split="SK" for stream-K."""
+    """Variant id of a tile with split factor 1/2/4/8, split="SK" for stream-K or "PR" for the
+    2-CTA multicast pair."""
     if split == SK:
         return RG_NUM_TILES * RG_NUM_SPLITS + tile
+    if split == PAIR:
+        return RG_NUM_TILES * RG_NUM_SPLITS + RG_NUM_TILES + tile
     return tile * RG_NUM_SPLITS + SPLITS.index(split)
 
 
 def variant_name(v: int) -> str:
+    if v >= RG_NUM_TILES * RG_NUM_SPLITS + RG_NUM_TILES:
+        bm, bn = TILES[v - RG_NUM_TILES * RG_NUM_SPLITS - RG_NUM_TILES]
+        return f"{bm}x{bn}/PR"
     if v >= RG_NUM_TILES * RG_NUM_SPLITS:
         bm, bn = TILES[v - RG_NUM_TILES * RG_NUM_SPLITS]
         return f"{bm}x{bn}/SK"

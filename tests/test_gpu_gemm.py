@@ -11,7 +11,7 @@ from oracle import gemm as og
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-ALL_VARIANTS = list(range(30))          # 24 split-K variants, then 6 stream-K
+ALL_VARIANTS = list(range(36))          # 24 split-K variants, 6 stream-K, 6 multicast pairs
 
 
 @pytest.fixture(scope="module")
@@ -201,3 +201,24 @@ def test_stream_k_beta_one(rg, ctx, v):
     a, b = synthetic.operands_bf16(M, N, K, seed=13)
     c0 = synthetic.normal_stream_f32(13, 5, M * N).reshape(M, N)
     check(run(rg, ctx, a, b, v, beta=1, c0=c0), a, b, c0=c0)
+
+
+@pytest.mark.parametrize("tile", range(6))
+@pytest.mark.parametrize("shape", [(384, 640, 1024), (1664, 1664, 2048), (128, 64, 256), (4096, 1152, 4096)])
+def test_pair_multicast(rg, ctx, tile, shape):
+    """2-CTA pairs sharing one operand by multicast, including odd tile counts (a partner past the
+    edge) and a single tile; bitwise equal to the unpaired kernel of the same tile (same summation)."""
+    M, N, K = shape
+    a, b = synthetic.operands_bf16(M, N, K, seed=14)
+    c = run(rg, ctx, a, b, rg.variant(tile, rg.PAIR))
+    if M * N * K <= 1024 * 1024 * 1024:
+        check(c, a, b)
+    assert np.array_equal(c, run(rg, ctx, a, b, rg.variant(tile, 1)))
+
+
+@pytest.mark.parametrize("tile", [0, 1, 5])
+def test_pair_beta_one(rg, ctx, tile):
+    M, N, K = 640, 384, 1536
+    a, b = synthetic.operands_bf16(M, N, K, seed=15)
+    c0 = synthetic.normal_stream_f32(15, 5, M * N).reshape(M, N)
+    check(run(rg, ctx, a, b, rg.variant(tile, rg.PAIR), beta=1, c0=c0), a, b, c0=c0)
