@@ -388,7 +388,8 @@ def main():
         "data": "synthetic",
         "config": {"workload": f"BF16 NN GEMM landscape, (M,N,K) in {{128..{Mx} step 128}}^3 = {ncell} cells, "
                                f"U[-1,1) BF16 operands (seed 0), FP32 accumulate/output",
-                   "smoothed": "best-of-24 autotune (6 tiles x split-K 1/2/4/8) + DP pad/split plan, O(1) lookup",
+                   "smoothed": "best-of-36 autotune (6 tiles x {split-K 1/2/4/8, stream-K, 2-CTA multicast "
+                               "pair}) + DP pad/split plan, O(1) lookup",
                    "plain": "fixed 128x128 tile, split 1",
                    "timing": "per cell: 1 warm-up launch, device spin, mean of 5 back-to-back launches between "
                              "CUDA events (paper protocol); operands of small cells stay L2-resident across the "
@@ -487,7 +488,7 @@ def extras(args, rg, ctx, grid, T0v, plan_smooth, A, B, C, flops, Mv, Nv, Kv, de
     tf, r, m = rg.rg_surface_stats(grid, T6.min(axis=0))
     ladder["best_of_6"] = summarize(tf, r, m)
     tf, r, m = rg.rg_surface_stats(grid, T0v.min(axis=0))
-    ladder["best_of_24_autotune"] = summarize(tf, r, m)
+    ladder["best_of_all_variants_autotune"] = summarize(tf, r, m)
     for name, rows, flags in (("dp_pad_on_best_of_6", s1_rows, rg.RG_PLAN_PAD_ONLY),
                               ("dp_split_pad_on_best_of_6", s1_rows, 0),
                               ("dp_split_pad_on_fixed", [fixed_v], 0)):
@@ -544,6 +545,13 @@ def extras(args, rg, ctx, grid, T0v, plan_smooth, A, B, C, flops, Mv, Nv, Kv, de
                       ("best_of_6", ladder["best_of_6"]["mean_tflops"], ladder["best_of_6"]["R_N_slice"]),
                       ("dp_split_pad_on_best_of_6", ladder["dp_split_pad_on_best_of_6"]["measured"]["mean_tflops"],
                        ladder["dp_split_pad_on_best_of_6"]["measured"]["R_N_slice"]))}
+    # ---- four-surface decomposition (Sec. 4) with the memory twins
+    out["decomposition"] = decomposition(rg, ctx, grid, T0v, s1_rows, fixed_v, A, B, C, flops, p_burst, count)
+    # ---- fine step-32 cross-tile N sweep at M = K = 4096 with DP padding on the fine grid (Sec. 8.3-8.4)
+    if count * STEP >= 4096:
+        out["fine_N_sweep"] = fine_n_sweep(rg, ctx, A, B, C)
+    # ---- measurement methodology (Sec. 5.3-5.4, Sec. 8.2): run-order drift, co-allocation, per-config spread
+    out["methodology"] = methodology(rg, ctx, grid, T0v, fixed_v, plan_smooth, A, B, C, dev, count)
     # ---- serving (continuous batching over the grouped GEMM), at half the saturated capacity
     out["serving"] = serving(rg, ctx, grid, T0v, A, B, count)
     # ---- FP8 e4m3 block-scaled GEMM on the {512..4096 step 512}^3 subgrid
@@ -552,6 +560,149 @@ def extras(args, rg, ctx, grid, T0v, plan_smooth, A, B, C, flops, Mv, Nv, Kv, de
     out["e2e"] = e2e(rg, ctx, plan_smooth, a_bits, b_bits, dev, count)
     # ---- CPU oracle baseline on this host
     out["cpu_baseline"] = cpu_baseline(count)
+    return out
+
+
+def decomposition(rg, ctx, grid, T0v, s1_rows, fixed_v, A, B, C, flops, p_burst, count):
+    """Compute / memory / GEMM / overhead surfaces (Sec. 4): the fixed tile over the whole grid, and
+    every tile's twin on the largest-K slice for the best-of-6 surface and the N profile of Fig. 6."""
+    out = {}
+
+    def summary(g, tg, tm, fl):
+        _, over, st = rg.rg_decompose(g, tg, tm, p_burst)
+        _, r_mem, m_mem = rg.rg_surface_stats(g, tm)
+        _, r_gemm, m_gemm = rg.rg_surface_stats(g, tg)
+        return {"compute_bound_share": float(st[0]), "overhead_share_mean": float(st[1]),
+                "overhead_share_pooled": float(st[2]), "memory_share_mean": float(st[3]),
+                "memory_equiv_tflops_mean": m_mem, "memory_equiv_R_N_slice": r_mem["R_N_slice"],
+                "memory_equiv_R_3D": r_mem["R_3D"], "gemm_R_N_slice": r_gemm["R_N_slice"],
+                "gemm_R_3D": r_gemm["R_3D"]}, over
+
+    tm_fixed = rg.rg_sweep_memtwin(ctx, grid, [rg.variant_tile(fixed_v)], A, B, C)[0]
+    out["fixed_128x128_full_grid"], _ = summary(grid, T0v[fixed_v], tm_fixed, flops)
+    kmax = STEP * count
+    gk = rg.make_grid((STEP, STEP, count), (STEP, STEP, count), (kmax, STEP, 1))
+    tm6 = rg.rg_sweep_memtwin(ctx, gk, list(range(rg.RG_NUM_TILES)), A, B, C)
+    tg6 = np.stack([T0v[v].reshape(count, count, count)[:, :, -1].ravel() for v in s1_rows])
+    win = tg6.argmin(axis=0)
+    cols = np.arange(tg6.shape[1])
+    best_g, best_m = tg6[win, cols], tm6[win, cols]
+    out["best_of_6_K_max_slice"], over = summary(gk, best_g, best_m, None)
+    # Fig. 6: the time stack along N at M = K = max, fixed tile
+    ti = rg.variant_tile(fixed_v)
+    row = slice((count - 1) * count, count * count)
+    prof = []
+    for j in range(count):
+        n = STEP * (j + 1)
+        tg = float(T0v[fixed_v].reshape(count, count, count)[count - 1, j, -1])
+        tm = float(tm6[ti][row][j])
+        tc = 2.0 * kmax * n * kmax / (p_burst * 1e3)
+        prof.append({"N": n, "compute_ns": tc, "memory_ns": tm, "gemm_ns": tg, "overhead_ns": tg - max(tc, tm)})
+    out["N_profile_fixed_tile_M_K_max"] = prof[3::4]
+    out["note"] = ("memory twin = the tile's GEMM kernel with every MMA a no-op (same TMA loads, pipeline, "
+                   "TMEM read-back and stores); compute = 2MNK at the measured bf16 burst peak; "
+                   "memory_equiv_* = statistics of the surface 2MNK / t_memory")
+    return out
+
+
+def fine_n_sweep(rg, ctx, A, B, C, n0=3000, step=32, count=35, mk=4096):
+    """N = 3000..4088 step 32 at M = K = 4096 for every tile (split 1), then DP padding (T0 -> T1) on
+    that fine grid per tile and on the best-of-6 envelope (Sec. 8.3-8.4, Tables 13-14)."""
+    g = rg.make_grid((mk, STEP, 1), (n0, step, count), (mk, STEP, 1))
+    rows = [rg.variant(t, 1) for t in range(rg.RG_NUM_TILES)]
+    T0 = rg.rg_sweep(ctx, g, rows, A, B, C)
+    Ns = n0 + step * np.arange(count)
+    out = {"grid": f"M = K = {mk}, N = {n0}..{Ns[-1]} step {step}"}
+
+    def stats(t_row):
+        tf, r, m = rg.rg_surface_stats(g, t_row)
+        return tf, r["R_N"], m
+
+    def entry(t_rows, vids, bn):
+        t0 = t_rows.min(axis=0) if t_rows.ndim == 2 else t_rows
+        tf0, r0, m0 = stats(t0)
+        h = rg.rg_plan_build_ex(g, np.atleast_2d(t_rows), vids, rg.RG_PLAN_PAD_ONLY)
+        t1 = rg.rg_plan_tables(h)["T1"]
+        rg.rg_plan_free(h)
+        tf1, r1, m1 = stats(t1)
+        valleys = [int(i) for i in range(1, count - 1) if tf0[i] < tf0[i - 1] and tf0[i] < tf0[i + 1]]
+        lag, corr = sawtooth_period(tf0)
+        e = {"T0_roughness": r0, "T1_roughness": r1, "reduction_pct": 100.0 * (1 - r1 / r0) if r0 > 0 else 0.0,
+             "T0_mean": m0, "T1_mean": m1, "T0_min": float(tf0.min()), "T1_min": float(tf1.min()),
+             "period_N": None if lag is None else int(lag * step), "period_autocorr": corr,
+             "valleys_N": [int(Ns[i]) for i in valleys]}
+        if bn:
+            mods = [int(Ns[i]) % bn for i in valleys]
+            e["valley_N_mod_BN"] = mods
+            e["valley_N_mod_BN_mode"] = max(set(mods), key=mods.count) if mods else None
+        return e
+
+    for t, v in enumerate(rows):
+        out[rg.variant_name(v)] = entry(T0[t], [v], rg.TILES[t][1])
+    out["best_of_6_envelope"] = entry(T0, rows, None)
+    return out
+
+
+def _ranks(x):
+    r = np.empty(len(x))
+    r[np.argsort(x, kind="stable")] = np.arange(len(x))
+    return r
+
+
+def methodology(rg, ctx, grid, T0v, fixed_v, plan, A, B, C, dev, count, runs=50):
+    """Sec. 5.3-5.4: a sequential-order sweep against the randomized one (run-order drift); the memory
+    twin on co-allocated prefixes against freshly allocated exact-size buffers; Sec. 8.2 / Table 12:
+    the spread of 50 independent measurements of five configurations through the smoothed plan."""
+    import torch
+    out = {}
+    o = rg.rg_sweep_opts_default()
+    o.shuffle = 0
+    t_seq = rg.rg_sweep(ctx, grid, [fixed_v], A, B, C, o)[0].astype(np.float64)
+    t_rnd = T0v[fixed_v].astype(np.float64)
+    ratio = t_seq / t_rnd
+    order = np.arange(len(ratio))
+    rho = float(np.corrcoef(_ranks(ratio), _ranks(order))[0, 1])
+    blocks = ratio.reshape(count, -1)
+    tenth = max(1, blocks.shape[1] // 10)
+    out["order"] = {"median_abs_rel_diff_pct": float(100 * np.median(np.abs(ratio - 1))),
+                    "mean_ratio_seq_over_random": float(ratio.mean()),
+                    "spearman_ratio_vs_sequential_order": rho,
+                    "first_tenth_vs_last_tenth_of_M_blocks_pct":
+                        float(100 * (blocks[:, :tenth].mean() / blocks[:, -tenth:].mean() - 1))}
+    # co-allocation: 64 seeded cells, memory twin of the fixed tile
+    rs = np.random.default_rng(0)
+    cells = rs.choice(count ** 3, 64, replace=False)
+    slow = []
+    for c in cells:
+        a, b, k = c // (count * count), (c // count) % count, c % count
+        M, N, K = STEP * (a + 1), STEP * (b + 1), STEP * (k + 1)
+        g1 = rg.make_grid((M, STEP, 1), (N, STEP, 1), (K, STEP, 1))
+        t_co = rg.rg_sweep_memtwin(ctx, g1, [rg.variant_tile(fixed_v)], A, B, C)[0][0]
+        Ai = torch.empty(M * K, dtype=torch.bfloat16, device=dev).copy_(A[:M * K])
+        Bi = torch.empty(K * N, dtype=torch.bfloat16, device=dev).copy_(B[:K * N])
+        Ci = torch.empty(M * N, dtype=torch.float32, device=dev)
+        t_iso = rg.rg_sweep_memtwin(ctx, g1, [rg.variant_tile(fixed_v)], Ai, Bi, Ci)[0][0]
+        slow.append(t_co / t_iso)
+        del Ai, Bi, Ci
+    slow = np.array(slow)
+    out["coallocation"] = {"cells": 64, "mean_slowdown_coallocated_over_isolated": float(slow.mean()),
+                           "share_over_20pct": float(np.mean(slow > 1.2)),
+                           "share_over_5pct": float(np.mean(slow > 1.05))}
+    # per-configuration spread over 50 independent measurements (Table 12's five configurations)
+    confs = {"aligned_rect_4096x2048x4096": (4096, 2048, 4096), "aligned_square_4096^3": (4096, 4096, 4096),
+             "misaligned_N3168": (4096, 3168, 4096), "misaligned_N3096": (4096, 3096, 4096),
+             "saturation_2560x1536x4096": (2560, 1536, 4096)}
+    spread = {}
+    for name, (M, N, K) in confs.items():
+        if max(M, N, K) > STEP * count:
+            continue
+        g1 = rg.make_grid((M, STEP, 1), (N, STEP, 1), (K, STEP, 1))
+        ts = np.array([rg.rg_sweep(ctx, g1, [0], A, B, C, plan=plan)[0][0] for _ in range(runs)], np.float64)
+        tf = 2.0 * M * N * K / (ts * 1e3)
+        spread[name] = {"mean_tflops": float(tf.mean()), "std": float(tf.std(ddof=1)),
+                        "cv_pct": float(100 * tf.std(ddof=1) / tf.mean()),
+                        "range_pct": float(100 * (tf.max() - tf.min()) / tf.mean())}
+    out["per_config_spread_50_runs"] = spread
     return out
 
 

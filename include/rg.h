@@ -167,7 +167,9 @@ int rg_gemm(rg_ctx* ctx, int64_t M, int64_t N, int64_t K,
  * T0_ns: [n_variants][cells] int64 nanoseconds (cells in the grid's linear
  * order), variant_ids[v] the library variant measured in row v.  Builds
  * best-of selection, T1 (padding), T2 (splitting) and every cell's leaf list.
- * The grid must have start == step on every axis (whole multiples of the step). */
+ * The grid must have start == step on every axis (whole multiples of the step),
+ * except with RG_PLAN_PAD_ONLY, where any grid is accepted (padding moves to a
+ * larger grid cell; nothing is split). */
 int rg_plan_build(const rg_grid* grid, const int64_t* T0_ns, int32_t n_variants,
                   const int32_t* variant_ids, rg_plan** out);
 /* As rg_plan_build with flags: RG_PLAN_PAD_ONLY stops after T1 (padding only:
@@ -340,6 +342,30 @@ int rg_kol(double mean_a, double mean_o, double r_a, double r_o, double out[2], 
 int rg_sweep(rg_ctx* ctx, const rg_grid* grid, int32_t n_variants, const int32_t* variant_ids,
              const rg_plan* plan, const void* A, const void* B, float* C,
              const rg_sweep_opts* opts, int64_t* t_ns_out, void* stream);
+
+/* ---- four-surface decomposition (Sec. 4, Figs. 5-6, Table 3) ----
+ * The memory twin of a tile runs the tile's GEMM kernel (split 1, beta 0) with
+ * every MMA replaced by a no-op: the same TMA loads of A and B, the same
+ * pipeline, TMEM read-back and TMA stores of C.  C receives whatever the
+ * accumulators held (undefined values): the twin exists to be timed.
+ * rg_gemm_memtwin: one launch, arguments and errors as rg_gemm with variant
+ * RG_VARIANT(tile, 0).  rg_sweep_memtwin: rg_sweep's protocol and operand
+ * conventions over the n_tiles tile ids (0..RG_NUM_TILES-1); nothing is pruned;
+ * t_ns_out[t][cell]. */
+int rg_gemm_memtwin(rg_ctx* ctx, int64_t M, int64_t N, int64_t K, const void* A, int64_t lda, const void* B,
+                    int64_t ldb, float* C, int64_t ldc, int32_t tile, void* stream);
+int rg_sweep_memtwin(rg_ctx* ctx, const rg_grid* grid, int32_t n_tiles, const int32_t* tile_ids, const void* A,
+                     const void* B, float* C, const rg_sweep_opts* opts, int64_t* t_ns_out, void* stream);
+/* Host.  Per cell of `grid` (times in ns, all > 0; P = p_tflops > 0):
+ *   compute_ns_out[cell]  = (2.0 * M * N * K) / (P * 1e3)          (useful flops at peak)
+ *   overhead_ns_out[cell] = t_gemm - max(compute, t_mem)            (may be negative)
+ * stats_out = {share of cells with compute > t_mem (compute-bound),
+ *              mean over cells of overhead / t_gemm,
+ *              sum overhead / sum t_gemm,
+ *              mean over cells of t_mem / t_gemm}.
+ * Any output may be NULL.  Sums are correctly rounded.  Errors: RG_ERR_INVALID. */
+int rg_decompose(const rg_grid* grid, const int64_t* t_gemm_ns, const int64_t* t_mem_ns, double p_tflops,
+                 double* compute_ns_out, double* overhead_ns_out, double stats_out[4]);
 
 /* ---- GEMM without device allocation ----
  * The paper has no counterpart to this entry point.  It is for callers that

@@ -170,6 +170,7 @@ __device__ __forceinline__ Unit split_unit(const CUtensorMap* a, const CUtensorM
 struct SingleSched {
   static constexpr bool kMapsInGlobal = false;
   static constexpr int kMulticast = 0;
+  static constexpr bool kMemOnly = false;
   static constexpr int rank = 0;
   const CUtensorMap* a;
   const CUtensorMap* b;
@@ -194,6 +195,13 @@ struct SingleSched {
   }
 };
 
+// The memory twin of SingleSched: the same units, loads and stores, with the
+// MMAs replaced by no-ops (the memory surface of the four-surface decomposition,
+// Sec. 4).  Its output is whatever the accumulators held: timing only.
+struct MemTwinSched : SingleSched {
+  static constexpr bool kMemOnly = true;
+};
+
 // Stream-K (hybrid): whole waves of tiles run data-parallel, one tile per CTA
 // per wave (tile g + i * G on CTA g, for tiles below dp_tiles = G * floor(T / G));
 // the remaining tiles' K iterations are divided evenly among the first tail CTAs:
@@ -205,6 +213,7 @@ struct SingleSched {
 struct StreamKSched {
   static constexpr bool kMapsInGlobal = false;
   static constexpr int kMulticast = 0;
+  static constexpr bool kMemOnly = false;
   static constexpr int rank = 0;
   const CUtensorMap* a;
   const CUtensorMap* b;
@@ -290,6 +299,7 @@ template <int MODE>
 struct PairSched {
   static constexpr bool kMapsInGlobal = false;
   static constexpr int kMulticast = MODE;
+  static constexpr bool kMemOnly = false;
   const CUtensorMap* a;
   const CUtensorMap* b;
   const CUtensorMap* c;
@@ -355,6 +365,7 @@ struct alignas(64) GroupHeader {
 struct GroupSched {
   static constexpr bool kMapsInGlobal = true;
   static constexpr int kMulticast = 0;
+  static constexpr bool kMemOnly = false;
   static constexpr int rank = 0;
   const GroupHeader* h;
   const GroupItem* items;
@@ -505,7 +516,9 @@ __device__ __forceinline__ void gemm_body(Sched& sched, float* ws, int32_t* tick
         ok = __all_sync(FULL, mbar_wait(full_bar(stage), ph, timeout, abort_flag));
         if (!ok) break;
         tc_fence_after();
-        if (lane == 0) {
+        if (lane == 0 && Sched::kMemOnly) {
+          mbar_arrive(empty_bar(stage));  // no MMA reads the stage: it is free once its bytes have landed
+        } else if (lane == 0) {
           const uint32_t sa = sbase + stage * C::STAGE_BYTES;
           const uint32_t sb = sa + C::A_BYTES;
 #pragma unroll
@@ -529,7 +542,12 @@ __device__ __forceinline__ void gemm_body(Sched& sched, float* ws, int32_t* tick
         }
       }
       if (!ok) break;
-      if (lane == 0) mma_commit(tfull_bar(acc));
+      if (lane == 0) {
+        if constexpr (Sched::kMemOnly)
+          mbar_arrive(tfull_bar(acc));
+        else
+          mma_commit(tfull_bar(acc));
+      }
       __syncwarp();
       if (++acc == C::NBUF) {
         acc = 0;
@@ -721,6 +739,16 @@ __global__ void __launch_bounds__(kThreads, 1)
 
 template <int BM, int BN, int STAGES>
 __global__ void __launch_bounds__(kThreads, 1)
+    gemm_bf16_memtwin_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                             const __grid_constant__ CUtensorMap tmC, const __grid_constant__ CUtensorMap tmW,
+                             const GemmArgs args) {
+  MemTwinSched sched{{&tmA,        &tmB,          &tmC,   &tmW,  args.tiles_m, args.tiles_n,
+                      args.splits, args.kblocks, args.M, args.N, args.beta}};
+  gemm_body<BM, BN, STAGES>(sched, args.ws, args.tickets, args.err, args.timeout, args.stall);
+}
+
+template <int BM, int BN, int STAGES>
+__global__ void __launch_bounds__(kThreads, 1)
     gemm_bf16_streamk_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                              const __grid_constant__ CUtensorMap tmC, const __grid_constant__ CUtensorMap tmW,
                              const GemmArgs args) {
@@ -767,6 +795,7 @@ struct TileKernel {
   KernFn pair;  // 2-CTA cluster instance sharing one operand by multicast
   int pair_mode;  // 1: pairs along M share B; 2: pairs along N share A
   int bm, bn, smem;
+  KernFn mem;     // memory twin (loads and stores, no MMA)
 };
 
 // The pair shares whichever operand tile is larger per K block (B when BN >= BM).
@@ -774,7 +803,8 @@ template <int BM, int BN, int ST>
 TileKernel make_tile_kernel() {
   constexpr int mode = BN >= BM ? 1 : 2;
   return TileKernel{gemm_bf16_kernel<BM, BN, ST>, gemm_bf16_streamk_kernel<BM, BN, ST>,
-                    gemm_bf16_pair_kernel<BM, BN, ST, mode>, mode, BM, BN, KCfg<BM, BN, ST>::SMEM_BYTES};
+                    gemm_bf16_pair_kernel<BM, BN, ST, mode>, mode, BM, BN, KCfg<BM, BN, ST>::SMEM_BYTES,
+                    gemm_bf16_memtwin_kernel<BM, BN, ST>};
 }
 
 using GroupedFn = void (*)(const GroupHeader*, const GroupItem*, int32_t*, long long);
@@ -1152,6 +1182,8 @@ extern "C" int rg_init(int device, int64_t workspace_bytes, rg_ctx** out) {
                                   tk.smem)) != cudaSuccess ||
         (e = cudaFuncSetAttribute(reinterpret_cast<const void*>(tk.pair), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   tk.smem)) != cudaSuccess ||
+        (e = cudaFuncSetAttribute(reinterpret_cast<const void*>(tk.mem), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  tk.smem)) != cudaSuccess ||
         (e = cudaFuncSetAttribute(reinterpret_cast<const void*>(rg::grouped_kernel(t)),
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, tk.smem)) != cudaSuccess) {
       delete ctx;
@@ -1263,14 +1295,20 @@ uint64_t splitmix_next(uint64_t& s) {
 }
 }  // namespace
 
-extern "C" int rg_sweep(rg_ctx* ctx, const rg_grid* grid, int32_t n_variants, const int32_t* variant_ids,
-                        const rg_plan* plan, const void* A, const void* B, float* C, const rg_sweep_opts* opts,
-                        int64_t* t_ns_out, void* stream) {
+// The sweep behind rg_sweep and rg_sweep_memtwin.  memtwin: the ids are tile
+// ids and every cell runs that tile's memory twin (never pruned).
+static int sweep_impl(rg_ctx* ctx, const rg_grid* grid, int32_t n_variants, const int32_t* variant_ids,
+                      const rg_plan* plan, const void* A, const void* B, float* C, const rg_sweep_opts* opts,
+                      int64_t* t_ns_out, void* stream, bool memtwin) {
   rg::clear_error();
   if (!ctx || !grid || !A || !B || !C || !t_ns_out) return rg::fail(RG_ERR_INVALID, "rg_sweep: null argument");
   if (!rg::grid_valid(*grid)) return rg::fail(RG_ERR_INVALID, "rg_sweep: invalid grid");
   if (plan ? n_variants != 1 : (n_variants <= 0 || !variant_ids))
     return rg::fail(RG_ERR_INVALID, "rg_sweep: variants");
+  if (memtwin)
+    for (int32_t i = 0; i < n_variants; ++i)
+      if (variant_ids[i] < 0 || variant_ids[i] >= RG_NUM_TILES)
+        return rg::fail(RG_ERR_INVALID, "rg_sweep_memtwin: tile id out of range");
   rg_sweep_opts o;
   rg_sweep_opts_default(&o);
   if (opts) o = *opts;
@@ -1299,7 +1337,7 @@ extern "C" int rg_sweep(rg_ctx* ctx, const rg_grid* grid, int32_t n_variants, co
   // A split-K variant is worth timing only where the unsplit tile count leaves
   // SMs idle and every split keeps at least two K blocks.
   auto pruned = [&](int64_t item) -> bool {
-    if (plan || !o.prune_splits) return false;
+    if (plan || memtwin || !o.prune_splits) return false;
     const int32_t v = variant_ids[item / cells];
     const int S = rg::variant_split(v);
     const bool sk = rg::variant_streamk(v);
@@ -1340,7 +1378,9 @@ extern "C" int rg_sweep(rg_ctx* ctx, const rg_grid* grid, int32_t n_variants, co
       rc = rg::plan_launches(ctx, plan, M, N, K, A, K, B, N, C, N, ls);
     } else {
       ls.resize(1);
-      rc = rg::prepare(ctx, M, N, K, A, K, B, N, C, N, variant_ids[item / cells], 0, 0, 0, 0, &ls[0]);
+      const int32_t v = variant_ids[item / cells];
+      rc = rg::prepare(ctx, M, N, K, A, K, B, N, C, N, memtwin ? RG_VARIANT(v, 0) : v, 0, 0, 0, 0, &ls[0]);
+      if (rc == RG_OK && memtwin) ls[0].fn = rg::tile_kernel(v).mem;
     }
     *launches = static_cast<int>(ls.size());
     return rc;
@@ -1355,6 +1395,30 @@ extern "C" int rg_sweep(rg_ctx* ctx, const rg_grid* grid, int32_t n_variants, co
   const int rc = rg::timed_sweep(ctx, order, o, st, t_ns_out, prep, run);
   if (rc != RG_OK) return rc;
   return rg_check(ctx, stream);
+}
+
+extern "C" int rg_sweep(rg_ctx* ctx, const rg_grid* grid, int32_t n_variants, const int32_t* variant_ids,
+                        const rg_plan* plan, const void* A, const void* B, float* C, const rg_sweep_opts* opts,
+                        int64_t* t_ns_out, void* stream) {
+  return sweep_impl(ctx, grid, n_variants, variant_ids, plan, A, B, C, opts, t_ns_out, stream, false);
+}
+
+extern "C" int rg_sweep_memtwin(rg_ctx* ctx, const rg_grid* grid, int32_t n_tiles, const int32_t* tile_ids,
+                                const void* A, const void* B, float* C, const rg_sweep_opts* opts, int64_t* t_ns_out,
+                                void* stream) {
+  return sweep_impl(ctx, grid, n_tiles, tile_ids, nullptr, A, B, C, opts, t_ns_out, stream, true);
+}
+
+extern "C" int rg_gemm_memtwin(rg_ctx* ctx, int64_t M, int64_t N, int64_t K, const void* A, int64_t lda,
+                               const void* B, int64_t ldb, float* C, int64_t ldc, int32_t tile, void* stream) {
+  rg::clear_error();
+  if (tile < 0 || tile >= RG_NUM_TILES) return rg::fail(RG_ERR_INVALID, "rg_gemm_memtwin: tile id out of range");
+  rg::Launch L;
+  int rc = rg::prepare(ctx, M, N, K, A, lda, B, ldb, C, ldc, RG_VARIANT(tile, 0), 0, 0, 0, 0, &L);
+  if (rc != RG_OK) return rc;
+  if (L.fn) L.fn = rg::tile_kernel(tile).mem;
+  cudaError_t e = rg::launch(ctx, L, static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? RG_OK : rg::cuda_fail(e, "rg_gemm_memtwin: launch");
 }
 
 // ------------------------------------------------------------------ grouped GEMM under CUDA graphs

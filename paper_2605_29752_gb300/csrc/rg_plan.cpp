@@ -95,7 +95,8 @@ extern "C" int rg_plan_build_ex(const rg_grid* grid, const int64_t* T0_ns, int32
     return rg::fail(RG_ERR_INVALID, "rg_plan_build: null argument or n_variants <= 0");
   if (flags & ~RG_PLAN_PAD_ONLY) return rg::fail(RG_ERR_INVALID, "rg_plan_build: unknown flags");
   if (!rg::grid_valid(*grid)) return rg::fail(RG_ERR_INVALID, "rg_plan_build: invalid grid");
-  if (grid->m.start != grid->m.step || grid->n.start != grid->n.step || grid->k.start != grid->k.step)
+  if (!(flags & RG_PLAN_PAD_ONLY) &&
+      (grid->m.start != grid->m.step || grid->n.start != grid->n.step || grid->k.start != grid->k.step))
     return rg::fail(RG_ERR_INVALID, "rg_plan_build: splitting needs start == step on every axis");
   for (int v = 0; v < n_variants; ++v) {
     if (variant_ids[v] < 0 || variant_ids[v] >= RG_NUM_VARIANTS)

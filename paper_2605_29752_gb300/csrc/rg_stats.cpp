@@ -247,3 +247,49 @@ extern "C" int rg_kol(double mean_a, double mean_o, double r_a, double r_o, doub
   bands[2] = std::min(T, S);
   return RG_OK;
 }
+
+// Four-surface decomposition (Sec. 4): the compute surface is the useful-flop
+// time at peak, the memory surface the measured memory twin, the overhead
+// surface what the GEMM takes beyond the larger of the two; a cell is
+// compute-bound when even a zero-waste kernel would be limited by compute
+// (t_compute > t_memory, Table 3).
+extern "C" int rg_decompose(const rg_grid* grid, const int64_t* t_gemm_ns, const int64_t* t_mem_ns, double p_tflops,
+                            double* compute_ns_out, double* overhead_ns_out, double stats_out[4]) {
+  rg::clear_error();
+  if (!grid || !t_gemm_ns || !t_mem_ns) return rg::fail(RG_ERR_INVALID, "rg_decompose: null argument");
+  if (!rg::grid_valid(*grid)) return rg::fail(RG_ERR_INVALID, "rg_decompose: invalid grid");
+  if (!(p_tflops > 0.0)) return rg::fail(RG_ERR_INVALID, "rg_decompose: peak must be positive");
+  const int64_t nm = grid->m.count, nn = grid->n.count, nk = grid->k.count;
+  const int64_t cells = nm * nn * nk;
+  for (int64_t i = 0; i < cells; ++i)
+    if (t_gemm_ns[i] <= 0 || t_mem_ns[i] <= 0) return rg::fail(RG_ERR_INVALID, "rg_decompose: times must be positive");
+  int64_t compute_bound = 0;
+  rg::ExactSum share_o, share_m, sum_o, sum_g;
+  for (int64_t a = 0; a < nm; ++a)
+    for (int64_t b = 0; b < nn; ++b)
+      for (int64_t c = 0; c < nk; ++c) {
+        const int64_t i = (a * nn + b) * nk + c;
+        const double M = static_cast<double>(rg::axis_value(grid->m, a));
+        const double N = static_cast<double>(rg::axis_value(grid->n, b));
+        const double K = static_cast<double>(rg::axis_value(grid->k, c));
+        const double flops = 2.0 * M * N * K;
+        const double tc = flops / (p_tflops * 1e3);
+        const double tg = static_cast<double>(t_gemm_ns[i]);
+        const double tm = static_cast<double>(t_mem_ns[i]);
+        const double to = tg - std::max(tc, tm);
+        if (compute_ns_out) compute_ns_out[i] = tc;
+        if (overhead_ns_out) overhead_ns_out[i] = to;
+        if (tc > tm) ++compute_bound;
+        share_o.add(to / tg);
+        share_m.add(tm / tg);
+        sum_o.add(to);
+        sum_g.add(tg);
+      }
+  if (stats_out) {
+    stats_out[0] = static_cast<double>(compute_bound) / static_cast<double>(cells);
+    stats_out[1] = share_o.value() / static_cast<double>(cells);
+    stats_out[2] = sum_o.value() / sum_g.value();
+    stats_out[3] = share_m.value() / static_cast<double>(cells);
+  }
+  return RG_OK;
+}

@@ -48,6 +48,12 @@ def variant(tile: int, split=1) -> int:
     return tile * RG_NUM_SPLITS + SPLITS.index(split)
 
 
+def variant_tile(v: int) -> int:
+    """Tile index (0..5) of a variant id."""
+    n = RG_NUM_TILES * RG_NUM_SPLITS
+    return v - n - RG_NUM_TILES if v >= n + RG_NUM_TILES else v - n if v >= n else v // RG_NUM_SPLITS
+
+
 def variant_name(v: int) -> str:
     if v >= RG_NUM_TILES * RG_NUM_SPLITS + RG_NUM_TILES:
         bm, bn = TILES[v - RG_NUM_TILES * RG_NUM_SPLITS - RG_NUM_TILES]
@@ -160,6 +166,10 @@ _sigs = {
     "rg_plan_load": (C.c_int, [C.c_char_p, _P, C.POINTER(_P)]),
     "rg_surface_stats": (C.c_int, [C.POINTER(rg_grid), _P, _P, _P, _P]),
     "rg_sweep": (C.c_int, [_P, C.POINTER(rg_grid), _I32, _P, _P, _P, _P, _P, C.POINTER(rg_sweep_opts), _P, _P]),
+    "rg_gemm_memtwin": (C.c_int, [_P, _I64, _I64, _I64, _P, _I64, _P, _I64, _P, _I64, _I32, _P]),
+    "rg_sweep_memtwin": (C.c_int, [_P, C.POINTER(rg_grid), _I32, _P, _P, _P, _P, C.POINTER(rg_sweep_opts), _P,
+                                   _P]),
+    "rg_decompose": (C.c_int, [C.POINTER(rg_grid), _P, _P, C.c_double, _P, _P, _P]),
 }
 for _name, (_res, _args) in _sigs.items():
     _f = getattr(_lib, _name)
@@ -384,6 +394,38 @@ def rg_sweep(ctx, grid: rg_grid, variant_ids, A, B, Cp, opts: rg_sweep_opts | No
     _check(_lib.rg_sweep(ctx, C.byref(grid), len(vids), vids.ctypes.data, plan, _ptr(A), _ptr(B), _ptr(Cp),
                          C.byref(o), out.ctypes.data, _stream(stream)), "rg_sweep")
     return out
+
+
+def rg_gemm_memtwin(ctx, M, N, K, A, lda, B, ldb, Cp, ldc, tile, stream=None) -> None:
+    """One launch of a tile's memory twin (loads and stores, no MMA; C gets undefined values)."""
+    _check(_lib.rg_gemm_memtwin(ctx, M, N, K, _ptr(A), lda, _ptr(B), ldb, _ptr(Cp), ldc, tile, _stream(stream)),
+           "rg_gemm_memtwin")
+
+
+def rg_sweep_memtwin(ctx, grid: rg_grid, tile_ids, A, B, Cp, opts: rg_sweep_opts | None = None,
+                     stream=None) -> np.ndarray:
+    """t_ns[len(tile_ids)][cells] of the tiles' memory twins under the sweep protocol."""
+    tids = np.ascontiguousarray(tile_ids, dtype=np.int32)
+    out = np.zeros((len(tids), grid_cells(grid)), np.int64)
+    o = opts or rg_sweep_opts_default()
+    _check(_lib.rg_sweep_memtwin(ctx, C.byref(grid), len(tids), tids.ctypes.data, _ptr(A), _ptr(B), _ptr(Cp),
+                                 C.byref(o), out.ctypes.data, _stream(stream)), "rg_sweep_memtwin")
+    return out
+
+
+def rg_decompose(grid: rg_grid, t_gemm_ns, t_mem_ns, p_tflops: float):
+    """(compute_ns[cells], overhead_ns[cells], stats[4]) of the four-surface decomposition."""
+    tg = np.ascontiguousarray(t_gemm_ns, dtype=np.int64).reshape(-1)
+    tm = np.ascontiguousarray(t_mem_ns, dtype=np.int64).reshape(-1)
+    n = grid_cells(grid)
+    if tg.size != n or tm.size != n:
+        raise ValueError("time surfaces must have one entry per grid cell")
+    comp = np.zeros(n, np.float64)
+    over = np.zeros(n, np.float64)
+    st = np.zeros(4, np.float64)
+    _check(_lib.rg_decompose(C.byref(grid), tg.ctypes.data, tm.ctypes.data, p_tflops, comp.ctypes.data,
+                             over.ctypes.data, st.ctypes.data), "rg_decompose")
+    return comp, over, st
 
 
 def rg_group_create(ctx: int, tile: int, max_items: int) -> int:

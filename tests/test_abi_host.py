@@ -208,3 +208,42 @@ def test_kol_matches_oracle(rg):
     from oracle import landscape as ol
     for args in ((58.7, 96.7, 16.8, 2.23), (76.3, 96.7, 5.0, 2.8), (96.0, 96.7, 2.0, 2.0), (10.0, 96.7, 1.0, 2.0)):
         assert rg.rg_kol(*args) == ol.kol(*args)
+
+
+def test_decompose_matches_oracle_bit_exact(rg):
+    from oracle import decompose as od
+    rng = np.random.default_rng(11)
+    for grid in (((128, 128, 32), (128, 128, 32), (128, 128, 4)), ((256, 128, 5), (3000, 32, 6), (4096, 128, 1))):
+        shape = tuple(a[2] for a in grid)
+        axes = [[a[0] + i * a[1] for i in range(a[2])] for a in grid]
+        tg = rng.integers(1000, 5_000_000, size=shape).astype(np.int64)
+        tm = rng.integers(500, 5_000_000, size=shape).astype(np.int64)
+        comp, over, st = rg.rg_decompose(rg.make_grid(*grid), tg, tm, 1900.7)
+        rc, ro, rs = od.decompose(*axes, tg, tm, 1900.7)
+        assert np.array_equal(comp.reshape(shape), rc) and np.array_equal(over.reshape(shape), ro)
+        assert np.array_equal(st, rs), (st, rs)
+    with pytest.raises(rg.RGError):
+        rg.rg_decompose(rg.make_grid((128, 128, 1), (128, 128, 1), (128, 128, 1)), [0], [1], 1.0)
+
+
+def test_pad_only_plan_on_a_fine_offset_grid_matches_oracle(rg):
+    """The fine cross-tile N grid (M = K = 4096, N = 3000..4088 step 32) is not a
+    multiple grid, so only padding applies; T1 and the pad targets are the oracle's."""
+    grid = ((4096, 128, 1), (3000, 32, 35), (4096, 128, 1))
+    g = rg.make_grid(*grid)
+    rng = np.random.default_rng(4)
+    vids = [rg.variant(t, 1) for t in range(6)]
+    T0v = rng.integers(50_000, 90_000, size=(6, 35)).astype(np.int64)
+    h = rg.rg_plan_build_ex(g, T0v, vids, rg.RG_PLAN_PAD_ONLY)
+    t = rg.rg_plan_tables(h)
+    T0s, arg = dp.best_of(T0v.reshape(6, 1, 35, 1))
+    T1, target = dp.pad_T1(T0s, grid)
+    assert np.array_equal(t["T0s"], T0s) and np.array_equal(t["T1"], T1)
+    assert np.array_equal(t["vstar"], np.asarray(vids)[arg])
+    assert np.array_equal(t["target"], np.asarray(target).reshape(t["target"].shape))
+    assert np.array_equal(t["T2"], T1) and not np.any(t["action"])
+    leaves, t2 = rg.rg_plan_lookup(h, 4096, 3001, 4096)      # rounds up to N = 3032
+    assert len(leaves) == 1 and leaves[0][7] == 3032 and leaves[0][10] >= 3032 and t2 == T1[0, 1, 0]
+    rg.rg_plan_free(h)
+    with pytest.raises(rg.RGError):
+        rg.rg_plan_build(g, T0v, vids)                         # splitting still needs start == step
