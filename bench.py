@@ -388,8 +388,8 @@ def main():
         "data": "synthetic",
         "config": {"workload": f"BF16 NN GEMM landscape, (M,N,K) in {{128..{Mx} step 128}}^3 = {ncell} cells, "
                                f"U[-1,1) BF16 operands (seed 0), FP32 accumulate/output",
-                   "smoothed": "best-of-36 autotune (6 tiles x {split-K 1/2/4/8, stream-K, 2-CTA multicast "
-                               "pair}) + DP pad/split plan, O(1) lookup",
+                   "smoothed": "best-of-38 autotune (6 tiles x {split-K 1/2/4/8, stream-K, 2-CTA multicast "
+                               "pair} + 2 cta_group::2 tiles) + DP pad/split plan, O(1) lookup",
                    "plain": "fixed 128x128 tile, split 1",
                    "timing": "per cell: 1 warm-up launch, device spin, mean of 5 back-to-back launches between "
                              "CUDA events (paper protocol); operands of small cells stay L2-resident across the "

@@ -68,10 +68,12 @@ struct GemmArgs {
   long long timeout;        // cycles per wait
 };
 
-template <int BM, int BN, int STAGES>
+// CTAS = 2: one CTA of a cta_group::2 pair (BM = 128 rows of its own, BN / 2
+// columns of B in its shared memory, M = 256 per MMA instruction).
+template <int BM, int BN, int STAGES, int CTAS = 1>
 struct KCfg {
   static constexpr int A_BYTES = BM * kBK * 2;
-  static constexpr int B_BYTES = kBK * BN * 2;
+  static constexpr int B_BYTES = kBK * (BN / CTAS) * 2;
   static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
   static constexpr int HALVES = BM / 128;
   static constexpr int ACC_COLS = HALVES * BN;
@@ -82,10 +84,11 @@ struct KCfg {
   static constexpr int STAGING_OFF = STAGES * STAGE_BYTES;
   static constexpr int BAR_OFF = STAGING_OFF + 4 * kStagingPerWarp;
   static constexpr int SMEM_BYTES = 1024 + BAR_OFF + 256;
-  static constexpr uint32_t IDESC = instr_desc(1, 1, 0, 1, 128, BN);
+  static constexpr uint32_t IDESC = instr_desc(1, 1, 0, 1, 128 * CTAS, BN);
   static_assert(A_BYTES % 1024 == 0 && B_BYTES % 1024 == 0, "stages must keep 1024-byte alignment");
   static_assert(SMEM_BYTES <= 232448, "shared memory budget");
   static_assert(BN % 64 == 0 && BN <= 256 && (BM == 128 || BM == 256), "tile shape");
+  static_assert(CTAS == 1 || (CTAS == 2 && BM == 128 && BN % 128 == 0), "pair tile shape");
 };
 
 __device__ __forceinline__ void st_shared_v4(uint32_t addr, float a, float b, float c, float d) {
@@ -171,6 +174,7 @@ struct SingleSched {
   static constexpr bool kMapsInGlobal = false;
   static constexpr int kMulticast = 0;
   static constexpr bool kMemOnly = false;
+  static constexpr bool k2Sm = false;
   static constexpr int rank = 0;
   const CUtensorMap* a;
   const CUtensorMap* b;
@@ -214,6 +218,7 @@ struct StreamKSched {
   static constexpr bool kMapsInGlobal = false;
   static constexpr int kMulticast = 0;
   static constexpr bool kMemOnly = false;
+  static constexpr bool k2Sm = false;
   static constexpr int rank = 0;
   const CUtensorMap* a;
   const CUtensorMap* b;
@@ -295,11 +300,16 @@ struct StreamKSched {
 // multicasts it to both, so the pair reads that operand from L2 once.  A CTA
 // whose tile falls outside the problem still loads and computes (zero-filled
 // reads) so that its partner's pipeline is fed; its stores are dropped.
-template <int MODE>
+//
+// TWO_SM (MODE 1): the same pairing of 128-row tiles along M, run as one
+// tcgen05 cta_group::2 unit instead: no multicast; each CTA loads its own 128
+// rows of A and half of the B tile's columns, the even CTA issues the MMAs.
+template <int MODE, bool TWO_SM = false>
 struct PairSched {
   static constexpr bool kMapsInGlobal = false;
-  static constexpr int kMulticast = MODE;
+  static constexpr int kMulticast = TWO_SM ? 0 : MODE;
   static constexpr bool kMemOnly = false;
+  static constexpr bool k2Sm = TWO_SM;
   const CUtensorMap* a;
   const CUtensorMap* b;
   const CUtensorMap* c;
@@ -366,6 +376,7 @@ struct GroupSched {
   static constexpr bool kMapsInGlobal = true;
   static constexpr int kMulticast = 0;
   static constexpr bool kMemOnly = false;
+  static constexpr bool k2Sm = false;
   static constexpr int rank = 0;
   const GroupHeader* h;
   const GroupItem* items;
@@ -396,7 +407,8 @@ struct GroupSched {
 template <int BM, int BN, int STAGES, class Sched>
 __device__ __forceinline__ void gemm_body(Sched& sched, float* ws, int32_t* tickets, int32_t* err, long long timeout,
                                           int stall) {
-  using C = KCfg<BM, BN, STAGES>;
+  constexpr bool P2 = Sched::k2Sm;  // one CTA of a cta_group::2 pair
+  using C = KCfg<BM, BN, STAGES, P2 ? 2 : 1>;
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw_s = smem_u32(smem_raw);
   uint8_t* smem = smem_raw + ((1024u - (raw_s & 1023u)) & 1023u);
@@ -425,19 +437,25 @@ __device__ __forceinline__ void gemm_body(Sched& sched, float* ws, int32_t* tick
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(tfull_bar(b), 1);
-      mbar_init(tempty_bar(b), 4);
+      // pair: the even CTA's accumulator is free once both CTAs' epilogue warps drained it
+      mbar_init(tempty_bar(b), P2 ? 8 : 4);
     }
     mbar_init(drain_bar, 1);
     *abort_flag = 0;
     fence_mbar_init();
   }
   if (warp == 1) {
-    tmem_alloc(smem_u32(tmem_slot), C::TMEM_COLS);
-    tmem_relinquish();
+    if constexpr (P2) {  // collective with the partner's warp 1: the same columns in both CTAs
+      tmem_alloc_pair(smem_u32(tmem_slot), C::TMEM_COLS);
+      tmem_relinquish_pair();
+    } else {
+      tmem_alloc(smem_u32(tmem_slot), C::TMEM_COLS);
+      tmem_relinquish();
+    }
   }
   tc_fence_before();
   __syncthreads();
-  if constexpr (Sched::kMulticast != 0) cluster_sync();  // the partner's barriers are initialised
+  if constexpr (Sched::kMulticast != 0 || P2) cluster_sync();  // the partner's barriers are initialised
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
   // Everything above overlaps the previous grid in the stream; nothing below
@@ -467,6 +485,15 @@ __device__ __forceinline__ void gemm_body(Sched& sched, float* ws, int32_t* tick
           }
           const uint32_t sa = sbase + stage * C::STAGE_BYTES;
           const uint32_t sb = sa + C::A_BYTES;
+          if constexpr (P2) {
+            // Both CTAs' loads complete on the even CTA's full barrier, which expects both halves.
+            if (sched.rank == 0) mbar_arrive_expect_tx(full_bar(stage), 2 * C::STAGE_BYTES);
+            const uint32_t fb = mapa_shared(full_bar(stage), 0);
+            tma_load_2d_pair(sa, w.a, fb, kb * kBK, w.tm * BM);
+#pragma unroll
+            for (int j = 0; j < BN / 128; ++j)
+              tma_load_2d_pair(sb + j * (kBK * 128), w.b, fb, w.tn * BN + sched.rank * (BN / 2) + j * 64, kb * kBK);
+          } else {
           mbar_arrive_expect_tx(full_bar(stage), C::STAGE_BYTES);
           if constexpr (Sched::kMulticast == 2) {  // A shared: this CTA's half of the rows, to both
             tma_load_2d_multicast(sa + sched.rank * (BM / 2) * 128, w.a, full_bar(stage), kb * kBK,
@@ -483,6 +510,7 @@ __device__ __forceinline__ void gemm_body(Sched& sched, float* ws, int32_t* tick
               tma_load_2d(sb + j * (kBK * 128), w.b, full_bar(stage), w.tn * BN + j * 64, kb * kBK);
             }
           }
+          }
           issued_mask |= 1u << stage;
           issued_ph = (issued_ph & ~(1u << stage)) | (ph << stage);
           if (++stage == STAGES) {
@@ -496,8 +524,16 @@ __device__ __forceinline__ void gemm_body(Sched& sched, float* ws, int32_t* tick
         *abort_flag = 1;
       }
       // no TMA write may still be landing when the CTA exits
-      for (int i = 0; i < STAGES; ++i)
-        if (issued_mask & (1u << i)) mbar_wait(full_bar(i), (issued_ph >> i) & 1u, kDrainCycles, no_abort);
+      if (!P2 || sched.rank == 0) {
+        for (int i = 0; i < STAGES; ++i)
+          if (issued_mask & (1u << i)) mbar_wait(full_bar(i), (issued_ph >> i) & 1u, kDrainCycles, no_abort);
+      } else if (!ok) {
+        // The odd CTA's loads complete on its partner's barriers; after an abort it
+        // gives them a bounded time to land (normally every one of them was consumed).
+        const long long t0 = clock64();
+        while (clock64() - t0 < (kDrainCycles >> 6)) {
+        }
+      }
     }
   } else if (warp == 1) {
     // ------------------------------------------------ MMA issuer (one thread)
@@ -505,7 +541,9 @@ __device__ __forceinline__ void gemm_body(Sched& sched, float* ws, int32_t* tick
     uint32_t ph = 0, aph = 0;
     bool ok = true;
     if (stall) ok = __all_sync(FULL, mbar_wait(drain_bar, 0, timeout, abort_flag));
-    for (int i = 0; ok && i < nunits; ++i) {
+    // a pair's odd CTA issues nothing: the even CTA's MMAs read and write both
+    const int issue_units = (!P2 || sched.rank == 0) ? nunits : 0;
+    for (int i = 0; ok && i < issue_units; ++i) {
       const Unit w = sched.unit(i);
       const int kb0 = w.kb0, kb1 = w.kb1;
       ok = __all_sync(FULL, mbar_wait(tempty_bar(acc), aph ^ 1u, timeout, abort_flag));
@@ -527,10 +565,15 @@ __device__ __forceinline__ void gemm_body(Sched& sched, float* ws, int32_t* tick
 #pragma unroll
             for (int h = 0; h < C::HALVES; ++h) {
               const uint64_t adesc = smem_desc_sw128(sa + h * (128 * 128) + k * 32, 16, 1024);
-              mma_f16(d0 + h * BN, adesc, bdesc, C::IDESC, (kb > kb0 || k > 0) ? 1u : 0u);
+              if constexpr (P2)
+                mma_f16_pair(d0, adesc, bdesc, C::IDESC, (kb > kb0 || k > 0) ? 1u : 0u);
+              else
+                mma_f16(d0 + h * BN, adesc, bdesc, C::IDESC, (kb > kb0 || k > 0) ? 1u : 0u);
             }
           }
-          if constexpr (Sched::kMulticast != 0)
+          if constexpr (P2)
+            mma_commit_pair_multicast(empty_bar(stage), 3);  // the stage is free in both CTAs
+          else if constexpr (Sched::kMulticast != 0)
             mma_commit_multicast(empty_bar(stage), 3);  // releases the stage in both CTAs of the pair
           else
             mma_commit(empty_bar(stage));
@@ -545,6 +588,8 @@ __device__ __forceinline__ void gemm_body(Sched& sched, float* ws, int32_t* tick
       if (lane == 0) {
         if constexpr (Sched::kMemOnly)
           mbar_arrive(tfull_bar(acc));
+        else if constexpr (P2)
+          mma_commit_pair_multicast(tfull_bar(acc), 3);  // both CTAs' halves of the accumulator are final
         else
           mma_commit(tfull_bar(acc));
       }
@@ -558,7 +603,10 @@ __device__ __forceinline__ void gemm_body(Sched& sched, float* ws, int32_t* tick
       if (lane == 0) {
         atomicExch(err, kErrMma);
         *abort_flag = 1;
-        mma_commit(drain_bar);  // completes once every issued MMA has finished
+        if constexpr (P2)
+          mma_commit_pair(drain_bar);
+        else
+          mma_commit(drain_bar);  // completes once every issued MMA has finished
       }
       __syncwarp();
       mbar_wait(drain_bar, 0, kDrainCycles, no_abort);
@@ -701,7 +749,12 @@ __device__ __forceinline__ void gemm_body(Sched& sched, float* ws, int32_t* tick
       }
       tc_fence_before();
       __syncwarp();
-      if (lane == 0) mbar_arrive(tempty_bar(acc));
+      if (lane == 0) {
+        if constexpr (P2)
+          mbar_arrive_cluster(mapa_shared(tempty_bar(acc), 0));  // the even CTA's MMA reuses it
+        else
+          mbar_arrive(tempty_bar(acc));
+      }
       if (++acc == C::NBUF) {
         acc = 0;
         aph ^= 1u;
@@ -718,11 +771,15 @@ __device__ __forceinline__ void gemm_body(Sched& sched, float* ws, int32_t* tick
   }
 
   __syncthreads();
-  // no CTA of a pair exits while its partner may still multicast into it or arrive on its barriers
-  if constexpr (Sched::kMulticast != 0) cluster_sync();
+  // no CTA of a pair exits while its partner may still multicast into it, arrive on
+  // its barriers or (cta_group::2) run MMAs on its shared memory and TMEM
+  if constexpr (Sched::kMulticast != 0 || P2) cluster_sync();
   if (warp == 1) {
     tc_fence_after();
-    tmem_dealloc(tmem_base, C::TMEM_COLS);
+    if constexpr (P2)
+      tmem_dealloc_pair(tmem_base, C::TMEM_COLS);
+    else
+      tmem_dealloc(tmem_base, C::TMEM_COLS);
   }
 }
 
@@ -766,6 +823,17 @@ __global__ void __launch_bounds__(kThreads, 1)
   gemm_body<BM, BN, STAGES>(sched, args.ws, args.tickets, args.err, args.timeout, args.stall);
 }
 
+// cta_group::2: 2-CTA clusters, each pair one 256 x BN output tile (128 rows per CTA).
+template <int BN, int STAGES>
+__global__ void __launch_bounds__(kThreads, 1)
+    gemm_bf16_2sm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                         const __grid_constant__ CUtensorMap tmC, const __grid_constant__ CUtensorMap tmW,
+                         const GemmArgs args) {
+  PairSched<1, true> sched{&tmA, &tmB, &tmC, &tmW, args.tiles_m, args.tiles_n, args.kblocks, args.M, args.N,
+                           args.beta};
+  gemm_body<128, BN, STAGES>(sched, args.ws, args.tickets, args.err, args.timeout, args.stall);
+}
+
 template <int BM, int BN, int STAGES>
 __global__ void __launch_bounds__(kThreads, 1)
     gemm_bf16_grouped_kernel(const GroupHeader* __restrict__ hdr, const GroupItem* __restrict__ items, int32_t* err,
@@ -796,15 +864,26 @@ struct TileKernel {
   int pair_mode;  // 1: pairs along M share B; 2: pairs along N share A
   int bm, bn, smem;
   KernFn mem;     // memory twin (loads and stores, no MMA)
+  KernFn two_sm;  // cta_group::2 instance (256-row tiles with BN >= 128), else null
+  int smem2;
 };
+
+// Stages of the cta_group::2 instances: 16 KB of A + BN/2 x 64 of B per stage and CTA.
+template <int BN>
+constexpr int kStages2Sm = BN == 256 ? 6 : 8;
 
 // The pair shares whichever operand tile is larger per K block (B when BN >= BM).
 template <int BM, int BN, int ST>
 TileKernel make_tile_kernel() {
   constexpr int mode = BN >= BM ? 1 : 2;
-  return TileKernel{gemm_bf16_kernel<BM, BN, ST>, gemm_bf16_streamk_kernel<BM, BN, ST>,
-                    gemm_bf16_pair_kernel<BM, BN, ST, mode>, mode, BM, BN, KCfg<BM, BN, ST>::SMEM_BYTES,
-                    gemm_bf16_memtwin_kernel<BM, BN, ST>};
+  TileKernel t{gemm_bf16_kernel<BM, BN, ST>, gemm_bf16_streamk_kernel<BM, BN, ST>,
+               gemm_bf16_pair_kernel<BM, BN, ST, mode>, mode, BM, BN, KCfg<BM, BN, ST>::SMEM_BYTES,
+               gemm_bf16_memtwin_kernel<BM, BN, ST>, nullptr, 0};
+  if constexpr (BM == 256 && BN >= 128) {
+    t.two_sm = gemm_bf16_2sm_kernel<BN, kStages2Sm<BN>>;
+    t.smem2 = KCfg<128, BN, kStages2Sm<BN>, 2>::SMEM_BYTES;
+  }
+  return t;
 }
 
 using GroupedFn = void (*)(const GroupHeader*, const GroupItem*, int32_t*, long long);
@@ -933,6 +1012,7 @@ static int prepare(rg_ctx* ctx, int64_t M, int64_t N, int64_t K, const void* A, 
   const int tile = variant_tile(variant);
   const bool sk = variant_streamk(variant);
   const bool pair = variant_pair(variant);
+  const bool two = variant_2sm(variant);
   const int splits = variant_split(variant);
   const TileKernel& tk = tile_kernel(tile);
   const int64_t tiles_m = (pm + tk.bm - 1) / tk.bm;
@@ -952,7 +1032,8 @@ static int prepare(rg_ctx* ctx, int64_t M, int64_t N, int64_t K, const void* A, 
       return fail(RG_ERR_SHAPE, "split-K workspace too small for this shape");
   }
   // pairs load the shared operand as two half boxes (half its rows each)
-  const bool half_a = pair && tk.pair_mode == 2, half_b = pair && tk.pair_mode == 1;
+  // (cta_group::2: each CTA loads its own 128 rows of A and 64-column boxes of B)
+  const bool half_a = (pair && tk.pair_mode == 2) || two, half_b = pair && tk.pair_mode == 1;
   rc = make_map(&L->a, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, A, K, M, lda * 2, kBK, half_a ? tk.bm / 2 : tk.bm);
   if (rc == RG_OK)
     rc = make_map(&L->b, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, B, N, K, ldb * 2, 64, half_b ? kBK / 2 : kBK);
@@ -965,14 +1046,14 @@ static int prepare(rg_ctx* ctx, int64_t M, int64_t N, int64_t K, const void* A, 
       L->w = L->c;  // unused without split-K
   }
   if (rc != RG_OK) return rc;
-  L->fn = sk ? tk.sk : pair ? tk.pair : tk.fn;
-  L->cluster = pair ? 2 : 1;
-  L->smem = tk.smem;
+  L->fn = sk ? tk.sk : pair ? tk.pair : two ? tk.two_sm : tk.fn;
+  L->cluster = (pair || two) ? 2 : 1;
+  L->smem = two ? tk.smem2 : tk.smem;
   L->ws_slots = slots;
   GemmArgs& g = L->args;
   g.M = static_cast<int32_t>(M);
   g.N = static_cast<int32_t>(N);
-  g.tiles_m = static_cast<int32_t>(tiles_m);
+  g.tiles_m = static_cast<int32_t>(two ? 2 * tiles_m : tiles_m);  // cta_group::2: 128-row tiles
   g.tiles_n = static_cast<int32_t>(tiles_n);
   g.splits = sk ? static_cast<int32_t>(skg.tail_ctas) : splits;  // stream-K: CTAs sharing the tail tiles
   g.dp_tiles = sk ? static_cast<int32_t>(skg.dp_tiles) : 0;
@@ -984,7 +1065,9 @@ static int prepare(rg_ctx* ctx, int64_t M, int64_t N, int64_t K, const void* A, 
   g.timeout = ctx->timeout;
   g.stall = ctx->stall;
   const int64_t units = tiles_m * tiles_n * splits;
-  if (pair) {  // 2-CTA clusters, one per pair of tiles, at most one CTA per SM
+  if (two) {  // one 2-CTA cluster per 256-row tile, at most one CTA per SM
+    L->grid = dim3(static_cast<unsigned>(2 * std::min<int64_t>(tiles_m * tiles_n, ctx->sm_count / 2)));
+  } else if (pair) {  // 2-CTA clusters, one per pair of tiles, at most one CTA per SM
     const int64_t pairs = tk.pair_mode == 1 ? ((tiles_m + 1) / 2) * tiles_n : tiles_m * ((tiles_n + 1) / 2);
     L->grid = dim3(static_cast<unsigned>(2 * std::min<int64_t>(pairs, ctx->sm_count / 2)));
   } else {
@@ -1184,6 +1267,8 @@ extern "C" int rg_init(int device, int64_t workspace_bytes, rg_ctx** out) {
                                   tk.smem)) != cudaSuccess ||
         (e = cudaFuncSetAttribute(reinterpret_cast<const void*>(tk.mem), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   tk.smem)) != cudaSuccess ||
+        (tk.two_sm && (e = cudaFuncSetAttribute(reinterpret_cast<const void*>(tk.two_sm),
+                                                cudaFuncAttributeMaxDynamicSharedMemorySize, tk.smem2)) != cudaSuccess) ||
         (e = cudaFuncSetAttribute(reinterpret_cast<const void*>(rg::grouped_kernel(t)),
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, tk.smem)) != cudaSuccess) {
       delete ctx;
@@ -1341,6 +1426,11 @@ static int sweep_impl(rg_ctx* ctx, const rg_grid* grid, int32_t n_variants, cons
     const int32_t v = variant_ids[item / cells];
     const int S = rg::variant_split(v);
     const bool sk = rg::variant_streamk(v);
+    if (rg::variant_2sm(v)) {  // a 256-row pair tile is worth it only beyond 128 rows
+      int64_t M, N, K;
+      dims(item, &M, &N, &K);
+      return M <= 128;
+    }
     if (rg::variant_pair(v)) {  // a pair needs a partner tile
       int64_t M, N, K;
       dims(item, &M, &N, &K);
@@ -1637,6 +1727,11 @@ static int noalloc_setup(int dev, NoallocDevice** out) {
       const TileKernel& tk = tile_kernel(t);
       for (KernFn fn : {tk.fn, tk.sk, tk.pair}) {
         e = cudaFuncSetAttribute(reinterpret_cast<const void*>(fn), cudaFuncAttributeMaxDynamicSharedMemorySize, tk.smem);
+        if (e != cudaSuccess) return cuda_fail(e, "rg_gemm_noalloc: shared-memory attribute");
+      }
+      if (tk.two_sm) {
+        e = cudaFuncSetAttribute(reinterpret_cast<const void*>(tk.two_sm), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 tk.smem2);
         if (e != cudaSuccess) return cuda_fail(e, "rg_gemm_noalloc: shared-memory attribute");
       }
     }

@@ -31,16 +31,22 @@ RG_ERR_NO_DEVICE = -9
 RG_T_UNMEASURED = 1 << 60
 RG_NUM_TILES = 6
 RG_NUM_SPLITS = 4
-RG_NUM_VARIANTS = RG_NUM_TILES * RG_NUM_SPLITS + 2 * RG_NUM_TILES
+RG_NUM_VARIANTS = RG_NUM_TILES * RG_NUM_SPLITS + 2 * RG_NUM_TILES + 2
 TILES = [(128, 64), (128, 128), (128, 256), (256, 64), (256, 128), (256, 256)]
 SPLITS = [1, 2, 4, 8]
 SK = "SK"
 PAIR = "PR"
+TWO_SM = "2SM"
+_BASE_2SM = RG_NUM_TILES * RG_NUM_SPLITS + 2 * RG_NUM_TILES
 
 
 def variant(tile: int, split=1) -> int:
-    """Variant id of a tile with split factor 1/2/4/8, split="SK" for stream-K or "PR" for the
-    2-CTA multicast pair."""
+    """Variant id of a tile with split factor 1/2/4/8, split="SK" for stream-K, "PR" for the
+    2-CTA multicast pair or "2SM" for the cta_group::2 pair (tiles 256x128 and 256x256 only)."""
+    if split == TWO_SM:
+        if tile not in (4, 5):
+            raise ValueError("the 2-SM variant exists for the 256x128 and 256x256 tiles only")
+        return _BASE_2SM + tile - 4
     if split == SK:
         return RG_NUM_TILES * RG_NUM_SPLITS + tile
     if split == PAIR:
@@ -51,10 +57,15 @@ def variant(tile: int, split=1) -> int:
 def variant_tile(v: int) -> int:
     """Tile index (0..5) of a variant id."""
     n = RG_NUM_TILES * RG_NUM_SPLITS
+    if v >= _BASE_2SM:
+        return 4 + v - _BASE_2SM
     return v - n - RG_NUM_TILES if v >= n + RG_NUM_TILES else v - n if v >= n else v // RG_NUM_SPLITS
 
 
 def variant_name(v: int) -> str:
+    if v >= _BASE_2SM:
+        bm, bn = TILES[4 + v - _BASE_2SM]
+        return f"{bm}x{bn}/2SM"
     if v >= RG_NUM_TILES * RG_NUM_SPLITS + RG_NUM_TILES:
         bm, bn = TILES[v - RG_NUM_TILES * RG_NUM_SPLITS - RG_NUM_TILES]
         return f"{bm}x{bn}/PR"

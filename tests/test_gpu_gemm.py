@@ -11,7 +11,7 @@ from oracle import gemm as og
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-ALL_VARIANTS = list(range(36))          # 24 split-K variants, 6 stream-K, 6 multicast pairs
+ALL_VARIANTS = list(range(38))          # 24 split-K variants, 6 stream-K, 6 multicast pairs, 2 cta_group::2
 
 
 @pytest.fixture(scope="module")
@@ -222,3 +222,50 @@ def test_pair_beta_one(rg, ctx, tile):
     a, b = synthetic.operands_bf16(M, N, K, seed=15)
     c0 = synthetic.normal_stream_f32(15, 5, M * N).reshape(M, N)
     check(run(rg, ctx, a, b, rg.variant(tile, rg.PAIR), beta=1, c0=c0), a, b, c0=c0)
+
+
+@pytest.mark.parametrize("tile", [4, 5])
+@pytest.mark.parametrize("shape", [(384, 640, 1024), (1664, 1664, 2048), (128, 64, 256), (200, 264, 96),
+                                   (4096, 1152, 4096)])
+def test_two_sm(rg, ctx, tile, shape):
+    """cta_group::2 pairs (one 256-row tile per 2-CTA cluster, B split by columns between
+    the CTAs): ragged edges, an odd CTA wholly past M, and a full-height case; bitwise
+    equal to the 1-CTA kernel of the same tile."""
+    M, N, K = shape
+    a, b = synthetic.operands_bf16(M, N, K, seed=16)
+    c = run(rg, ctx, a, b, rg.variant(tile, rg.TWO_SM))
+    if M * N * K <= 1024 * 1024 * 1024:
+        check(c, a, b)
+    else:
+        rs = np.random.default_rng(1)
+        rows, cols = rs.choice(M, 8, replace=False), rs.choice(N, 8, replace=False)
+        A64, B64 = og.bf16_bits_to_f64(a), og.bf16_bits_to_f64(b)
+        cr, sr, cc, sc = og.sampled_rows_cols(A64, B64, rows, cols)
+        for got, ref, s in ((c[rows, :], cr, sr), (c[:, cols], cc, sc)):
+            ratio, exact_zero = og.error_ratio(got, ref, s)
+            assert exact_zero and ratio <= og.bound(K), ratio
+    # the pair computes every output element with the same MMA sequence as the 1-CTA kernel
+    assert np.array_equal(c, run(rg, ctx, a, b, rg.variant(tile, 1)))
+
+
+@pytest.mark.parametrize("tile", [4, 5])
+def test_two_sm_exact_cases_beta_and_padding(rg, ctx, tile):
+    v = rg.variant(tile, rg.TWO_SM)
+    one = np.float32(1.0).view(np.uint32) >> 16
+    K = 256
+    eye = np.zeros((K, K), np.uint16)
+    eye[np.arange(K), np.arange(K)] = one
+    _, b = synthetic.operands_bf16(K, 320, K, seed=2)
+    assert np.array_equal(run(rg, ctx, eye, b, v), og.bf16_bits_to_f64(b).astype(np.float32))
+    ones_a = np.full((392, 384), one, np.uint16)
+    ones_b = np.full((384, 136), one, np.uint16)
+    assert np.all(run(rg, ctx, ones_a, ones_b, v) == 384.0)
+    M, N, K = 640, 384, 1536
+    a, b = synthetic.operands_bf16(M, N, K, seed=15)
+    c0 = synthetic.normal_stream_f32(15, 5, M * N).reshape(M, N)
+    check(run(rg, ctx, a, b, v, beta=1, c0=c0), a, b, c0=c0)
+    M, N, K = 256, 384, 256
+    a, b = synthetic.operands_bf16(M, N, K, seed=5)
+    c_plain = run(rg, ctx, a, b, v)
+    check(c_plain, a, b)
+    assert np.array_equal(c_plain, run(rg, ctx, a, b, v, pads=(M + 256, N + 128, K + 384)))
