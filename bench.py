@@ -445,13 +445,17 @@ def kernel_source_hash():
     return hashlib.sha256((open(os.path.join(csrc, "ptx.cuh")).read() + kern).encode()).hexdigest()
 
 
+CAPTURE_PROFILE = "gemm_bf16_256x256_2sm_8192x8192x4096"   # profiles/<name>.md and .json
+CAPTURE_VARIANT = "256x256/2SM"
+
+
 def roofline_capture(rg, ctx, p_burst, dev, reps=10):
-    """The kernel and shape of profiles/gemm_bf16_256x256_8192x8192x4096: timed live here, DRAM traffic
-    from that ncu capture (null once the kernel source differs from the captured one)."""
+    """The kernel and shape of profiles/<CAPTURE_PROFILE>: timed live here, DRAM traffic from that ncu
+    capture (null once the kernel source differs from the captured one)."""
     import torch
-    prof = json.load(open(os.path.join(ROOT, "profiles", "gemm_bf16_256x256_8192x8192x4096.json")))
+    prof = json.load(open(os.path.join(ROOT, "profiles", CAPTURE_PROFILE + ".json")))
     M, N, K = prof["shape"]
-    v = rg.variant(5, 1)
+    v = {rg.variant_name(x): x for x in range(rg.RG_NUM_VARIANTS)}[CAPTURE_VARIANT]
     A = torch.from_numpy(synthetic.bf16_uniform_stream(0, 1, M * K).view(np.int16)).to(dev).view(torch.bfloat16)
     B = torch.from_numpy(synthetic.bf16_uniform_stream(0, 2, K * N).view(np.int16)).to(dev).view(torch.bfloat16)
     C = torch.empty((M, N), device=dev)
@@ -472,7 +476,7 @@ def roofline_capture(rg, ctx, p_burst, dev, reps=10):
             "unit": "TFLOP/s", "frac": ach / p_burst, "traffic": traffic,
             "algorithmic_bytes": 2 * M * K + 2 * K * N + 4 * M * N,
             "note": "10 back-to-back launches between CUDA events; inputs 384 MiB > L2; traffic = ncu "
-                    "dram__bytes_read.sum + dram__bytes_write.sum per launch (profiles/gemm_bf16_256x256_8192x8192x4096.md)"}
+                    f"dram__bytes_read.sum + dram__bytes_write.sum per launch (profiles/{CAPTURE_PROFILE}.md)"}
 
 
 def extras(args, rg, ctx, grid, T0v, plan_smooth, A, B, C, flops, Mv, Nv, Kv, dev, a_bits, b_bits, s1_rows,

@@ -76,13 +76,16 @@ enum {
  * A otherwise, pairs along N); each CTA loads half of the shared tile and TMA
  * multicasts it to both, halving that operand's L2 reads. */
 #define RG_VARIANT_PAIR(tile) (RG_NUM_TILES * RG_NUM_SPLITS + RG_NUM_TILES + (tile))
-/* 2-SM variant of a 256-row tile (ids 36 for 256x128, 37 for 256x256): a 2-CTA
- * cluster computes one 256 x BN tile as a single tcgen05 cta_group::2 MMA unit;
- * each CTA loads 128 rows of A and BN/2 columns of B and holds its 128 output
- * rows in its own TMEM, so each SM moves 128 x BK + BN/2 x BK operand elements
- * per K block instead of 256 x BK + BN x BK.  Split 1. */
-#define RG_VARIANT_2SM(tile) (RG_NUM_TILES * RG_NUM_SPLITS + 2 * RG_NUM_TILES + (tile) - RG_TILE_256x128)
-#define RG_NUM_VARIANTS (RG_NUM_TILES * RG_NUM_SPLITS + 2 * RG_NUM_TILES + 2)
+/* 2-SM variant of a 256-row tile (ids 36..39 for 256x128, 40..43 for 256x256,
+ * split-K 1/2/4/8): a 2-CTA cluster computes one 256 x BN tile as a single
+ * tcgen05 cta_group::2 MMA unit; each CTA loads 128 rows of A and BN/2 columns
+ * of B and holds its 128 output rows in its own TMEM, so each SM moves
+ * 128 x BK + BN/2 x BK operand elements per K block instead of 256 x BK + BN x BK.
+ * With split-K each CTA publishes and reduces its own 128 rows as in the 1-CTA
+ * kernels (same workspace, tickets and fixed summation order). */
+#define RG_VARIANT_2SM(tile, log2_split) \
+  (RG_NUM_TILES * RG_NUM_SPLITS + 2 * RG_NUM_TILES + ((tile) - RG_TILE_256x128) * RG_NUM_SPLITS + (log2_split))
+#define RG_NUM_VARIANTS (RG_NUM_TILES * RG_NUM_SPLITS + 2 * RG_NUM_TILES + 2 * RG_NUM_SPLITS)
 
 typedef struct rg_ctx rg_ctx;
 typedef struct rg_plan rg_plan;

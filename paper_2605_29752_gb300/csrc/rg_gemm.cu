@@ -61,7 +61,7 @@ struct GemmArgs {
   int32_t beta;
   int32_t stall;            // test hook: the MMA warp first waits on a barrier nothing arrives on
   int32_t dp_tiles;         // stream-K: tiles run whole before the shared tail
-  int32_t reserved_;
+  int32_t panel;            // tile order: column panels of this many tiles (pairs: tile columns)
   float* ws;                // split-K partials [split][tile][BM][BN]
   int32_t* tickets;         // [tile][4], zero between launches
   int32_t* err;
@@ -147,9 +147,27 @@ struct Unit {
   int tile, ntiles;  // tile id / tile count of the problem (split-K workspace and tickets)
 };
 
+// Tile order: the tile grid is cut into column panels `panel` tiles wide and
+// walked row by row inside each panel, so the tiles resident at one time share a
+// panel of B that stays in L2 while A streams past.  panel >= tiles_n is plain
+// row-major order.
+__device__ __forceinline__ void tile_coords(int tile, int tiles_m, int tiles_n, int panel, int& tm, int& tn) {
+  if (panel >= tiles_n) {
+    tm = tile / tiles_n;
+    tn = tile % tiles_n;
+    return;
+  }
+  const int per = panel * tiles_m;
+  const int p = tile / per;
+  const int w = min(panel, tiles_n - p * panel);
+  const int r = tile - p * per;
+  tm = r / w;
+  tn = p * panel + r % w;
+}
+
 __device__ __forceinline__ Unit split_unit(const CUtensorMap* a, const CUtensorMap* b, const CUtensorMap* c,
                                            const CUtensorMap* w, int u, int tiles_m, int tiles_n, int splits,
-                                           int kblocks, int M, int N, int beta) {
+                                           int kblocks, int M, int N, int beta, int panel) {
   Unit x;
   x.a = a;
   x.b = b;
@@ -158,8 +176,7 @@ __device__ __forceinline__ Unit split_unit(const CUtensorMap* a, const CUtensorM
   x.tile = u / splits;
   x.s = u % splits;
   x.splits = splits;
-  x.tm = x.tile / tiles_n;
-  x.tn = x.tile % tiles_n;
+  tile_coords(x.tile, tiles_m, tiles_n, panel, x.tm, x.tn);
   x.kb0 = static_cast<int>(static_cast<long long>(x.s) * kblocks / splits);
   x.kb1 = static_cast<int>(static_cast<long long>(x.s + 1) * kblocks / splits);
   x.M = M;
@@ -181,6 +198,7 @@ struct SingleSched {
   const CUtensorMap* c;
   const CUtensorMap* w;
   int tiles_m, tiles_n, splits, kblocks, M, N, beta;
+  int panel = 1 << 30;
   __device__ __forceinline__ void prefetch() const {
     prefetch_tmap(a);
     prefetch_tmap(b);
@@ -195,7 +213,7 @@ struct SingleSched {
   }
   __device__ __forceinline__ Unit unit(int i) const {
     return split_unit(a, b, c, w, static_cast<int>(blockIdx.x) + i * static_cast<int>(gridDim.x), tiles_m, tiles_n,
-                      splits, kblocks, M, N, beta);
+                      splits, kblocks, M, N, beta, panel);
   }
 };
 
@@ -227,6 +245,7 @@ struct StreamKSched {
   int tiles_m, tiles_n, kblocks, M, N, beta;
   int tail = 0;      // CTAs sharing the tail tiles (from the launcher)
   int dp_tiles = 0;  // tiles run whole (from the launcher)
+  int panel = 1 << 30;
   long long iters = 0, begin = 0, end = 0;
   int G = 1, g = 0, T = 0, n_dp = 0, t0 = 0, n_sk = 0;
   __device__ __forceinline__ void prefetch() const {
@@ -287,8 +306,7 @@ struct StreamKSched {
       x.splits = last - first + 1;
       x.s = g - first;
     }
-    x.tm = x.tile / tiles_n;
-    x.tn = x.tile % tiles_n;
+    tile_coords(x.tile, tiles_m, tiles_n, panel, x.tm, x.tn);
     return x;
   }
 };
@@ -316,6 +334,8 @@ struct PairSched {
   const CUtensorMap* w;
   int tiles_m, tiles_n, kblocks, M, N, beta;
   int rank = 0, cid = 0, ncl = 1, pairs = 0, pn_count = 1;
+  int splits = 1;  // TWO_SM: K splits per pair tile (units = pairs x splits)
+  int panel = 1 << 30;
   __device__ __forceinline__ void prefetch() const {
     prefetch_tmap(a);
     prefetch_tmap(b);
@@ -328,25 +348,33 @@ struct PairSched {
     pn_count = MODE == 1 ? tiles_n : (tiles_n + 1) / 2;
     pairs = (MODE == 1 ? (tiles_m + 1) / 2 : tiles_m) * pn_count;
   }
-  __device__ __forceinline__ int count() const { return cid < pairs ? (pairs - 1 - cid) / ncl + 1 : 0; }
+  __device__ __forceinline__ int count() const {
+    const int units = pairs * splits;
+    return cid < units ? (units - 1 - cid) / ncl + 1 : 0;
+  }
   __device__ __forceinline__ Unit unit(int i) const {
-    const int p = cid + i * ncl;
+    const int u = cid + i * ncl;
+    const int p = u / splits;
     Unit x;
     x.a = a;
     x.b = b;
     x.c = c;
     x.w = w;
+    // the pair grid: (tiles_m + 1) / 2 x tiles_n pairs (MODE 1) or tiles_m x pn_count pairs (MODE 2)
+    int pr, pc;
     if (MODE == 1) {
-      x.tm = 2 * (p / pn_count) + rank;
-      x.tn = p % pn_count;
+      tile_coords(p, (tiles_m + 1) / 2, pn_count, panel, pr, pc);
+      x.tm = 2 * pr + rank;
+      x.tn = pc;
     } else {
-      x.tm = p / pn_count;
-      x.tn = 2 * (p % pn_count) + rank;
+      tile_coords(p, tiles_m, pn_count, panel > 1 ? panel / 2 : 1, pr, pc);
+      x.tm = pr;
+      x.tn = 2 * pc + rank;
     }
-    x.kb0 = 0;
-    x.kb1 = kblocks;
-    x.splits = 1;
-    x.s = 0;
+    x.s = u % splits;
+    x.splits = splits;
+    x.kb0 = static_cast<int>(static_cast<long long>(x.s) * kblocks / splits);
+    x.kb1 = static_cast<int>(static_cast<long long>(x.s + 1) * kblocks / splits);
     x.M = M;
     x.N = N;
     x.beta = beta;
@@ -400,7 +428,7 @@ struct GroupSched {
     }
     const GroupItem& it = items[lo];
     return split_unit(&it.a, &it.b, &it.c, nullptr, u - it.tile_start, it.tiles_m, it.tiles_n, 1, it.kblocks, it.M,
-                      it.N, it.beta);
+                      it.N, it.beta, it.tiles_n);
   }
 };
 
@@ -791,6 +819,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                      const GemmArgs args) {
   SingleSched sched{&tmA,        &tmB,          &tmC,   &tmW,  args.tiles_m, args.tiles_n,
                     args.splits, args.kblocks, args.M, args.N, args.beta};
+  sched.panel = args.panel;
   gemm_body<BM, BN, STAGES>(sched, args.ws, args.tickets, args.err, args.timeout, args.stall);
 }
 
@@ -801,6 +830,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                              const GemmArgs args) {
   MemTwinSched sched{{&tmA,        &tmB,          &tmC,   &tmW,  args.tiles_m, args.tiles_n,
                       args.splits, args.kblocks, args.M, args.N, args.beta}};
+  sched.panel = args.panel;
   gemm_body<BM, BN, STAGES>(sched, args.ws, args.tickets, args.err, args.timeout, args.stall);
 }
 
@@ -811,6 +841,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                              const GemmArgs args) {
   StreamKSched sched{&tmA,        &tmB,   &tmC,   &tmW,      args.tiles_m, args.tiles_n, args.kblocks,
                      args.M,      args.N, args.beta, args.splits /* CTAs sharing the tail */, args.dp_tiles};
+  sched.panel = args.panel;
   gemm_body<BM, BN, STAGES>(sched, args.ws, args.tickets, args.err, args.timeout, args.stall);
 }
 
@@ -820,6 +851,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                           const __grid_constant__ CUtensorMap tmC, const __grid_constant__ CUtensorMap tmW,
                           const GemmArgs args) {
   PairSched<MODE> sched{&tmA, &tmB, &tmC, &tmW, args.tiles_m, args.tiles_n, args.kblocks, args.M, args.N, args.beta};
+  sched.panel = args.panel;
   gemm_body<BM, BN, STAGES>(sched, args.ws, args.tickets, args.err, args.timeout, args.stall);
 }
 
@@ -831,6 +863,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                          const GemmArgs args) {
   PairSched<1, true> sched{&tmA, &tmB, &tmC, &tmW, args.tiles_m, args.tiles_n, args.kblocks, args.M, args.N,
                            args.beta};
+  sched.splits = args.splits;
+  sched.panel = args.panel;
   gemm_body<128, BN, STAGES>(sched, args.ws, args.tickets, args.err, args.timeout, args.stall);
 }
 
@@ -1028,7 +1062,7 @@ static int prepare(rg_ctx* ctx, int64_t M, int64_t N, int64_t K, const void* A, 
   const bool uses_ws = slots > 1;
   if (uses_ws) {
     const int64_t need = slots * tiles_m * tiles_n * tk.bm * tk.bn * 4;
-    if (need > ctx->ws_bytes || tiles_m * tiles_n * 4 > kMaxTickets)
+    if (need > ctx->ws_bytes || (two ? 2 : 1) * tiles_m * tiles_n * 4 > kMaxTickets)
       return fail(RG_ERR_SHAPE, "split-K workspace too small for this shape");
   }
   // pairs load the shared operand as two half boxes (half its rows each)
@@ -1058,6 +1092,11 @@ static int prepare(rg_ctx* ctx, int64_t M, int64_t N, int64_t K, const void* A, 
   g.splits = sk ? static_cast<int32_t>(skg.tail_ctas) : splits;  // stream-K: CTAs sharing the tail tiles
   g.dp_tiles = sk ? static_cast<int32_t>(skg.dp_tiles) : 0;
   g.kblocks = static_cast<int32_t>(kblocks);
+  {
+    // column panels whose B slice (panel tiles x padded K, BF16) is at most 32 MiB
+    const int64_t bcol = std::max<int64_t>(1, kblocks * kBK * tk.bn * 2);
+    g.panel = static_cast<int32_t>(std::max<int64_t>(1, std::min<int64_t>(tiles_n, (32LL << 20) / bcol)));
+  }
   g.beta = beta;
   g.ws = ctx->ws;
   g.tickets = ctx->tickets;
@@ -1065,8 +1104,8 @@ static int prepare(rg_ctx* ctx, int64_t M, int64_t N, int64_t K, const void* A, 
   g.timeout = ctx->timeout;
   g.stall = ctx->stall;
   const int64_t units = tiles_m * tiles_n * splits;
-  if (two) {  // one 2-CTA cluster per 256-row tile, at most one CTA per SM
-    L->grid = dim3(static_cast<unsigned>(2 * std::min<int64_t>(tiles_m * tiles_n, ctx->sm_count / 2)));
+  if (two) {  // one 2-CTA cluster per (256-row tile, split), at most one CTA per SM
+    L->grid = dim3(static_cast<unsigned>(2 * std::min<int64_t>(tiles_m * tiles_n * splits, ctx->sm_count / 2)));
   } else if (pair) {  // 2-CTA clusters, one per pair of tiles, at most one CTA per SM
     const int64_t pairs = tk.pair_mode == 1 ? ((tiles_m + 1) / 2) * tiles_n : tiles_m * ((tiles_n + 1) / 2);
     L->grid = dim3(static_cast<unsigned>(2 * std::min<int64_t>(pairs, ctx->sm_count / 2)));
@@ -1429,7 +1468,11 @@ static int sweep_impl(rg_ctx* ctx, const rg_grid* grid, int32_t n_variants, cons
     if (rg::variant_2sm(v)) {  // a 256-row pair tile is worth it only beyond 128 rows
       int64_t M, N, K;
       dims(item, &M, &N, &K);
-      return M <= 128;
+      if (M <= 128) return true;
+      if (S == 1) return false;
+      const rg::TileShape ts = rg::tile_shape(rg::variant_tile(v));
+      const int64_t ctas = 2 * ((M + ts.bm - 1) / ts.bm) * ((N + ts.bn - 1) / ts.bn);
+      return ctas >= ctx->sm_count || (K + rg::kBK - 1) / rg::kBK < 2 * S;
     }
     if (rg::variant_pair(v)) {  // a pair needs a partner tile
       int64_t M, N, K;
@@ -1768,7 +1811,8 @@ extern "C" int rg_gemm_noalloc(int64_t M, int64_t N, int64_t K, const void* A, i
       slots = rg::sk_geometry(tiles, kb, d->sm_count).max_pieces;
     }
     const int64_t need = slots > 1 ? slots * tiles * ts.bm * ts.bn * 4 : 0;
-    if (need > rg::kNoallocPartialBytes || (slots > 1 && tiles > RG_NOALLOC_MAX_TILES))
+    const int64_t ticket_tiles = rg::variant_2sm(variant) ? 2 * tiles : tiles;  // cta_group::2: 128-row tiles
+    if (need > rg::kNoallocPartialBytes || (slots > 1 && ticket_tiles > RG_NOALLOC_MAX_TILES))
       return rg::fail(RG_ERR_SHAPE, "rg_gemm_noalloc: split-K needs " + std::to_string(need) +
                                         " scratch bytes and " + std::to_string(tiles) + " tiles; the fixed scratch holds " +
                                         std::to_string(rg::kNoallocPartialBytes) + " bytes and " +

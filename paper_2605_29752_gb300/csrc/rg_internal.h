@@ -40,7 +40,7 @@ struct TileShape {
 TileShape tile_shape(int tile);
 // Variant ids: tile * RG_NUM_SPLITS + log2(split) for the split-K variants, then
 // RG_VARIANT_SK(tile) (stream-K), RG_VARIANT_PAIR(tile) (multicast pairs) and
-// RG_VARIANT_2SM(tile) (cta_group::2, 256-row tiles with BN >= 128).
+// RG_VARIANT_2SM(tile, log2(split)) (cta_group::2, 256-row tiles with BN >= 128).
 constexpr int kClassicVariants = RG_NUM_TILES * RG_NUM_SPLITS;
 constexpr int kPairVariants = kClassicVariants + RG_NUM_TILES;
 constexpr int k2SmVariants = kPairVariants + RG_NUM_TILES;
@@ -48,12 +48,16 @@ inline bool variant_streamk(int v) { return v >= kClassicVariants && v < kPairVa
 inline bool variant_pair(int v) { return v >= kPairVariants && v < k2SmVariants; }
 inline bool variant_2sm(int v) { return v >= k2SmVariants; }
 inline int variant_tile(int v) {
-  return v >= k2SmVariants    ? RG_TILE_256x128 + (v - k2SmVariants)
+  return v >= k2SmVariants    ? RG_TILE_256x128 + (v - k2SmVariants) / RG_NUM_SPLITS
          : v >= kPairVariants ? v - kPairVariants
          : v >= kClassicVariants ? v - kClassicVariants
                                  : v / RG_NUM_SPLITS;
 }
-inline int variant_split(int v) { return v >= kClassicVariants ? 1 : 1 << (v % RG_NUM_SPLITS); }
+inline int variant_split(int v) {
+  return v >= k2SmVariants ? 1 << ((v - k2SmVariants) % RG_NUM_SPLITS)
+         : v >= kClassicVariants ? 1
+                                 : 1 << (v % RG_NUM_SPLITS);
+}
 // Stream-K geometry shared by the launcher, the sweep's pruning and the kernel:
 // whole waves of tiles run data-parallel (one tile per CTA per wave); only the
 // remainder tiles are divided among tail_ctas CTAs by K iterations (each at

@@ -31,7 +31,7 @@ RG_ERR_NO_DEVICE = -9
 RG_T_UNMEASURED = 1 << 60
 RG_NUM_TILES = 6
 RG_NUM_SPLITS = 4
-RG_NUM_VARIANTS = RG_NUM_TILES * RG_NUM_SPLITS + 2 * RG_NUM_TILES + 2
+RG_NUM_VARIANTS = RG_NUM_TILES * RG_NUM_SPLITS + 2 * RG_NUM_TILES + 2 * RG_NUM_SPLITS
 TILES = [(128, 64), (128, 128), (128, 256), (256, 64), (256, 128), (256, 256)]
 SPLITS = [1, 2, 4, 8]
 SK = "SK"
@@ -42,11 +42,13 @@ _BASE_2SM = RG_NUM_TILES * RG_NUM_SPLITS + 2 * RG_NUM_TILES
 
 def variant(tile: int, split=1) -> int:
     """Variant id of a tile with split factor 1/2/4/8, split="SK" for stream-K, "PR" for the
-    2-CTA multicast pair or "2SM" for the cta_group::2 pair (tiles 256x128 and 256x256 only)."""
-    if split == TWO_SM:
+    2-CTA multicast pair, or "2SM" / ("2SM", S) for the cta_group::2 pair with split factor S
+    (tiles 256x128 and 256x256 only)."""
+    if split == TWO_SM or (isinstance(split, tuple) and split[0] == TWO_SM):
         if tile not in (4, 5):
             raise ValueError("the 2-SM variant exists for the 256x128 and 256x256 tiles only")
-        return _BASE_2SM + tile - 4
+        s = 1 if split == TWO_SM else split[1]
+        return _BASE_2SM + (tile - 4) * RG_NUM_SPLITS + SPLITS.index(s)
     if split == SK:
         return RG_NUM_TILES * RG_NUM_SPLITS + tile
     if split == PAIR:
@@ -58,14 +60,15 @@ def variant_tile(v: int) -> int:
     """Tile index (0..5) of a variant id."""
     n = RG_NUM_TILES * RG_NUM_SPLITS
     if v >= _BASE_2SM:
-        return 4 + v - _BASE_2SM
+        return 4 + (v - _BASE_2SM) // RG_NUM_SPLITS
     return v - n - RG_NUM_TILES if v >= n + RG_NUM_TILES else v - n if v >= n else v // RG_NUM_SPLITS
 
 
 def variant_name(v: int) -> str:
     if v >= _BASE_2SM:
-        bm, bn = TILES[4 + v - _BASE_2SM]
-        return f"{bm}x{bn}/2SM"
+        bm, bn = TILES[4 + (v - _BASE_2SM) // RG_NUM_SPLITS]
+        s = SPLITS[(v - _BASE_2SM) % RG_NUM_SPLITS]
+        return f"{bm}x{bn}/2SM" + ("" if s == 1 else f"-S{s}")
     if v >= RG_NUM_TILES * RG_NUM_SPLITS + RG_NUM_TILES:
         bm, bn = TILES[v - RG_NUM_TILES * RG_NUM_SPLITS - RG_NUM_TILES]
         return f"{bm}x{bn}/PR"

@@ -11,7 +11,7 @@ from oracle import gemm as og
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-ALL_VARIANTS = list(range(38))          # 24 split-K variants, 6 stream-K, 6 multicast pairs, 2 cta_group::2
+ALL_VARIANTS = list(range(44))          # 24 split-K, 6 stream-K, 6 multicast pairs, 8 cta_group::2 (2 tiles x 4 splits)
 
 
 @pytest.fixture(scope="module")
@@ -269,3 +269,52 @@ def test_two_sm_exact_cases_beta_and_padding(rg, ctx, tile):
     c_plain = run(rg, ctx, a, b, v)
     check(c_plain, a, b)
     assert np.array_equal(c_plain, run(rg, ctx, a, b, v, pads=(M + 256, N + 128, K + 384)))
+
+
+@pytest.mark.parametrize("tile", [4, 5])
+@pytest.mark.parametrize("split", [2, 4, 8])
+def test_two_sm_split_k(rg, ctx, tile, split):
+    """cta_group::2 with split-K: each CTA reduces its own 128 rows in the fixed split
+    order, so the result is bitwise that of the 1-CTA kernel with the same split; beta = 1
+    accumulates."""
+    v = rg.variant(tile, (rg.TWO_SM, split))
+    for (M, N, K), seed in (((512, 384, 2048), 7), ((200, 264, 1000), 8), ((1024, 1024, 4096), 9)):
+        a, b = synthetic.operands_bf16(M, N, K, seed=seed)
+        c = run(rg, ctx, a, b, v)
+        if M * N * K <= 1024 * 1024 * 1024:
+            check(c, a, b)
+        assert np.array_equal(c, run(rg, ctx, a, b, rg.variant(tile, split)))
+        assert np.array_equal(c, run(rg, ctx, a, b, v))
+    M, N, K = 640, 384, 1536
+    a, b = synthetic.operands_bf16(M, N, K, seed=13)
+    c0 = synthetic.normal_stream_f32(13, 5, M * N).reshape(M, N)
+    check(run(rg, ctx, a, b, v, beta=1, c0=c0), a, b, c0=c0)
+
+
+@pytest.mark.parametrize("tile", range(6))
+def test_column_panel_tile_order(rg, ctx, tile):
+    """N = 8192 with K = 4096 puts more tile columns than one 32 MiB panel of B holds, so
+    tiles run in column panels: every variant family still covers every tile once
+    (sampled rows and columns against the oracle; pair and cta_group::2 forms bitwise
+    equal to the 1-CTA kernel)."""
+    M, N, K = 520, 8192, 4096
+    a, b = synthetic.operands_bf16(M, N, K, seed=21)
+    c = run(rg, ctx, a, b, rg.variant(tile, 1))
+    rs = np.random.default_rng(2)
+    rows, cols = rs.choice(M, 6, replace=False), rs.choice(N, 6, replace=False)
+    A64, B64 = og.bf16_bits_to_f64(a), og.bf16_bits_to_f64(b)
+    cr, sr, cc, sc = og.sampled_rows_cols(A64, B64, rows, cols)
+    for got, ref, s in ((c[rows, :], cr, sr), (c[:, cols], cc, sc)):
+        ratio, exact_zero = og.error_ratio(got, ref, s)
+        assert exact_zero and ratio <= og.bound(K), ratio
+    others = [rg.variant(tile, rg.PAIR), rg.variant(tile, rg.SK)]
+    if tile >= 4:
+        others.append(rg.variant(tile, rg.TWO_SM))
+    for v in others:
+        got = run(rg, ctx, a, b, v)
+        if v == rg.variant(tile, rg.SK):
+            check_rows = got[rows, :]
+            ratio, exact_zero = og.error_ratio(check_rows, cr, sr)
+            assert exact_zero and ratio <= og.bound(K), (rg.variant_name(v), ratio)
+        else:
+            assert np.array_equal(got, c), rg.variant_name(v)
