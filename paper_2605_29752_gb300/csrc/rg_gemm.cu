@@ -389,15 +389,17 @@ struct PairSched {
 // concatenation of every item's tiles (item i owns units [tile_start, tile_start
 // + tiles_m * tiles_n)).  Each item carries its own tensor maps (in global
 // memory), launch extents and beta; no split-K.
-struct alignas(64) GroupItem {
+// Work-list records keep CUtensorMap's 128-byte alignment: a 128-byte header,
+// then 512-byte items (three maps and the sizes).
+struct alignas(128) GroupItem {
   CUtensorMap a, b, c;
   int32_t M, N, beta, tiles_m;
   int32_t tiles_n, kblocks, tile_start, reserved;
 };
-struct alignas(64) GroupHeader {
+struct alignas(128) GroupHeader {
   int32_t n_items;
   int32_t total_tiles;
-  int32_t reserved[14];
+  int32_t reserved[30];
 };
 
 struct GroupSched {
@@ -1585,6 +1587,7 @@ struct rg_group {
 };
 
 namespace rg {
+static_assert(sizeof(GroupHeader) == 128 && sizeof(GroupItem) == 512, "work-list record sizes");
 static size_t group_bytes(int n) { return sizeof(GroupHeader) + static_cast<size_t>(n) * sizeof(GroupItem); }
 
 static void group_free(rg_group* g) {
