@@ -149,6 +149,18 @@ int rg_check(rg_ctx* ctx, void* stream);
 /* Set the bounded-wait budget in GPU clock cycles for later launches
  * (default 2e9, about a second).  A test may set it tiny to force the timeout path. */
 int rg_set_timeout_cycles(rg_ctx* ctx, int64_t cycles);
+/* Declare (enable = 1) that A and B of the GEMMs this context launches from now
+ * on are not written by any work enqueued before them on their stream (static
+ * operands, such as weights).  The kernels then start loading A and B and
+ * running their MMAs before the preceding grid in the stream has completed
+ * (programmatic dependent launch); only the epilogue, which writes C and the
+ * split-K workspace, waits for it, so independent GEMMs on static operands
+ * overlap on idle SMs.  Default 0: every global access waits.  rg_sweep and
+ * rg_sweep_memtwin always time with it off (a timed launch must not overlap the
+ * previous one's work) and restore the setting afterwards.  Enabling it while a
+ * preceding kernel writes A or B is a data race.  Errors: RG_ERR_INVALID for a
+ * null context. */
+int rg_set_static_operands(rg_ctx* ctx, int32_t enable);
 /* Failure-path testing: while enabled, every GEMM launch of this context first
  * makes its MMA warp wait on a barrier that nothing arrives on, so that bounded
  * wait expires after the timeout budget; the kernel then records the error,

@@ -62,6 +62,8 @@ struct GemmArgs {
   int32_t stall;            // test hook: the MMA warp first waits on a barrier nothing arrives on
   int32_t dp_tiles;         // stream-K: tiles run whole before the shared tail
   int32_t panel;            // tile order: column panels of this many tiles (pairs: tile columns)
+  int32_t early;            // 1: A and B are static, so loads may start before the preceding grid completes
+  int32_t reserved_;
   float* ws;                // split-K partials [split][tile][BM][BN]
   int32_t* tickets;         // [tile][4], zero between launches
   int32_t* err;
@@ -436,7 +438,7 @@ struct GroupSched {
 
 template <int BM, int BN, int STAGES, class Sched>
 __device__ __forceinline__ void gemm_body(Sched& sched, float* ws, int32_t* tickets, int32_t* err, long long timeout,
-                                          int stall) {
+                                          int stall, int early) {
   constexpr bool P2 = Sched::k2Sm;  // one CTA of a cta_group::2 pair
   using C = KCfg<BM, BN, STAGES, P2 ? 2 : 1>;
   extern __shared__ uint8_t smem_raw[];
@@ -489,8 +491,11 @@ __device__ __forceinline__ void gemm_body(Sched& sched, float* ws, int32_t* tick
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
   // Everything above overlaps the previous grid in the stream; nothing below
-  // touches global memory before that grid has completed.
-  grid_dependency_wait();
+  // touches global memory before that grid has completed -- except, when A and
+  // B are declared static (early), the operand loads and the MMAs, which touch
+  // only A, B, shared memory and TMEM: then only the epilogue, which writes C
+  // and the split-K workspace, waits for the previous grid.
+  if (!early) grid_dependency_wait();
   grid_launch_dependents();
   sched.init();
   const int nunits = sched.count();
@@ -643,6 +648,7 @@ __device__ __forceinline__ void gemm_body(Sched& sched, float* ws, int32_t* tick
     }
   } else {
     // ------------------------------------------------ epilogue (warps 2-5)
+    if (early) grid_dependency_wait();
     const int q = warp & 3;  // TMEM lanes 32q..32q+31 are the ones this warp may read
     const uint32_t stg0 = sbase + C::STAGING_OFF + (warp - 2) * kStagingPerWarp;
     int acc = 0, sbuf = 0;
@@ -822,7 +828,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   SingleSched sched{&tmA,        &tmB,          &tmC,   &tmW,  args.tiles_m, args.tiles_n,
                     args.splits, args.kblocks, args.M, args.N, args.beta};
   sched.panel = args.panel;
-  gemm_body<BM, BN, STAGES>(sched, args.ws, args.tickets, args.err, args.timeout, args.stall);
+  gemm_body<BM, BN, STAGES>(sched, args.ws, args.tickets, args.err, args.timeout, args.stall, args.early);
 }
 
 template <int BM, int BN, int STAGES>
@@ -833,7 +839,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   MemTwinSched sched{{&tmA,        &tmB,          &tmC,   &tmW,  args.tiles_m, args.tiles_n,
                       args.splits, args.kblocks, args.M, args.N, args.beta}};
   sched.panel = args.panel;
-  gemm_body<BM, BN, STAGES>(sched, args.ws, args.tickets, args.err, args.timeout, args.stall);
+  gemm_body<BM, BN, STAGES>(sched, args.ws, args.tickets, args.err, args.timeout, args.stall, args.early);
 }
 
 template <int BM, int BN, int STAGES>
@@ -844,7 +850,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   StreamKSched sched{&tmA,        &tmB,   &tmC,   &tmW,      args.tiles_m, args.tiles_n, args.kblocks,
                      args.M,      args.N, args.beta, args.splits /* CTAs sharing the tail */, args.dp_tiles};
   sched.panel = args.panel;
-  gemm_body<BM, BN, STAGES>(sched, args.ws, args.tickets, args.err, args.timeout, args.stall);
+  gemm_body<BM, BN, STAGES>(sched, args.ws, args.tickets, args.err, args.timeout, args.stall, args.early);
 }
 
 template <int BM, int BN, int STAGES, int MODE>
@@ -854,7 +860,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                           const GemmArgs args) {
   PairSched<MODE> sched{&tmA, &tmB, &tmC, &tmW, args.tiles_m, args.tiles_n, args.kblocks, args.M, args.N, args.beta};
   sched.panel = args.panel;
-  gemm_body<BM, BN, STAGES>(sched, args.ws, args.tickets, args.err, args.timeout, args.stall);
+  gemm_body<BM, BN, STAGES>(sched, args.ws, args.tickets, args.err, args.timeout, args.stall, args.early);
 }
 
 // cta_group::2: 2-CTA clusters, each pair one 256 x BN output tile (128 rows per CTA).
@@ -867,7 +873,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                            args.beta};
   sched.splits = args.splits;
   sched.panel = args.panel;
-  gemm_body<128, BN, STAGES>(sched, args.ws, args.tickets, args.err, args.timeout, args.stall);
+  gemm_body<128, BN, STAGES>(sched, args.ws, args.tickets, args.err, args.timeout, args.stall, args.early);
 }
 
 template <int BM, int BN, int STAGES>
@@ -875,7 +881,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     gemm_bf16_grouped_kernel(const GroupHeader* __restrict__ hdr, const GroupItem* __restrict__ items, int32_t* err,
                              long long timeout) {
   GroupSched sched{hdr, items, 0, 0};
-  gemm_body<BM, BN, STAGES>(sched, nullptr, nullptr, err, timeout, 0);
+  gemm_body<BM, BN, STAGES>(sched, nullptr, nullptr, err, timeout, 0, 0);
 }
 
 // Device-side spin of about `ns` nanoseconds (global timer), so that launches
@@ -953,6 +959,7 @@ struct rg_ctx {
   int32_t* err = nullptr;
   long long timeout = 2000000000LL;
   int32_t stall = 0;
+  int32_t static_operands = 0;  // rg_set_static_operands
   int64_t launches = 0;
   std::vector<cudaEvent_t> events;
 };
@@ -1105,6 +1112,7 @@ static int prepare(rg_ctx* ctx, int64_t M, int64_t N, int64_t K, const void* A, 
   g.err = ctx->err;
   g.timeout = ctx->timeout;
   g.stall = ctx->stall;
+  g.early = ctx->static_operands;
   const int64_t units = tiles_m * tiles_n * splits;
   if (two) {  // one 2-CTA cluster per (256-row tile, split), at most one CTA per SM
     L->grid = dim3(static_cast<unsigned>(2 * std::min<int64_t>(tiles_m * tiles_n * splits, ctx->sm_count / 2)));
@@ -1364,6 +1372,12 @@ extern "C" int rg_launch_count(const rg_ctx* ctx, int64_t* out) {
   return RG_OK;
 }
 
+extern "C" int rg_set_static_operands(rg_ctx* ctx, int32_t enable) {
+  if (!ctx) return rg::fail(RG_ERR_INVALID, "rg_set_static_operands: null context");
+  ctx->static_operands = enable ? 1 : 0;
+  return RG_OK;
+}
+
 extern "C" int rg_set_timeout_cycles(rg_ctx* ctx, int64_t cycles) {
   if (!ctx || cycles <= 0) return rg::fail(RG_ERR_INVALID, "rg_set_timeout_cycles: bad argument");
   ctx->timeout = cycles;
@@ -1527,7 +1541,14 @@ static int sweep_impl(rg_ctx* ctx, const rg_grid* grid, int32_t n_variants, cons
     }
     return cudaSuccess;
   };
+  // The sweep times one GEMM at a time: the static-operand mode stays off even
+  // though the operands are constant, because it would let a launch's loads and
+  // MMAs run on idle SMs while the launch ahead of it is still running, so the
+  // per-launch time would measure several overlapped GEMMs.
+  const int32_t saved_static = ctx->static_operands;
+  ctx->static_operands = 0;
   const int rc = rg::timed_sweep(ctx, order, o, st, t_ns_out, prep, run);
+  ctx->static_operands = saved_static;
   if (rc != RG_OK) return rc;
   return rg_check(ctx, stream);
 }

@@ -153,6 +153,7 @@ _sigs = {
     "rg_sm_count": (C.c_int, [_P, C.POINTER(_I32)]),
     "rg_check": (C.c_int, [_P, _P]),
     "rg_set_timeout_cycles": (C.c_int, [_P, _I64]),
+    "rg_set_static_operands": (C.c_int, [_P, _I32]),
     "rg_gemm": (C.c_int, [_P, _I64, _I64, _I64, _P, _I64, _P, _I64, _P, _I64, _I32, _I32, _I64, _I64, _I64, _P]),
     "rg_plan_build": (C.c_int, [C.POINTER(rg_grid), _P, _I32, _P, C.POINTER(_P)]),
     "rg_plan_build_ex": (C.c_int, [C.POINTER(rg_grid), _P, _I32, _P, _I32, C.POINTER(_P)]),
@@ -276,6 +277,11 @@ def rg_check_status(ctx: int, stream=None) -> int:
 
 def rg_set_timeout_cycles(ctx: int, cycles: int) -> None:
     _check(_lib.rg_set_timeout_cycles(ctx, cycles), "rg_set_timeout_cycles")
+
+
+def rg_set_static_operands(ctx, enable: bool) -> None:
+    """Declare that A and B are not written by earlier work on the stream (see include/rg.h)."""
+    _check(_lib.rg_set_static_operands(ctx, 1 if enable else 0), "rg_set_static_operands")
 
 
 def rg_gemm(ctx, M, N, K, A, lda, B, ldb, Cp, ldc, variant_id, beta=0, pm=0, pn=0, pk=0, stream=None) -> None:

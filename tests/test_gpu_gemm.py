@@ -318,3 +318,38 @@ def test_column_panel_tile_order(rg, ctx, tile):
             assert exact_zero and ratio <= og.bound(K), (rg.variant_name(v), ratio)
         else:
             assert np.array_equal(got, c), rg.variant_name(v)
+
+
+def test_static_operands_mode(rg, ctx):
+    """With A and B declared static, loads and MMAs start before the preceding grid
+    completes and only the epilogue waits for it: back-to-back launches into the same
+    C, a K-split plan-style chain (beta = 1 after beta = 0) and split-K launches give
+    bitwise the results of the default mode."""
+    M, N, K = 640, 520, 1536
+    a, b = synthetic.operands_bf16(M, N, K, seed=22)
+    A, B = dev_bf16(a), dev_bf16(b)
+    vs = [rg.variant(1, 1), rg.variant(2, 4), rg.variant(5, rg.TWO_SM), rg.variant(0, rg.SK), rg.variant(2, rg.PAIR)]
+    results = {}
+    for static in (False, True):
+        rg.rg_set_static_operands(ctx, static)
+        try:
+            for v in vs:
+                C = torch.full((M, N), float("nan"), device="cuda")
+                for _ in range(4):                                  # the same C rewritten back to back
+                    rg.rg_gemm(ctx, M, N, K, A, K, B, N, C, N, v)
+                rg.rg_check(ctx)
+                results[(static, v)] = C.cpu().numpy()
+            # K split into two chained launches: C = A[:, :k1] B[:k1] then C += A[:, k1:] B[k1:]
+            k1 = 512
+            C = torch.full((M, N), float("nan"), device="cuda")
+            rg.rg_gemm(ctx, M, N, k1, A, K, B, N, C, N, rg.variant(1, 1), 0)
+            rg.rg_gemm(ctx, M, N, K - k1, A[:, k1:], K, B[k1:], N, C, N, rg.variant(1, 1), 1)
+            rg.rg_check(ctx)
+            results[(static, "chain")] = C.cpu().numpy()
+        finally:
+            rg.rg_set_static_operands(ctx, False)
+    for v in vs:
+        check(results[(True, v)], a, b)
+        assert np.array_equal(results[(True, v)], results[(False, v)]), rg.variant_name(v)
+    check(results[(True, "chain")], a, b)
+    assert np.array_equal(results[(True, "chain")], results[(False, "chain")])
