@@ -220,11 +220,44 @@ def cpu_baseline(count, budget_s=15.0, seed=0):
         if time.perf_counter() - t_start > budget_s:
             break
     cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
-    return {"value": float(np.mean(vals)), "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
-            "sample": f"{len(used)} cells drawn uniformly from the {count}^3 grid (seed {seed}); oracle FP64 "
-                      f"GEMM (numpy matmul, float64) per cell; value = mean per-cell TFLOP/s; "
-                      f"aggregate {flops / secs / 1e12:.4f} TFLOP/s over {secs:.1f} s",
-            "aggregate_tflops": flops / secs / 1e12}
+    out = {"value": float(np.mean(vals)), "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
+           "sample": f"{len(used)} cells drawn uniformly from the {count}^3 grid (seed {seed}); oracle FP64 "
+                     f"GEMM (numpy matmul, float64) per cell; value = mean per-cell TFLOP/s; "
+                     f"aggregate {flops / secs / 1e12:.4f} TFLOP/s over {secs:.1f} s",
+           "aggregate_tflops": flops / secs / 1e12}
+    out.update(host_steps_timing(count, seed))
+    return out
+
+
+def host_steps_timing(count, seed=0, variants=6):
+    """The host steps of the path on a seeded synthetic T0 table of the whole grid: the oracle's
+    pure-Python DP (best-of, T1, T2) and roughness, beside the library's native plan build and
+    statistics on the same table (one thread each)."""
+    from oracle import dp, roughness
+    from paper_2605_29752_gb300 import rg
+    rs = np.random.default_rng(seed)
+    shape = (count, count, count)
+    T0v = rs.integers(1000, 10 ** 7, size=(variants,) + shape).astype(np.int64)
+    grid = ((STEP, STEP, count),) * 3
+    t0 = time.perf_counter()
+    T0s, _ = dp.best_of(T0v)
+    T1, _ = dp.pad_T1(T0s, grid)
+    dp.split_T2(T1, grid)
+    t_oracle_dp = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    roughness.roughness_all(roughness.surface(T0s, grid))
+    t_oracle_r = time.perf_counter() - t0
+    g = rg.make_grid((STEP, STEP, count))
+    t0 = time.perf_counter()
+    h = rg.rg_plan_build(g, T0v.reshape(variants, -1), list(range(variants)))
+    t_lib_dp = time.perf_counter() - t0
+    rg.rg_plan_free(h)
+    t0 = time.perf_counter()
+    rg.rg_surface_stats(g, T0s.reshape(-1))
+    t_lib_r = time.perf_counter() - t0
+    return {"host_steps": {"table": f"{variants} variants x {count}^3 cells, seeded uniform integers",
+                           "oracle_dp_s": t_oracle_dp, "oracle_roughness_s": t_oracle_r,
+                           "library_plan_build_s": t_lib_dp, "library_surface_stats_s": t_lib_r}}
 
 
 def reference_arm(args):
