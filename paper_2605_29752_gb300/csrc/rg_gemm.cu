@@ -179,8 +179,9 @@ __device__ __forceinline__ Unit split_unit(const CUtensorMap* a, const CUtensorM
   x.s = u % splits;
   x.splits = splits;
   tile_coords(x.tile, tiles_m, tiles_n, panel, x.tm, x.tn);
-  x.kb0 = static_cast<int>(static_cast<long long>(x.s) * kblocks / splits);
-  x.kb1 = static_cast<int>(static_cast<long long>(x.s + 1) * kblocks / splits);
+  // 32-bit: splits <= 8 and kblocks <= 2^24, so (s + 1) * kblocks < 2^27
+  x.kb0 = splits == 1 ? 0 : x.s * kblocks / splits;
+  x.kb1 = splits == 1 ? kblocks : (x.s + 1) * kblocks / splits;
   x.M = M;
   x.N = N;
   x.beta = beta;
@@ -375,8 +376,8 @@ struct PairSched {
     }
     x.s = u % splits;
     x.splits = splits;
-    x.kb0 = static_cast<int>(static_cast<long long>(x.s) * kblocks / splits);
-    x.kb1 = static_cast<int>(static_cast<long long>(x.s + 1) * kblocks / splits);
+    x.kb0 = splits == 1 ? 0 : x.s * kblocks / splits;
+    x.kb1 = splits == 1 ? kblocks : (x.s + 1) * kblocks / splits;
     x.M = M;
     x.N = N;
     x.beta = beta;
@@ -495,9 +496,17 @@ __device__ __forceinline__ void gemm_body(Sched& sched, float* ws, int32_t* tick
   // B are declared static (early), the operand loads and the MMAs, which touch
   // only A, B, shared memory and TMEM: then only the epilogue, which writes C
   // and the split-K workspace, waits for the previous grid.
+  // The schedule of a single problem depends only on kernel parameters, so it,
+  // and the producer's first unit, are worked out while the previous grid may
+  // still be running (a grouped work list is read after the wait).
+  Unit first{};
+  if constexpr (!Sched::kMapsInGlobal) {
+    sched.init();
+    if (warp == 0 && lane == 0 && sched.count() > 0) first = sched.unit(0);
+  }
   if (!early) grid_dependency_wait();
   grid_launch_dependents();
-  sched.init();
+  if constexpr (Sched::kMapsInGlobal) sched.init();
   const int nunits = sched.count();
 
   if (warp == 0) {
@@ -508,7 +517,7 @@ __device__ __forceinline__ void gemm_body(Sched& sched, float* ws, int32_t* tick
       uint32_t issued_mask = 0, issued_ph = 0;
       bool ok = true;
       for (int i = 0; ok && i < nunits; ++i) {
-        const Unit w = sched.unit(i);
+        const Unit w = (!Sched::kMapsInGlobal && i == 0) ? first : sched.unit(i);
         if constexpr (Sched::kMapsInGlobal) {
           tensormap_fence_acquire(w.a);
           tensormap_fence_acquire(w.b);
