@@ -512,7 +512,7 @@ __device__ __forceinline__ void gemm_body(Sched& sched, float* ws, int32_t* tick
   if (warp == 0) {
     // ------------------------------------------------ TMA producer (one thread)
     if (lane == 0) {
-      int stage = 0;
+      int stage = 0, fills = 0;
       uint32_t ph = 0;
       uint32_t issued_mask = 0, issued_ph = 0;
       bool ok = true;
@@ -523,10 +523,12 @@ __device__ __forceinline__ void gemm_body(Sched& sched, float* ws, int32_t* tick
           tensormap_fence_acquire(w.b);
         }
         for (int kb = w.kb0; kb < w.kb1; ++kb) {
-          if (!mbar_wait(empty_bar(stage), ph ^ 1u, timeout, abort_flag)) {
+          // a stage's first fill needs no wait: nothing has used it yet
+          if (fills >= STAGES && !mbar_wait(empty_bar(stage), ph ^ 1u, timeout, abort_flag)) {
             ok = false;
             break;
           }
+          ++fills;
           const uint32_t sa = sbase + stage * C::STAGE_BYTES;
           const uint32_t sb = sa + C::A_BYTES;
           if constexpr (P2) {
