@@ -583,80 +583,80 @@ __device__ __forceinline__ void gemm_body(Sched& sched, float* ws, int32_t* tick
     }
   } else if (warp == 1) {
     // ------------------------------------------------ MMA issuer (one thread)
-    int stage = 0, acc = 0;
-    uint32_t ph = 0, aph = 0;
-    bool ok = true;
-    if (stall) ok = __all_sync(FULL, mbar_wait(drain_bar, 0, timeout, abort_flag));
-    // a pair's odd CTA issues nothing: the even CTA's MMAs read and write both
-    const int issue_units = (!P2 || sched.rank == 0) ? nunits : 0;
-    for (int i = 0; ok && i < issue_units; ++i) {
-      const Unit w = sched.unit(i);
-      const int kb0 = w.kb0, kb1 = w.kb1;
-      ok = __all_sync(FULL, mbar_wait(tempty_bar(acc), aph ^ 1u, timeout, abort_flag));
-      if (!ok) break;
-      tc_fence_after();
-      const uint32_t d0 = tmem_base + static_cast<uint32_t>(acc * C::ACC_COLS);
-      for (int kb = kb0; kb < kb1; ++kb) {
-        ok = __all_sync(FULL, mbar_wait(full_bar(stage), ph, timeout, abort_flag));
+    // Lane 0 alone runs the loop: tcgen05.mma and tcgen05.commit are issued by a
+    // single thread, and keeping the other 31 lanes out of the loop saves a warp
+    // vote and a warp reconvergence per stage (about 200 of the 550 cycles a stage
+    // cost when the whole warp stepped through it).
+    if (lane == 0) {
+      int stage = 0, acc = 0;
+      uint32_t ph = 0, aph = 0;
+      bool ok = true;
+      if (stall) ok = mbar_wait(drain_bar, 0, timeout, abort_flag);
+      // a pair's odd CTA issues nothing: the even CTA's MMAs read and write both
+      const int issue_units = (!P2 || sched.rank == 0) ? nunits : 0;
+      for (int i = 0; ok && i < issue_units; ++i) {
+        const Unit w = sched.unit(i);
+        const int kb0 = w.kb0, kb1 = w.kb1;
+        ok = mbar_wait(tempty_bar(acc), aph ^ 1u, timeout, abort_flag);
         if (!ok) break;
         tc_fence_after();
-        if (lane == 0 && Sched::kMemOnly) {
-          mbar_arrive(empty_bar(stage));  // no MMA reads the stage: it is free once its bytes have landed
-        } else if (lane == 0) {
-          const uint32_t sa = sbase + stage * C::STAGE_BYTES;
-          const uint32_t sb = sa + C::A_BYTES;
+        const uint32_t d0 = tmem_base + static_cast<uint32_t>(acc * C::ACC_COLS);
+        for (int kb = kb0; kb < kb1; ++kb) {
+          ok = mbar_wait(full_bar(stage), ph, timeout, abort_flag);
+          if (!ok) break;
+          tc_fence_after();
+          if constexpr (Sched::kMemOnly) {
+            mbar_arrive(empty_bar(stage));  // no MMA reads the stage: it is free once its bytes have landed
+          } else {
+            const uint32_t sa = sbase + stage * C::STAGE_BYTES;
+            const uint32_t sb = sa + C::A_BYTES;
 #pragma unroll
-          for (int k = 0; k < kBK / 16; ++k) {
-            const uint64_t bdesc = smem_desc_sw128(sb + k * 2048, kBK * 128, 1024);
+            for (int k = 0; k < kBK / 16; ++k) {
+              const uint64_t bdesc = smem_desc_sw128(sb + k * 2048, kBK * 128, 1024);
 #pragma unroll
-            for (int h = 0; h < C::HALVES; ++h) {
-              const uint64_t adesc = smem_desc_sw128(sa + h * (128 * 128) + k * 32, 16, 1024);
-              if constexpr (P2)
-                mma_f16_pair(d0, adesc, bdesc, C::IDESC, (kb > kb0 || k > 0) ? 1u : 0u);
-              else
-                mma_f16(d0 + h * BN, adesc, bdesc, C::IDESC, (kb > kb0 || k > 0) ? 1u : 0u);
+              for (int h = 0; h < C::HALVES; ++h) {
+                const uint64_t adesc = smem_desc_sw128(sa + h * (128 * 128) + k * 32, 16, 1024);
+                if constexpr (P2)
+                  mma_f16_pair(d0, adesc, bdesc, C::IDESC, (kb > kb0 || k > 0) ? 1u : 0u);
+                else
+                  mma_f16(d0 + h * BN, adesc, bdesc, C::IDESC, (kb > kb0 || k > 0) ? 1u : 0u);
+              }
             }
+            if constexpr (P2)
+              mma_commit_pair_multicast(empty_bar(stage), 3);  // the stage is free in both CTAs
+            else if constexpr (Sched::kMulticast != 0)
+              mma_commit_multicast(empty_bar(stage), 3);  // releases the stage in both CTAs of the pair
+            else
+              mma_commit(empty_bar(stage));
           }
-          if constexpr (P2)
-            mma_commit_pair_multicast(empty_bar(stage), 3);  // the stage is free in both CTAs
-          else if constexpr (Sched::kMulticast != 0)
-            mma_commit_multicast(empty_bar(stage), 3);  // releases the stage in both CTAs of the pair
-          else
-            mma_commit(empty_bar(stage));
+          if (++stage == STAGES) {
+            stage = 0;
+            ph ^= 1u;
+          }
         }
-        __syncwarp();
-        if (++stage == STAGES) {
-          stage = 0;
-          ph ^= 1u;
-        }
-      }
-      if (!ok) break;
-      if (lane == 0) {
+        if (!ok) break;
         if constexpr (Sched::kMemOnly)
           mbar_arrive(tfull_bar(acc));
         else if constexpr (P2)
           mma_commit_pair_multicast(tfull_bar(acc), 3);  // both CTAs' halves of the accumulator are final
         else
           mma_commit(tfull_bar(acc));
+        if (++acc == C::NBUF) {
+          acc = 0;
+          aph ^= 1u;
+        }
       }
-      __syncwarp();
-      if (++acc == C::NBUF) {
-        acc = 0;
-        aph ^= 1u;
-      }
-    }
-    if (!ok) {
-      if (lane == 0) {
+      if (!ok) {
         atomicExch(err, kErrMma);
         *abort_flag = 1;
         if constexpr (P2)
           mma_commit_pair(drain_bar);
         else
           mma_commit(drain_bar);  // completes once every issued MMA has finished
+        mbar_wait(drain_bar, 0, kDrainCycles, no_abort);
       }
-      __syncwarp();
-      mbar_wait(drain_bar, 0, kDrainCycles, no_abort);
     }
+    __syncwarp();
   } else {
     // ------------------------------------------------ epilogue (warps 2-5)
     if (early) grid_dependency_wait();
