@@ -610,16 +610,22 @@ __device__ __forceinline__ void gemm_body(Sched& sched, float* ws, int32_t* tick
           } else {
             const uint32_t sa = sbase + stage * C::STAGE_BYTES;
             const uint32_t sb = sa + C::A_BYTES;
+            // The descriptors of the stage's K steps differ only in their start
+            // address field (bits 0-13, address >> 4; no carry: shared addresses
+            // stay below 2^18), so they are the stage's base descriptors plus constants.
+            const uint64_t adesc0 = smem_desc_sw128(sa, 16, 1024);
+            const uint64_t bdesc0 = smem_desc_sw128(sb, kBK * 128, 1024);
+            const uint32_t first = kb > kb0 ? 1u : 0u;
 #pragma unroll
             for (int k = 0; k < kBK / 16; ++k) {
-              const uint64_t bdesc = smem_desc_sw128(sb + k * 2048, kBK * 128, 1024);
+              const uint64_t bdesc = bdesc0 + static_cast<uint64_t>((k * 2048) >> 4);
 #pragma unroll
               for (int h = 0; h < C::HALVES; ++h) {
-                const uint64_t adesc = smem_desc_sw128(sa + h * (128 * 128) + k * 32, 16, 1024);
+                const uint64_t adesc = adesc0 + static_cast<uint64_t>((h * (128 * 128) + k * 32) >> 4);
                 if constexpr (P2)
-                  mma_f16_pair(d0, adesc, bdesc, C::IDESC, (kb > kb0 || k > 0) ? 1u : 0u);
+                  mma_f16_pair(d0, adesc, bdesc, C::IDESC, k > 0 ? 1u : first);
                 else
-                  mma_f16(d0 + h * BN, adesc, bdesc, C::IDESC, (kb > kb0 || k > 0) ? 1u : 0u);
+                  mma_f16(d0 + h * BN, adesc, bdesc, C::IDESC, k > 0 ? 1u : first);
               }
             }
             if constexpr (P2)
