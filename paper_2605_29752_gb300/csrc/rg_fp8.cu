@@ -151,49 +151,48 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (issued_mask & (1u << i)) mbar_wait(full_bar(i), (issued_ph >> i) & 1u, kDrainCycles, no_abort);
     }
   } else if (warp == 1) {
-    int stage = 0, acc = 0;
-    uint32_t ph = 0, aph = 0;
-    bool ok = true;
-    for (int u = blockIdx.x; ok && u < total; u += gridDim.x) {
-      for (int kb = 0; kb < args.kblocks; ++kb) {
-        ok = __all_sync(FULL, mbar_wait(tempty_bar(acc), aph ^ 1u, args.timeout, abort_flag));
-        if (!ok) break;
-        ok = __all_sync(FULL, mbar_wait(full_bar(stage), ph, args.timeout, abort_flag));
-        if (!ok) break;
-        tc_fence_after();
-        if (lane == 0) {
+    // Lane 0 alone issues the MMAs and commits (no per-K-block warp vote).
+    if (lane == 0) {
+      int stage = 0, acc = 0;
+      uint32_t ph = 0, aph = 0;
+      bool ok = true;
+      for (int u = blockIdx.x; ok && u < total; u += gridDim.x) {
+        for (int kb = 0; kb < args.kblocks; ++kb) {
+          ok = mbar_wait(tempty_bar(acc), aph ^ 1u, args.timeout, abort_flag);
+          if (!ok) break;
+          ok = mbar_wait(full_bar(stage), ph, args.timeout, abort_flag);
+          if (!ok) break;
+          tc_fence_after();
           const uint32_t sa = sbase + stage * STAGE_BYTES;
           const uint32_t sb = sa + A_BYTES;
           const uint32_t d = tmem_base + static_cast<uint32_t>(acc * BN);
+          // K steps differ only in the descriptors' start address field (address >> 4)
+          const uint64_t adesc0 = smem_desc_sw128(sa, 16, 1024);
+          const uint64_t bdesc0 = smem_desc_sw128(sb, BK * 128, 1024);  // halves BK*128 apart
 #pragma unroll
-          for (int k = 0; k < BK / 32; ++k) {
-            const uint64_t adesc = smem_desc_sw128(sa + k * 32, 16, 1024);
-            const uint64_t bdesc = smem_desc_sw128(sb + k * (32 * 128), BK * 128, 1024);  // halves BK*128 apart
-            mma_f8(d, adesc, bdesc, IDESC, k > 0 ? 1u : 0u);
-          }
+          for (int k = 0; k < BK / 32; ++k)
+            mma_f8(d, adesc0 + static_cast<uint64_t>((k * 32) >> 4), bdesc0 + static_cast<uint64_t>((k * (32 * 128)) >> 4),
+                   IDESC, k > 0 ? 1u : 0u);
           mma_commit(empty_bar(stage));
           mma_commit(tfull_bar(acc));
-        }
-        __syncwarp();
-        if (++stage == STAGES) {
-          stage = 0;
-          ph ^= 1u;
-        }
-        if (++acc == NACC) {
-          acc = 0;
-          aph ^= 1u;
+          if (++stage == STAGES) {
+            stage = 0;
+            ph ^= 1u;
+          }
+          if (++acc == NACC) {
+            acc = 0;
+            aph ^= 1u;
+          }
         }
       }
-    }
-    if (!ok) {
-      if (lane == 0) {
+      if (!ok) {
         atomicExch(args.err, 2);
         *abort_flag = 1;
         mma_commit(drain_bar);
+        mbar_wait(drain_bar, 0, kDrainCycles, no_abort);
       }
-      __syncwarp();
-      mbar_wait(drain_bar, 0, kDrainCycles, no_abort);
     }
+    __syncwarp();
   } else {
     // promotion warps 2..9: lane quarter q (the TMEM lanes this warp may read), column half hc
     const int e = warp - 2;
