@@ -34,6 +34,8 @@ def _dev_bf16(bits):
     ((384, 512, 1024), 14, 1),       # 256x64, split 4, beta = 1
     ((2048, 1536, 1024), 8, 0),      # 128x256, split 1
     ((640, 512, 2048), 25, 0),       # 128x128, stream-K
+    ((768, 1024, 2048), 40, 0),      # 256x256 cta_group::2 pair, split 1
+    ((520, 512, 2048), 41, 0),       # 256x256 cta_group::2 pair, split 2, ragged M
 ])
 def test_matches_rg_gemm_twice(rg, shape, v, beta):
     M, N, K = shape
