@@ -5,8 +5,10 @@ the smoothed stack (autotuned best-of tiles and split factors + the DP
 padding/splitting plan, O(1) lookup, fused execution), on one GB300.
 
 Setup (not timed, "offline once per hardware/software stack"): the autotune
-sweep times all 24 kernel variants (6 tiles x split-K 1/2/4/8) on every cell
-and builds the plan tables.  One timed step re-measures, for every cell, the
+sweep times all 44 kernel variants (6 tiles x {split-K 1/2/4/8, stream-K,
+2-CTA multicast pair}, and the two 256-row tiles as tcgen05 cta_group::2 pairs
+with split-K 1/2/4/8) on every cell, with the library's pruning, and builds the
+plan tables.  One timed step re-measures, for every cell, the
 plain fixed 128x128 tile and the smoothed plan with the paper's protocol (one
 warm-up launch, then the mean of 5 back-to-back launches between CUDA events),
 then computes both surfaces' mean and roughness in the library.
