@@ -247,3 +247,16 @@ def test_pad_only_plan_on_a_fine_offset_grid_matches_oracle(rg):
     rg.rg_plan_free(h)
     with pytest.raises(rg.RGError):
         rg.rg_plan_build(g, T0v, vids)                         # splitting still needs start == step
+
+
+def test_context_entry_points_reject_a_null_context(rg):
+    """Host-side argument checks of the context entry points, without a GPU."""
+    lib = rg.library()
+    g = _grid(rg, 1, 1, 1)
+    assert lib.rg_set_static_operands(None, 1) == rg.RG_ERR_INVALID
+    assert lib.rg_set_timeout_cycles(None, 5) == rg.RG_ERR_INVALID
+    assert lib.rg_gemm_memtwin(None, 128, 128, 128, None, 128, None, 128, None, 128, 1, None) == rg.RG_ERR_INVALID
+    import ctypes
+    assert lib.rg_sweep_memtwin(None, ctypes.byref(g), 1, None, None, None, None, None, None, None) \
+        == rg.RG_ERR_INVALID
+    assert lib.rg_gemm(None, 128, 128, 128, None, 128, None, 128, None, 128, 0, 0, 0, 0, 0, None) == rg.RG_ERR_INVALID
