@@ -19,7 +19,6 @@ from __future__ import annotations
 
 import argparse
 import json
-import math
 import os
 import statistics
 import subprocess
@@ -585,7 +584,7 @@ def extras(args, rg, ctx, grid, T0v, plan_smooth, A, B, C, flops, Mv, Nv, Kv, de
                       ("dp_split_pad_on_best_of_6", ladder["dp_split_pad_on_best_of_6"]["measured"]["mean_tflops"],
                        ladder["dp_split_pad_on_best_of_6"]["measured"]["R_N_slice"]))}
     # ---- four-surface decomposition (Sec. 4) with the memory twins
-    out["decomposition"] = decomposition(rg, ctx, grid, T0v, s1_rows, fixed_v, A, B, C, flops, p_burst, count)
+    out["decomposition"] = decomposition(rg, ctx, grid, T0v, s1_rows, fixed_v, A, B, C, p_burst, count)
     # ---- fine step-32 cross-tile N sweep at M = K = 4096 with DP padding on the fine grid (Sec. 8.3-8.4)
     if count * STEP >= 4096:
         out["fine_N_sweep"] = fine_n_sweep(rg, ctx, A, B, C)
@@ -602,12 +601,12 @@ def extras(args, rg, ctx, grid, T0v, plan_smooth, A, B, C, flops, Mv, Nv, Kv, de
     return out
 
 
-def decomposition(rg, ctx, grid, T0v, s1_rows, fixed_v, A, B, C, flops, p_burst, count):
+def decomposition(rg, ctx, grid, T0v, s1_rows, fixed_v, A, B, C, p_burst, count):
     """Compute / memory / GEMM / overhead surfaces (Sec. 4): the fixed tile over the whole grid, and
     every tile's twin on the largest-K slice for the best-of-6 surface and the N profile of Fig. 6."""
     out = {}
 
-    def summary(g, tg, tm, fl):
+    def summary(g, tg, tm):
         _, over, st = rg.rg_decompose(g, tg, tm, p_burst)
         _, r_mem, m_mem = rg.rg_surface_stats(g, tm)
         _, r_gemm, m_gemm = rg.rg_surface_stats(g, tg)
@@ -618,7 +617,7 @@ def decomposition(rg, ctx, grid, T0v, s1_rows, fixed_v, A, B, C, flops, p_burst,
                 "gemm_R_3D": r_gemm["R_3D"]}, over
 
     tm_fixed = rg.rg_sweep_memtwin(ctx, grid, [rg.variant_tile(fixed_v)], A, B, C)[0]
-    out["fixed_128x128_full_grid"], _ = summary(grid, T0v[fixed_v], tm_fixed, flops)
+    out["fixed_128x128_full_grid"], _ = summary(grid, T0v[fixed_v], tm_fixed)
     kmax = STEP * count
     gk = rg.make_grid((STEP, STEP, count), (STEP, STEP, count), (kmax, STEP, 1))
     tm6 = rg.rg_sweep_memtwin(ctx, gk, list(range(rg.RG_NUM_TILES)), A, B, C)
@@ -626,7 +625,7 @@ def decomposition(rg, ctx, grid, T0v, s1_rows, fixed_v, A, B, C, flops, p_burst,
     win = tg6.argmin(axis=0)
     cols = np.arange(tg6.shape[1])
     best_g, best_m = tg6[win, cols], tm6[win, cols]
-    out["best_of_6_K_max_slice"], over = summary(gk, best_g, best_m, None)
+    out["best_of_6_K_max_slice"], _ = summary(gk, best_g, best_m)
     # Fig. 6: the time stack along N at M = K = max, fixed tile
     ti = rg.variant_tile(fixed_v)
     row = slice((count - 1) * count, count * count)

@@ -5,7 +5,6 @@ import os
 from fractions import Fraction
 
 import numpy as np
-import pytest
 
 from oracle import landscape, roughness
 
