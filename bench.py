@@ -428,8 +428,8 @@ def main():
                    "timing": "per cell: 1 warm-up launch, device spin, mean of 5 back-to-back launches between "
                              "CUDA events (paper protocol, warm per cell: operands of small cells stay L2-resident "
                              "across their 5 launches, no flush); between timed steps: inputs larger than L2 (each "
-                             "step reads all of A and B, 2 x 32 MiB, and writes all of C, 64 MiB: 128 MiB against "
-                             "the 126 MB L2, across 65,536 cell measurements)",
+                             "step reads all of A and B, 2 x 32 MiB, and writes all of C, 64 MiB: 134 MB against "
+                             "the 129 MB L2, across 65,536 cell measurements)",
                    "parallelism": "single GPU" if world == 1 else f"{world} independent replicas"},
         "plain": {k: float(np.mean([p[k] for p in plain])) for k in plain[0]},
         "smoothed": {k: float(np.mean([s[k] for s in smooth])) for k in smooth[0]},
