@@ -188,17 +188,20 @@ def summarize(tf, r, mean):
 
 
 def sawtooth_period(series):
-    """Lag (in grid steps, 1..8) of the largest autocorrelation of the step-to-step changes."""
+    """Lag (in grid steps, 1..8) with the largest autocorrelation of the step-to-step changes; among lags
+    within 0.02 of the best, the smallest (a period's multiples correlate as well as the period itself)."""
     d = np.diff(np.asarray(series, dtype=np.float64))
     d = d - d.mean()
-    best, arg = -np.inf, None
+    corr = {}
     for lag in range(1, 9):
         if lag >= len(d):
             break
-        c = float(np.dot(d[:-lag], d[lag:]) / (np.linalg.norm(d[:-lag]) * np.linalg.norm(d[lag:]) + 1e-30))
-        if c > best:
-            best, arg = c, lag
-    return arg, best
+        corr[lag] = float(np.dot(d[:-lag], d[lag:]) / (np.linalg.norm(d[:-lag]) * np.linalg.norm(d[lag:]) + 1e-30))
+    if not corr:
+        return None, float("nan")
+    best = max(corr.values())
+    lag = min(k for k, c in corr.items() if c >= best - 0.02)
+    return lag, corr[lag]
 
 
 def cpu_baseline(count, budget_s=15.0, seed=0):
