@@ -300,7 +300,8 @@ typedef struct {
 typedef struct {
   int64_t admitted_ns, launched_ns, done_ns;
   int32_t batch;              /* index of the grouped launch that ran it, -1 if none */
-  int32_t status;             /* RG_OK, RG_ERR_ADMISSION or RG_ERR_INVALID */
+  int32_t status;             /* RG_OK; RG_ERR_ADMISSION (never fits the budget); or, from the checks of
+                                 rg_gemm made at admission, RG_ERR_INVALID / RG_ERR_ALIGN / RG_ERR_SHAPE */
 } rg_serve_result;
 typedef struct {
   int64_t requests, batches, admission_stalls;

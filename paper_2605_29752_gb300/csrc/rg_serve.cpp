@@ -21,6 +21,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdint>
 #include <chrono>
 #include <cmath>
 #include <deque>
@@ -81,6 +82,20 @@ struct Arena {  // first-fit allocator over one device allocation, 256-byte gran
 };
 
 int64_t request_bytes(const rg_serve_request& r) { return 2 * r.M * r.K + 2 * r.K * r.N + 4 * r.M * r.N; }
+
+// The per-request checks of rg_gemm (sizes, leading dimensions, TMA alignment),
+// made at admission so that one malformed request is rejected alone instead of
+// failing the grouped launch it would join.
+int request_status(const rg_serve_request& r) {
+  if (r.M <= 0 || r.N <= 0 || r.K <= 0 || !r.A || !r.B) return RG_ERR_INVALID;
+  if (r.lda < r.K || r.ldb < r.N || (r.C && r.ldc < r.N)) return RG_ERR_INVALID;
+  if ((reinterpret_cast<uintptr_t>(r.A) & 15) || (reinterpret_cast<uintptr_t>(r.B) & 15) || (r.lda % 8) ||
+      (r.ldb % 8))
+    return RG_ERR_ALIGN;
+  if (r.C && ((reinterpret_cast<uintptr_t>(r.C) & 15) || (r.ldc % 4))) return RG_ERR_ALIGN;
+  if (r.M > (1 << 30) || r.N > (1 << 30) || r.K > (1 << 30)) return RG_ERR_SHAPE;
+  return RG_OK;
+}
 
 double percentile(std::vector<double> v, double p) {
   if (v.empty()) return 0.0;
@@ -191,10 +206,10 @@ extern "C" int rg_serve(rg_ctx* ctx, const rg_plan* plan, const rg_serve_opts* o
     // admission, in arrival order
     while (next < n && reqs[next].arrival_ns <= now) {
       const rg_serve_request& r = reqs[next];
-      const int64_t bytes = request_bytes(r);
-      if (r.M <= 0 || r.N <= 0 || r.K <= 0 || bytes > opts->hbm_budget_bytes ||
-          (r.C == nullptr && 4 * r.M * r.N > arena.size)) {
-        results[next].status = r.M <= 0 || r.N <= 0 || r.K <= 0 ? RG_ERR_INVALID : RG_ERR_ADMISSION;
+      const int st = request_status(r);
+      const int64_t bytes = st == RG_OK ? request_bytes(r) : 0;
+      if (st != RG_OK || bytes > opts->hbm_budget_bytes || (r.C == nullptr && 4 * r.M * r.N > arena.size)) {
+        results[next].status = st != RG_OK ? st : RG_ERR_ADMISSION;
         results[next].done_ns = now;
         ++done_count;
         ++next;

@@ -131,3 +131,23 @@ def test_admission_budget(rg, ctx, streams):
     res, st = rg.rg_serve(ctx, None, opts, [(M, N, K, A, K, B, N, None, N, t) for M, N, K, t in trace])
     rg.rg_check(ctx)
     assert st["requests"] == 200 and st["tflops"] > 0
+
+
+def test_malformed_requests_are_rejected_alone(rg, ctx, streams):
+    """rg_gemm's checks run at admission: a misaligned, an undersized and a negative request
+    each get their own status while the well-formed requests around them are served."""
+    _, _, A, B = streams
+    opts = rg.rg_serve_opts_default()
+    opts.hbm_budget_bytes = 1 << 30
+    outs = [torch.full((256, 256), float("nan"), device="cuda") for _ in range(2)]
+    bad_c = torch.zeros(256 * 256 + 4, device="cuda")
+    reqs = [(256, 256, 256, A, 256, B, 256, outs[0], 256, 0),
+            (256, 256, 256, A, 252, B, 256, bad_c, 256, 0),             # lda < K
+            (256, 256, 256, A, 256, B, 256, bad_c[1:], 256, 0),          # C not 16-byte aligned
+            (-1, 256, 256, A, 256, B, 256, bad_c, 256, 0),               # negative size
+            (256, 256, 256, A, 256, B, 256, outs[1], 256, 0)]
+    res, st = rg.rg_serve(ctx, None, opts, reqs)
+    rg.rg_check(ctx)
+    assert [r["status"] for r in res] == [0, rg.RG_ERR_INVALID, rg.RG_ERR_ALIGN, rg.RG_ERR_INVALID, 0]
+    assert st["requests"] == 2
+    assert not torch.isnan(outs[0]).any() and torch.equal(outs[0], outs[1])
