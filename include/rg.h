@@ -270,9 +270,11 @@ int rg_gemm_grouped(rg_group* group, const rg_group_problem* problems, int32_t n
  * fit under hbm_budget_bytes next to the admitted, unfinished requests; one
  * that can never fit is rejected with RG_ERR_ADMISSION in its result.  Each
  * request goes through rg_plan_lookup (plan may be NULL): a single-leaf cell
- * lends its padded launch extents, a split cell runs as-is.  Whenever one of
- * max_inflight slots is free, up to max_batch admitted requests form one
- * grouped launch (rg_gemm_grouped, CUDA graph replay) on that slot's stream, so
+ * lends its tile shape (the tile of its autotuned variant) and its padded
+ * launch extents; a split cell, or any request without a plan, runs as-is on
+ * opts->tile.  Whenever one of max_inflight slots is free, up to max_batch
+ * admitted requests form one batch: one grouped launch per tile shape among
+ * them (rg_gemm_grouped, CUDA graph replay) on that slot's stream, so
  * batches formed while others run overlap them on the device; finished batches
  * release budget and admit waiting requests.  A request with C == NULL gets its
  * output (ldc = N) from an arena of hbm_budget_bytes allocated for the run and
@@ -284,7 +286,7 @@ typedef struct {
   int64_t hbm_budget_bytes;   /* default 64 GiB */
   int32_t max_batch;          /* requests per grouped launch; default 64 */
   int32_t max_inflight;       /* grouped launches on the GPU at once, 1..16; default 2 */
-  int32_t tile;               /* tile of the grouped kernel; default RG_TILE_128x128 */
+  int32_t tile;               /* tile for requests the plan does not route; default RG_TILE_128x128 */
   int32_t reserved;
 } rg_serve_opts;
 typedef struct {

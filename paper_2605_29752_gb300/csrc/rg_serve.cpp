@@ -8,10 +8,12 @@
 //     never fit is rejected (RG_ERR_ADMISSION); an admitted request whose C is
 //     NULL gets its output from an arena of budget bytes owned by the run;
 //   - routing: each request goes through the plan's O(1) lookup; a single-leaf
-//     cell contributes its padded launch extents (the DP's padding), a split cell
-//     runs as-is (its pieces would need ordered launches);
+//     cell contributes its autotuned tile shape and its padded launch extents (the
+//     DP's padding), a split cell runs as-is on the default tile (its pieces would
+//     need ordered launches);
 //   - batching: whenever an in-flight slot is free and admitted requests are
-//     waiting, up to max_batch of them become one grouped launch (a CUDA graph
+//     waiting, up to max_batch of them become one grouped launch per tile shape
+//     among them (a CUDA graph
 //     replay) on that slot's stream; up to max_inflight launches are on the GPU at
 //     once, so a batch admitted while another runs overlaps it on the device;
 //   - completion: slots are polled with events; a finished batch releases its
@@ -130,7 +132,7 @@ extern "C" int rg_serve(rg_ctx* ctx, const rg_plan* plan, const rg_serve_opts* o
   for (int32_t i = 0; i < n; ++i) need_arena = need_arena || reqs[i].C == nullptr;
 
   struct Slot {
-    rg_group* group = nullptr;
+    rg_group* group[RG_NUM_TILES] = {};  // one grouped kernel per tile shape
     cudaStream_t stream = nullptr;
     cudaEvent_t done = nullptr;
     std::vector<int32_t> members;
@@ -141,17 +143,20 @@ extern "C" int rg_serve(rg_ctx* ctx, const rg_plan* plan, const rg_serve_opts* o
   auto cleanup = [&]() {
     for (auto& s : slots) {
       if (s.stream) cudaStreamSynchronize(s.stream);
-      if (s.group) rg_group_destroy(s.group);
+      for (rg_group* g : s.group)
+        if (g) rg_group_destroy(g);
       if (s.done) cudaEventDestroy(s.done);
       if (s.stream) cudaStreamDestroy(s.stream);
     }
     arena.release_all();
   };
   for (auto& s : slots) {
-    int rc = rg_group_create(ctx, opts->tile, opts->max_batch, &s.group);
-    if (rc != RG_OK) {
-      cleanup();
-      return rc;
+    for (int t = 0; t < RG_NUM_TILES; ++t) {
+      const int rc = rg_group_create(ctx, t, opts->max_batch, &s.group[t]);
+      if (rc != RG_OK) {
+        cleanup();
+        return rc;
+      }
     }
     if (cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming) != cudaSuccess) {
@@ -172,7 +177,7 @@ extern "C" int rg_serve(rg_ctx* ctx, const rg_plan* plan, const rg_serve_opts* o
     results[i].batch = -1;
   }
   std::deque<int32_t> ready;
-  std::vector<rg_group_problem> probs;
+  std::vector<rg_group_problem> probs[RG_NUM_TILES];
   int64_t resident = 0, stalls = 0, batches = 0, done_count = 0;
   int32_t next = 0;
   bool stalled_head = false;
@@ -242,7 +247,7 @@ extern "C" int rg_serve(rg_ctx* ctx, const rg_plan* plan, const rg_serve_opts* o
     if (!ready.empty()) {
       for (auto& s : slots) {
         if (s.busy || ready.empty()) continue;
-        probs.clear();
+        for (auto& pv : probs) pv.clear();
         s.members.clear();
         while (!ready.empty() && static_cast<int32_t>(s.members.size()) < opts->max_batch) {
           const int32_t i = ready.front();
@@ -252,20 +257,24 @@ extern "C" int rg_serve(rg_ctx* ctx, const rg_plan* plan, const rg_serve_opts* o
           p.M = r.M; p.N = r.N; p.K = r.K;
           p.A = r.A; p.lda = r.lda; p.B = r.B; p.ldb = r.ldb;
           p.C = c_ptr[i]; p.ldc = r.C ? r.ldc : r.N;
-          if (plan) {
+          int tile = opts->tile;
+          if (plan) {  // a single-leaf cell lends its autotuned tile and its padded extents
             const rg_leaf* lv = nullptr;
             int32_t nl = 0;
             if (rg_plan_lookup(plan, r.M, r.N, r.K, &lv, &nl, nullptr) == RG_OK && nl == 1) {
+              tile = rg::variant_tile(lv[0].variant);
               p.pm = std::max(lv[0].pm, r.M);
               p.pn = std::max(lv[0].pn, r.N);
               p.pk = std::max(lv[0].pk, r.K);
             }
           }
-          probs.push_back(p);
+          probs[tile].push_back(p);
           s.members.push_back(i);
         }
         const int64_t t = now_ns();
-        rc = rg_gemm_grouped(s.group, probs.data(), static_cast<int32_t>(probs.size()), s.stream);
+        for (int tl = 0; tl < RG_NUM_TILES && rc == RG_OK; ++tl)  // one grouped launch per tile shape present
+          if (!probs[tl].empty())
+            rc = rg_gemm_grouped(s.group[tl], probs[tl].data(), static_cast<int32_t>(probs[tl].size()), s.stream);
         if (rc == RG_OK && cudaEventRecord(s.done, s.stream) != cudaSuccess)
           rc = rg::fail(RG_ERR_CUDA, "rg_serve: event record");
         if (rc != RG_OK) break;

@@ -151,3 +151,40 @@ def test_malformed_requests_are_rejected_alone(rg, ctx, streams):
     assert [r["status"] for r in res] == [0, rg.RG_ERR_INVALID, rg.RG_ERR_ALIGN, rg.RG_ERR_INVALID, 0]
     assert st["requests"] == 2
     assert not torch.isnan(outs[0]).any() and torch.equal(outs[0], outs[1])
+
+
+def test_serving_routes_each_request_to_its_autotuned_tile(rg, ctx, streams):
+    """A plan whose best tile differs from cell to cell (a synthetic T0 table over all six split-1
+    tiles): each batch runs one grouped launch per tile present, and every result matches the
+    oracle and, bitwise, rg_gemm with that cell's tile and padding."""
+    a_bits, b_bits, A, B = streams
+    g = rg.make_grid((128, 128, 8))
+    rows = [rg.variant(t, 1) for t in range(6)]
+    rs = np.random.default_rng(17)
+    T0 = rs.integers(1000, 100000, size=(6, 8 * 8 * 8)).astype(np.int64)
+    plan = rg.rg_plan_build_ex(g, T0, rows, rg.RG_PLAN_PAD_ONLY)
+    try:
+        trace = _trace(60, 50000.0, seed=6)
+        outs = [torch.full((M, N), float("nan"), device="cuda") for M, N, K, _ in trace]
+        opts = rg.rg_serve_opts_default()
+        opts.max_batch = 16
+        res, st = rg.rg_serve(ctx, plan, opts, _requests(trace, A, B, outs))
+        rg.rg_check(ctx)
+        assert all(r["status"] == 0 for r in res)
+        tiles_used = set()
+        for i, (M, N, K, _) in enumerate(trace):
+            a = og.bf16_bits_to_f64(a_bits[:M * K].reshape(M, K))
+            b = og.bf16_bits_to_f64(b_bits[:K * N].reshape(K, N))
+            ok, ratio = og.check(outs[i].cpu().numpy(), a, b)
+            assert ok, (i, ratio)
+            leaves, _ = rg.rg_plan_lookup(plan, M, N, K)
+            v, pm, pn, pk = leaves[0][0], leaves[0][9], leaves[0][10], leaves[0][11]
+            tiles_used.add(rg.variant_tile(v))
+            ref = torch.full((M, N), float("nan"), device="cuda")
+            rg.rg_gemm(ctx, M, N, K, A, K, B, N, ref, N, rg.variant(rg.variant_tile(v), 1), 0,
+                       max(pm, M), max(pn, N), max(pk, K))
+            rg.rg_check(ctx)
+            assert torch.equal(ref, outs[i]), i
+        assert len(tiles_used) >= 3
+    finally:
+        rg.rg_plan_free(plan)
