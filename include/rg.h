@@ -119,10 +119,14 @@ typedef struct {
   uint64_t seed;              /* shuffle seed; default 0                             */
   int64_t spin_ns;            /* device spin before each timed group, per queued launch,
                                  so the launches queue behind it; default 4000       */
-  int32_t prune_splits;       /* 1: skip split-K variants (S > 1) on cells where the
-                                 unsplit tile count already fills the SMs or a split
-                                 would get fewer than 2 K blocks; their entries are
-                                 set to RG_T_UNMEASURED; default 1                   */
+  int32_t prune_splits;       /* 1: skip variants that cannot help on a cell, their
+                                 entries set to RG_T_UNMEASURED; default 1:
+                                 split-K (S > 1, also cta_group::2) where the unsplit
+                                 CTA count already fills the SMs or a split would get
+                                 fewer than 2 K blocks; stream-K where whole waves
+                                 leave no remainder spread over several CTAs;
+                                 multicast pairs with fewer than 2 tiles;
+                                 cta_group::2 pairs with M <= 128                     */
   int32_t reserved;
 } rg_sweep_opts;
 /* Time entry of a (variant, cell) pair the sweep did not measure: larger than
