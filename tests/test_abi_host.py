@@ -278,3 +278,19 @@ def test_plan_tables_match_oracle_with_many_ties(rg):
         _compare_plan(rg, T0v, vids, (nm, nn, nk))
 
     check()
+
+
+def test_surface_stats_bit_exact_over_a_wide_dynamic_range(rg):
+    """Times from 1 ns to 1e15 ns make TFLOP/s values span about 24 orders of magnitude, where
+    a plain floating-point sum would lose the small terms; the correctly rounded sums must
+    still equal the oracle's math.fsum results bit for bit."""
+    rng = np.random.default_rng(23)
+    shape = (6, 7, 5)
+    t = np.exp(rng.uniform(0, np.log(1e15), size=shape)).astype(np.int64) + 1
+    g = _grid(rg, *shape)
+    ogrid = ((128, 128, shape[0]), (128, 128, shape[1]), (128, 128, shape[2]))
+    S = roughness.surface(t, ogrid)
+    tf, r, mean = rg.rg_surface_stats(g, t)
+    assert np.array_equal(tf.reshape(shape), S)
+    assert mean == roughness.mean(S)
+    assert r == roughness.roughness_all(S)
