@@ -5,10 +5,9 @@ the smoothed stack (autotuned best-of tiles and split factors + the DP
 padding/splitting plan, O(1) lookup, fused execution), on one GB300.
 
 Setup (not timed, "offline once per hardware/software stack"): the autotune
-sweep times all 44 kernel variants (6 tiles x {split-K 1/2/4/8, stream-K,
-2-CTA multicast pair}, and the two 256-row tiles as tcgen05 cta_group::2 pairs
-with split-K 1/2/4/8) on every cell, with the library's pruning, and builds the
-plan tables.  One timed step re-measures, for every cell, the
+sweep times all 38 kernel variants (6 tiles x {split-K 1/2/4/8, stream-K}, and
+the two 256-row tiles as tcgen05 cta_group::2 pairs with split-K 1/2/4/8) on
+every cell, with the library's pruning, and builds the plan tables.  One timed step re-measures, for every cell, the
 plain fixed 128x128 tile and the smoothed plan with the paper's protocol (one
 warm-up launch, then the mean of 5 back-to-back launches between CUDA events),
 then computes both surfaces' mean and roughness in the library.
@@ -47,6 +46,8 @@ def parse():
     p.add_argument("--count", type=int, default=COUNT, help="grid points per axis (32 = the full grid)")
     p.add_argument("--no-extras", action="store_true", help="skip the ladder / cross-tile / e2e / CPU sections")
     p.add_argument("--out", default=None, help="also write the JSON line (and surfaces) here")
+    p.add_argument("--clock-log", default=None,
+                   help="CSV file for the nvidia-smi clock samples of the timed region (default: a temp file)")
     p.add_argument("--shape", type=int, nargs=3, default=None, metavar=("M", "N", "K"),
                    help="time one GEMM shape with --variant instead of the landscape (profiling aid)")
     p.add_argument("--variant", default="256x256/S1", help="variant for --shape, e.g. 128x256/S1")
@@ -100,10 +101,11 @@ class ClockSampler:
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, index):
+    def __init__(self, index, path=None):
+        import tempfile
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+        self.path = path or os.path.join(tempfile.gettempdir(), f"rg_bench_clocks_rank{index}_{os.getpid()}.csv")
 
     def __enter__(self):
         try:
@@ -181,10 +183,53 @@ def stats_of(rg, grid, t_ns):
     return tf, r, mean
 
 
-def summarize(tf, r, mean):
-    return {"mean_tflops": mean, "p50_tflops": float(np.percentile(tf, 50)), "p99_tflops": float(np.percentile(tf, 99)),
-            "p01_tflops": float(np.percentile(tf, 1)), "max_tflops": float(tf.max()),
-            "R_N_slice": r["R_N_slice"], "R_3D": r["R_3D"], "R_M": r["R_M"], "R_N": r["R_N"], "R_K": r["R_K"]}
+def roof_times_ns(Mv, Nv, Kv, p_tflops, bw_gbs):
+    """Per-cell roofline time t_roof = max(2MNK / P, (2MK + 2KN + 4MN) / BW) in ns (useful flops and
+    algorithmic bytes of the BF16-in, FP32-out GEMM)."""
+    Mv, Nv, Kv = (np.asarray(x, dtype=np.float64) for x in (Mv, Nv, Kv))
+    t_c = 2.0 * Mv * Nv * Kv / (p_tflops * 1e3)
+    t_m = (2.0 * Mv * Kv + 2.0 * Kv * Nv + 4.0 * Mv * Nv) / bw_gbs
+    return np.maximum(t_c, t_m)
+
+
+def summarize(tf, r, mean, t_ns=None, troof=None):
+    out = {"mean_tflops": mean, "p50_tflops": float(np.percentile(tf, 50)),
+           "p99_tflops": float(np.percentile(tf, 99)), "p01_tflops": float(np.percentile(tf, 1)),
+           "max_tflops": float(tf.max()), "R_N_slice": r["R_N_slice"], "R_3D": r["R_3D"], "R_M": r["R_M"],
+           "R_N": r["R_N"], "R_K": r["R_K"], "R_N_slice_over_mean": r["R_N_slice"] / mean if mean else None}
+    if t_ns is not None and troof is not None:
+        # mean over cells of t_roof / t_measured: the per-stage roofline fraction
+        out["roofline_mean_frac"] = float(np.mean(troof / np.asarray(t_ns, dtype=np.float64).ravel()))
+    return out
+
+
+def slice_attribution(tf, count, kmax):
+    """Where the N-axis roughness of the largest-K slice sits: its adjacent-N pairs split by the
+    size MNK of the pair's larger cell (launch-bound < 1e9 <= mid < 1e10 <= saturated)."""
+    S = np.asarray(tf, dtype=np.float64).reshape(count, count, count)[:, :, -1]
+    d = np.abs(np.diff(S, axis=1))
+    M = (np.arange(1, count + 1) * STEP)[:, None].astype(np.float64)
+    N = (np.arange(2, count + 1) * STEP)[None, :].astype(np.float64)
+    mnk = M * N * float(kmax) * np.ones_like(d)
+    total = d.sum()
+    out = {}
+    for name, sel in (("MNK<1e9", mnk < 1e9), ("1e9<=MNK<1e10", (mnk >= 1e9) & (mnk < 1e10)),
+                      ("MNK>=1e10", mnk >= 1e10)):
+        out[name] = {"pair_share": float(sel.mean()), "abs_step_share": float(d[sel].sum() / total) if total else 0.0,
+                     "mean_abs_step": float(d[sel].mean()) if sel.any() else 0.0,
+                     "contribution_to_R_N_slice": float(d[sel].sum() / d.size)}
+    return out
+
+
+def noise_floor(tf_a, tf_b, count):
+    """Roughness of the repeat-to-repeat difference surface (tf_a - tf_b) / sqrt(2): what measurement
+    noise alone contributes to R_N on the largest-K slice and to the 3-axis R."""
+    D = ((np.asarray(tf_a, np.float64) - np.asarray(tf_b, np.float64)) / np.sqrt(2.0)).reshape(count, count, count)
+    rN_slice = float(np.mean(np.abs(np.diff(D[:, :, -1], axis=1))))
+    r3 = float(np.mean([np.mean(np.abs(np.diff(D, axis=ax))) for ax in range(3)]))
+    return {"R_N_slice": rN_slice, "R_3D": r3,
+            "median_abs_rel_diff_pct": float(100 * np.median(np.abs(np.asarray(tf_a) - np.asarray(tf_b)) /
+                                                           np.asarray(tf_b)))}
 
 
 def sawtooth_period(series):
@@ -204,31 +249,97 @@ def sawtooth_period(series):
     return lag, corr[lag]
 
 
-def cpu_baseline(count, budget_s=15.0, seed=0):
-    """The oracle's FP64 GEMM timed on this host's cores on a bounded, seeded sample of cells."""
+def cpu_info():
+    """CPU model and the BLAS numpy uses, for the CPU-baseline record."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if not model:
+        import platform
+        model = platform.processor() or platform.machine()
+    blas = None
+    try:
+        cfg = np.show_config(mode="dicts")
+        b = cfg.get("Build Dependencies", {}).get("blas", {})
+        blas = {k: b.get(k) for k in ("name", "version", "openblas configuration") if b.get(k)}
+    except Exception:  # noqa: BLE001 - older numpy has no dict mode
+        blas = None
+    return {"cpu_model": model, "numpy": np.__version__, "blas": blas}
+
+
+def cpu_baseline(count, seed=0, strata=256, gpu_config1=None):
+    """The oracle, as it stands, on this host's cores (numpy FP64 matmul uses every core):
+    (1) the 64 cells of the small sweep {128..512}^3, with the full-matrix error of the GPU's plain
+    kernel on each against the oracle when gpu_config1 is given; (2) a stratified sample of the whole
+    grid (cells sorted by MNK into `strata` equal strata, one seeded cell per stratum) extrapolated
+    to the full sweep; (3) the textbook triple loop at 128^3 on one core; (4) the host steps."""
     from oracle import gemm as og
-    cells = synthetic.uniform_cells(4096, (count, count, count), seed=seed)
-    t_start = time.perf_counter()
-    vals, flops, secs, used = [], 0.0, 0.0, []
-    for a, b, c in cells:
-        M, N, K = (int(a) + 1) * STEP, (int(b) + 1) * STEP, (int(c) + 1) * STEP
-        ab, bb = synthetic.operands_bf16(M, N, K, seed=0)
-        A, B = og.bf16_bits_to_f64(ab), og.bf16_bits_to_f64(bb)
-        t0 = time.perf_counter()
-        og.gemm_f64(A, B)
-        dt = time.perf_counter() - t0
-        vals.append(2.0 * M * N * K / dt / 1e12)
-        flops += 2.0 * M * N * K
-        secs += dt
-        used.append((M, N, K))
-        if time.perf_counter() - t_start > budget_s:
-            break
     cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
-    out = {"value": float(np.mean(vals)), "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
-           "sample": f"{len(used)} cells drawn uniformly from the {count}^3 grid (seed {seed}); oracle FP64 "
-                     f"GEMM (numpy matmul, float64) per cell; value = mean per-cell TFLOP/s; "
-                     f"aggregate {flops / secs / 1e12:.4f} TFLOP/s over {secs:.1f} s",
-           "aggregate_tflops": flops / secs / 1e12}
+    Mx = STEP * count
+    a64 = og.bf16_bits_to_f64(synthetic.bf16_uniform_stream(0, synthetic.TAG_A, Mx * Mx))
+    b64 = og.bf16_bits_to_f64(synthetic.bf16_uniform_stream(0, synthetic.TAG_B, Mx * Mx))
+
+    def operands(M, N, K):
+        return a64[:M * K].reshape(M, K), b64[:K * N].reshape(K, N)
+
+    def timed(M, N, K):
+        A, B = operands(M, N, K)
+        t0 = time.perf_counter()
+        c = og.gemm_f64(A, B)
+        return time.perf_counter() - t0, c
+    out = {"unit": "TFLOP/s", "cores": cores, "kind": "oracle", **cpu_info()}
+    # (1) small sweep
+    c1_vals, c1_flops, c1_secs, worst = [], 0.0, 0.0, 0.0
+    small = [128, 256, 384, 512]
+    for M in small:
+        for N in small:
+            for K in small:
+                dt, c64 = timed(M, N, K)
+                c1_vals.append(2.0 * M * N * K / dt / 1e12)
+                c1_flops += 2.0 * M * N * K
+                c1_secs += dt
+                if gpu_config1 is not None:
+                    A, B = operands(M, N, K)
+                    ratio, exact = og.error_ratio(gpu_config1(M, N, K), c64, og.abs_sum(A, B))
+                    worst = max(worst, ratio if exact else float("inf"))
+    out["small_sweep_64_cells"] = {"mean_tflops": float(np.mean(c1_vals)), "aggregate_tflops": c1_flops / c1_secs / 1e12,
+                                   "seconds": c1_secs}
+    if gpu_config1 is not None:
+        out["small_sweep_64_cells"]["gpu_plain_max_error_ratio"] = worst
+        out["small_sweep_64_cells"]["error_bound_at_K512"] = og.bound(512)
+    # (2) stratified sample of the whole grid
+    Mv, Nv, Kv = cell_sizes(count)
+    fl = 2.0 * Mv * Nv * Kv
+    order = np.argsort(fl, kind="stable")
+    groups = np.array_split(order, strata)
+    rs = np.random.default_rng(seed)
+    vals, secs, flops, extrap = [], 0.0, 0.0, 0.0
+    for g in groups:
+        i = int(g[rs.integers(len(g))])
+        dt, _ = timed(int(Mv[i]), int(Nv[i]), int(Kv[i]))
+        vals.append(fl[i] / dt / 1e12)
+        secs += dt
+        flops += fl[i]
+        extrap += dt * len(g)
+    out.update({"value": float(np.mean(vals)), "aggregate_tflops": flops / secs / 1e12,
+                "full_sweep_extrapolated_s": extrap, "full_sweep_flops": float(fl.sum()),
+                "full_sweep_extrapolated_tflops": float(fl.sum()) / extrap / 1e12,
+                "sample": f"{strata} cells, one per stratum of the {count}^3 grid sorted by MNK ({len(groups[0])} "
+                          f"cells per stratum, seed {seed}); oracle FP64 numpy matmul per cell on {cores} cores; "
+                          f"value = mean per-cell TFLOP/s; {secs:.1f} s of CPU GEMM; the full sweep extrapolated as "
+                          f"sum over strata of (sample time x stratum size)"})
+    # (3) triple loop, one core
+    A, B = operands(128, 128, 128)
+    t0 = time.perf_counter()
+    og.gemm_f64_loops(A, B)
+    dt = time.perf_counter() - t0
+    out["triple_loop_128cube_one_core"] = {"seconds": dt, "tflops": 2.0 * 128 ** 3 / dt / 1e12}
     out.update(host_steps_timing(count, seed))
     return out
 
@@ -370,7 +481,7 @@ def main():
     n_launch0 = rg.rg_launch_count(ctx)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     results = []
-    with ClockSampler(local) as clk:
+    with ClockSampler(local, args.clock_log) as clk:
         torch.cuda.nvtx.range_push("timed")
         ev0.record()
         t0 = time.perf_counter()
@@ -385,20 +496,31 @@ def main():
     n_launch = rg.rg_launch_count(ctx) - n_launch0
     step_ms = max_over_ranks(ev0.elapsed_time(ev1) / args.steps, dist, dev)
 
-    plain = [summarize(*stats_of(rg, grid, tp)) for tp, _ in results]
-    smooth = [summarize(*stats_of(rg, grid, ts)) for _, ts in results]
+    peaks = {}
+    pk_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pk_path):
+        peaks = json.load(open(pk_path))
+    p_burst = peaks.get("bf16_tflops") or 1900.0
+    bw = peaks.get("hbm_gbs") or 6800.0
+    peak_src = "measured" if peaks else "fallback"
+    troof = roof_times_ns(Mv, Nv, Kv, p_burst, bw)
+
+    plain = [summarize(*stats_of(rg, grid, tp), t_ns=tp, troof=troof) for tp, _ in results]
+    smooth = [summarize(*stats_of(rg, grid, ts), t_ns=ts, troof=troof) for _, ts in results]
     value = mean_over_ranks(float(np.mean([s["mean_tflops"] for s in smooth])), dist, dev)
     last_p, last_s = results[-1]
     agg_flops = float(flops.sum())
     agg_smooth = agg_flops / (last_s.astype(np.float64).sum() * 1e-9) / 1e12
     agg_plain = agg_flops / (last_p.astype(np.float64).sum() * 1e-9) / 1e12
-
-    peaks = {}
-    pk_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
-    if os.path.exists(pk_path):
-        peaks = json.load(open(pk_path))
-    p_burst = peaks.get("bf16_tflops", 1900.7 if not peaks else None) or 1900.7
-    peak_src = "measured" if peaks else "fallback"
+    tf_p = [stats_of(rg, grid, tp)[0] for tp, _ in results]
+    tf_s = [stats_of(rg, grid, ts)[0] for _, ts in results]
+    rough = {"plain_slice_attribution": slice_attribution(tf_p[-1], count, Mx),
+             "smoothed_slice_attribution": slice_attribution(tf_s[-1], count, Mx)}
+    if len(results) >= 2:
+        rough["noise_floor_plain"] = noise_floor(tf_p[-1], tf_p[-2], count)
+        rough["noise_floor_smoothed"] = noise_floor(tf_s[-1], tf_s[-2], count)
+    rough["note"] = ("N-axis roughness of the K = max slice split by the size of each adjacent pair's larger "
+                     "cell; noise floor = roughness of (repeat - repeat) / sqrt(2) of two timed steps")
 
     # dominant kernel of the smoothed pass: the variant whose single-leaf cells take the most device time
     leaf_v = np.full(ncell, -1, dtype=np.int64)
@@ -425,8 +547,8 @@ def main():
         "data": "synthetic",
         "config": {"workload": f"BF16 NN GEMM landscape, (M,N,K) in {{128..{Mx} step 128}}^3 = {ncell} cells, "
                                f"U[-1,1) BF16 operands (seed 0), FP32 accumulate/output",
-                   "smoothed": "best-of-38 autotune (6 tiles x {split-K 1/2/4/8, stream-K, 2-CTA multicast "
-                               "pair} + 2 cta_group::2 tiles) + DP pad/split plan, O(1) lookup",
+                   "smoothed": f"best-of-{rg.RG_NUM_VARIANTS} autotune (6 tiles x {{split-K 1/2/4/8, stream-K}} + "
+                               "2 cta_group::2 tiles x split-K 1/2/4/8) + DP pad/split plan, O(1) lookup",
                    "plain": "fixed 128x128 tile, split 1",
                    "timing": "per cell: 1 warm-up launch, device spin, mean of 5 back-to-back launches between "
                              "CUDA events (paper protocol, warm per cell: operands of small cells stay L2-resident "
@@ -441,6 +563,7 @@ def main():
         "mean_gain_pct": 100.0 * (value / np.mean([p["mean_tflops"] for p in plain]) - 1),
         "roofline": {"bound": "tensor", "achieved": dom_ach, "peak": p_burst, "unit": "TFLOP/s",
                      "frac": dom_ach / p_burst, "traffic": None,
+                     "mean_frac": float(np.mean([q["roofline_mean_frac"] for q in smooth])),
                      "kernel": f"gemm_bf16 {rg.variant_name(dom)}",
                      "note": f"dominant kernel of the smoothed pass ({100 * dom_share:.1f}% of its device time, "
                              f"{int(dsel.sum())} single-launch cells): useful 2MNK flops / CUDA-event time of "
@@ -448,6 +571,12 @@ def main():
                              f"differ in size, so DRAM traffic is given per launch for one captured shape "
                              f"under roofline_capture"},
         "roofline_all_gemms": {"achieved": agg_smooth, "frac": agg_smooth / p_burst, "unit": "TFLOP/s"},
+        "roofline_mean_frac": {"plain": float(np.mean([p["roofline_mean_frac"] for p in plain])),
+                               "smoothed": float(np.mean([q["roofline_mean_frac"] for q in smooth])),
+                               "definition": "mean over the cells of t_roof / t_measured, t_roof = max(2MNK / P, "
+                                             "(2MK + 2KN + 4MN) / BW)", "P_tflops": p_burst, "BW_gbs": bw,
+                               "peaks": peak_src},
+        "roughness_analysis": rough,
         "plain_aggregate_tflops": agg_plain,
         "peak_cell": {"M": int(Mv[bi]), "N": int(Nv[bi]), "K": int(Kv[bi]), "tflops": float(best_tf[bi]),
                       "variant": rg.variant_name(int(T0v[:, bi].argmin())), "frac": float(best_tf[bi]) / p_burst},
@@ -461,7 +590,7 @@ def main():
         line["roofline_capture"] = roofline_capture(rg, ctx, p_burst, dev)
     if not args.no_extras and rank == 0:
         line.update(extras(args, rg, ctx, grid, T0v, plan_smooth, A, B, C, flops, Mv, Nv, Kv, dev, a_bits, b_bits,
-                           s1_rows, fixed_v, p_burst, sms))
+                           s1_rows, fixed_v, p_burst, sms, troof, bw))
     rg.rg_plan_free(plan_smooth)
     rg.rg_destroy(ctx)
     if rank == 0:
@@ -519,33 +648,33 @@ def roofline_capture(rg, ctx, p_burst, dev, reps=10):
 
 
 def extras(args, rg, ctx, grid, T0v, plan_smooth, A, B, C, flops, Mv, Nv, Kv, dev, a_bits, b_bits, s1_rows,
-           fixed_v, p_burst, sms):
+           fixed_v, p_burst, sms, troof, bw):
     import torch
     out = {}
     count = args.count
     # ---- ladder: fixed -> best-of-6 -> DP pad -> DP split+pad -> autotuner + DP (Sec. 7.5, Table 10)
     ladder = {}
     tf, r, m = rg.rg_surface_stats(grid, T0v[fixed_v])
-    ladder["fixed_128x128"] = summarize(tf, r, m)
+    ladder["fixed_128x128"] = summarize(tf, r, m, T0v[fixed_v], troof)
     T6 = T0v[s1_rows]
     tf, r, m = rg.rg_surface_stats(grid, T6.min(axis=0))
-    ladder["best_of_6"] = summarize(tf, r, m)
+    ladder["best_of_6"] = summarize(tf, r, m, T6.min(axis=0), troof)
     tf, r, m = rg.rg_surface_stats(grid, T0v.min(axis=0))
-    ladder["best_of_all_variants_autotune"] = summarize(tf, r, m)
+    ladder["best_of_all_variants_autotune"] = summarize(tf, r, m, T0v.min(axis=0), troof)
     for name, rows, flags in (("dp_pad_on_best_of_6", s1_rows, rg.RG_PLAN_PAD_ONLY),
                               ("dp_split_pad_on_best_of_6", s1_rows, 0),
                               ("dp_split_pad_on_fixed", [fixed_v], 0)):
         h = rg.rg_plan_build_ex(grid, T0v[rows], rows, flags)
         t = rg.rg_plan_tables(h)
         tf, r, m = rg.rg_surface_stats(grid, t["T2"])
-        pred = summarize(tf, r, m)
+        pred = summarize(tf, r, m, t["T2"], troof)
         meas = rg.rg_sweep(ctx, grid, [0], A, B, C, plan=h)[0]
         tf, r, m = rg.rg_surface_stats(grid, meas)
-        ladder[name] = {"predicted": pred, "measured": summarize(tf, r, m)}
+        ladder[name] = {"predicted": pred, "measured": summarize(tf, r, m, meas, troof)}
         rg.rg_plan_free(h)
     t = rg.rg_plan_tables(plan_smooth)
     tf, r, m = rg.rg_surface_stats(grid, t["T2"])
-    ladder["autotune_dp_split_pad_predicted"] = summarize(tf, r, m)
+    ladder["autotune_dp_split_pad_predicted"] = summarize(tf, r, m, t["T2"], troof)
     out["ladder"] = ladder
     # ---- DP action distribution at the largest K (Sec. 7.3, Table 9)
     act = t["action"][:, :, -1].ravel()
@@ -566,8 +695,9 @@ def extras(args, rg, ctx, grid, T0v, plan_smooth, A, B, C, flops, Mv, Nv, Kv, de
             t_line = T0v[v].reshape(count, count, count)[ia, :, ik]
             tfl = 2.0 * 2048 * 2048 * (np.arange(1, count + 1) * STEP) / (t_line * 1e3)
             lag, corr = sawtooth_period(tfl)
-            ct[rg.variant_name(v)] = {"period_steps": lag, "autocorr": corr, "mean": float(tfl.mean()),
-                                      "roughness": float(np.mean(np.abs(np.diff(tfl))))}
+            ct[rg.variant_name(v)] = {"period": "aliased at step 128 (periods below 256 cannot show; see "
+                                                "fine_N_sweep)", "best_lag_steps": lag, "lag_autocorr": corr,
+                                      "mean": float(tfl.mean()), "roughness": float(np.mean(np.abs(np.diff(tfl))))}
         out["cross_tile_N_at_M_K_2048"] = ct
     # ---- first-principles GB300 landscapes (Sec. 9) and KOL grades (Sec. 10) of the measured surfaces
     bw = (json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("hbm_gbs", 6800.0)
@@ -596,14 +726,40 @@ def extras(args, rg, ctx, grid, T0v, plan_smooth, A, B, C, flops, Mv, Nv, Kv, de
     # ---- measurement methodology (Sec. 5.3-5.4, Sec. 8.2): run-order drift, co-allocation, per-config spread
     out["methodology"] = methodology(rg, ctx, grid, T0v, fixed_v, plan_smooth, A, B, C, dev, count)
     # ---- serving (continuous batching over the grouped GEMM), at half the saturated capacity
-    out["serving"] = serving(rg, ctx, grid, T0v, A, B, count)
+    out["serving"] = serving(rg, ctx, plan_smooth, A, B, count)
     # ---- FP8 e4m3 block-scaled GEMM on the {512..4096 step 512}^3 subgrid
     out["fp8"] = fp8_landscape(rg, ctx, dev, count)
     # ---- e2e: host buffers through the public API (H2D, plan GEMM, D2H per cell)
     out["e2e"] = e2e(rg, ctx, plan_smooth, a_bits, b_bits, dev, count)
-    # ---- CPU oracle baseline on this host
-    out["cpu_baseline"] = cpu_baseline(count)
+    # ---- the small sweep {128..512}^3 on the fixed tile (its own configuration)
+    out["small_sweep_config"] = small_sweep(rg, ctx, A, B, C, fixed_v, p_burst, bw)
+
+    def gpu_config1(M, N, K):
+        Cc = torch.empty((M, N), device=dev)
+        rg.rg_gemm(ctx, M, N, K, A, K, B, N, Cc, N, fixed_v)
+        rg.rg_check(ctx)
+        return Cc.cpu().numpy()
+    # ---- CPU oracle baseline on this host (and the small sweep's full-matrix errors against it)
+    out["cpu_baseline"] = cpu_baseline(count, gpu_config1=gpu_config1 if count >= 4 else None)
+    if count >= 4:
+        out["small_sweep_config"]["max_error_ratio_vs_oracle"] = \
+            out["cpu_baseline"]["small_sweep_64_cells"]["gpu_plain_max_error_ratio"]
+        out["small_sweep_config"]["error_bound"] = "K * 2^-24 (K <= 512: 3.05e-5)"
     return out
+
+
+def small_sweep(rg, ctx, A, B, C, fixed_v, p_burst, bw):
+    """The 64-cell sweep (M, N, K) in {128, 256, 384, 512}^3 with the single fixed 128x128 tile: its
+    surface (from rg_sweep), roughness along each axis, mean TFLOP/s and roofline fraction."""
+    g = rg.make_grid((STEP, STEP, 4))
+    t, tf, st = rg.rg_sweep_surfaces(ctx, g, [fixed_v], A, B, C)
+    Mv, Nv, Kv = cell_sizes(4)
+    troof = roof_times_ns(Mv, Nv, Kv, p_burst, bw)
+    keys = rg.SWEEP_STATS
+    return {"grid": "{128, 256, 384, 512}^3 = 64 cells", "variant": rg.variant_name(fixed_v),
+            **{k: float(st[0][i]) for i, k in enumerate(keys)},
+            "roofline_mean_frac": float(np.mean(troof / t[0].astype(np.float64))),
+            "surface_tflops": [round(float(x), 3) for x in tf[0]]}
 
 
 def decomposition(rg, ctx, grid, T0v, s1_rows, fixed_v, A, B, C, p_burst, count):
@@ -749,11 +905,10 @@ def methodology(rg, ctx, grid, T0v, fixed_v, plan, A, B, C, dev, count, runs=50)
     return out
 
 
-def serving(rg, ctx, grid, T0v, A, B, count, n_req=20000, n_warm=1000, tile=1):
+def serving(rg, ctx, plan, A, B, count, n_req=20000, n_warm=1000, tile=1):
     """Poisson stream of GEMM requests, shapes uniform over the grid cells, served by rg_serve with a
-    64 GB budget; the rate is half the measured saturated capacity."""
-    rows = [rg.variant(t, 1) for t in range(rg.RG_NUM_TILES)]   # the grouped kernel runs split 1 tiles
-    plan = rg.rg_plan_build_ex(grid, T0v[rows], rows, rg.RG_PLAN_PAD_ONLY)
+    64 GB budget through the smoothed plan (each request's leaves: autotuned variant, padding and
+    splits); the rate is half the measured saturated capacity."""
     opts = rg.rg_serve_opts_default()
     opts.hbm_budget_bytes = 64 << 30
     opts.max_batch = 64
@@ -770,25 +925,25 @@ def serving(rg, ctx, grid, T0v, A, B, count, n_req=20000, n_warm=1000, tile=1):
         reqs = [(M, N, K, A, K, B, N, None, N, t) for M, N, K, t in tr]
         return rg.rg_serve(ctx, plan, opts, reqs)
 
-    try:
-        run(trace(500, None, 11))                                   # warm the graphs and clocks
-        _, closed = run(trace(4000, None, 12))                      # all arrive at t = 0: saturated
-        capacity = 4000 / closed["wall_s"]
-        rate = 0.5 * capacity
-        run(trace(n_warm, rate, 13))
-        res, st = run(trace(n_req, rate, 14))
-    finally:
-        rg.rg_plan_free(plan)
+    run(trace(500, None, 11))                                   # warm the graphs and clocks
+    _, closed = run(trace(4000, None, 12))                      # all arrive at t = 0: saturated
+    capacity = 4000 / closed["wall_s"]
+    rate = 0.5 * capacity
+    run(trace(n_warm, rate, 13))
+    res, st = run(trace(n_req, rate, 14))
     ok = sum(1 for r in res if r["status"] == 0)
+    leaves = [len(rg.rg_plan_lookup(plan, M, N, K)[0]) for M, N, K, _ in trace(n_req, rate, 14)]
     return {"requests": n_req, "served": ok, "warmup_requests": n_warm, "rate_req_per_s": rate,
             "saturated_capacity_req_per_s": capacity, "saturated_tflops": closed["tflops"],
             "p50_latency_us": st["p50_latency_us"], "p99_latency_us": st["p99_latency_us"],
             "mean_latency_us": st["mean_latency_us"], "tflops": st["tflops"], "batches": st["batches"],
             "admission_stalls": st["admission_stalls"], "hbm_budget_gb": 64,
-            "tiles": "per request, the best-of-6 tile of a pad-only plan (one grouped launch per tile in a batch)",
+            "routing": f"the smoothed plan ({rg.RG_NUM_VARIANTS}-variant autotune + DP pad/split): each request "
+                       f"becomes its cell's leaves, phase by phase one grouped launch per kernel family "
+                       f"(split-K and cta_group::2 items; stream-K choices run as their tile, split 1)",
+            "multi_leaf_requests_share": float(np.mean(np.array(leaves) > 1)),
             "max_batch": opts.max_batch, "max_inflight": opts.max_inflight,
-            "note": "latency = host-observed completion - arrival; requests route through a best-of-6 "
-                    "pad-only plan lookup; outputs from a 64 GB arena"}
+            "note": "latency = host-observed completion - arrival; outputs from a 64 GB arena"}
 
 
 def fp8_landscape(rg, ctx, dev, count):
@@ -815,37 +970,33 @@ def fp8_landscape(rg, ctx, dev, count):
 
 
 def e2e(rg, ctx, plan, a_bits, b_bits, dev, count, ncells=96):
+    """The smoothed plan end to end through the C ABI on host buffers: rg_gemm_plan_host copies
+    the cell's A and B from pinned host memory, executes the plan and copies C back to pinned
+    host memory before it returns; timed on the host clock per call."""
     import torch
     cells = synthetic.uniform_cells(ncells, (count, count, count), seed=7)
     Mx = STEP * count
     ha = torch.from_numpy(a_bits.view(np.int16)).pin_memory()
     hb = torch.from_numpy(b_bits.view(np.int16)).pin_memory()
     hc = torch.empty(Mx * Mx, dtype=torch.float32).pin_memory()
-    da = torch.empty(Mx * Mx, dtype=torch.int16, device=dev)
-    db = torch.empty(Mx * Mx, dtype=torch.int16, device=dev)
-    dc = torch.empty(Mx * Mx, dtype=torch.float32, device=dev)
-    vals, h2d, d2h = [], 0, 0
     stream = torch.cuda.current_stream()
-    for rep in range(2):                              # first pass warms up
+    vals, h2d, d2h = [], 0, 0
+    for rep in range(2):                              # the first pass grows the staging buffers and warms up
         vals = []
         h2d = d2h = 0
         for a, b, c in cells:
             M, N, K = (int(a) + 1) * STEP, (int(b) + 1) * STEP, (int(c) + 1) * STEP
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record()
-            da[:M * K].copy_(ha[:M * K], non_blocking=True)
-            db[:K * N].copy_(hb[:K * N], non_blocking=True)
-            rg.rg_gemm_plan(ctx, plan, M, N, K, da, K, db, N, dc, N, stream=stream)
-            hc[:M * N].copy_(dc[:M * N], non_blocking=True)
-            e1.record()
-            e1.synchronize()
-            vals.append(2.0 * M * N * K / (e0.elapsed_time(e1) * 1e-3) / 1e12)
+            t0 = time.perf_counter()
+            rg.rg_gemm_plan_host(ctx, plan, M, N, K, ha, K, hb, N, hc, N, stream=stream)
+            dt = time.perf_counter() - t0
+            vals.append(2.0 * M * N * K / dt / 1e12)
             h2d += 2 * M * K + 2 * K * N
             d2h += 4 * M * N
     return {"value": float(np.mean(vals)), "unit": "TFLOP/s", "h2d_bytes_per_step": int(h2d),
-            "d2h_bytes_per_step": int(d2h),
-            "sample": f"{ncells} cells drawn uniformly (seed 7); per cell pinned-host A,B -> device, "
-                      f"rg_gemm_plan, C -> pinned host, timed with CUDA events; mean per-cell TFLOP/s"}
+            "d2h_bytes_per_step": int(d2h), "api": "rg_gemm_plan_host (C ABI, host buffers)",
+            "sample": f"{ncells} cells drawn uniformly (seed 7); per cell one rg_gemm_plan_host call: pinned-host "
+                      f"A, B -> device staging, plan GEMM, C -> pinned host, stream synchronised inside the call; "
+                      f"host-clock time per call; mean per-cell TFLOP/s"}
 
 
 if __name__ == "__main__":

@@ -55,10 +55,10 @@ enum {
 
 /* ---- kernel variants ----
  * Six output tiles (BM x BN), each with an in-kernel split-K factor S in
- * {1, 2, 4, 8} (id = tile * RG_NUM_SPLITS + log2(S)), a stream-K
- * schedule (id = RG_VARIANT_SK(tile)) and a 2-CTA multicast pair
- * (id = RG_VARIANT_PAIR(tile)).  Ties in best-of selection go to the
- * lowest id.                                                   (Sec. 6.1, 6.4) */
+ * {1, 2, 4, 8} (id = tile * RG_NUM_SPLITS + log2(S)) and a stream-K schedule
+ * (id = RG_VARIANT_SK(tile)); the two 256-row tiles with BN >= 128 also run as
+ * tcgen05 cta_group::2 pairs (RG_VARIANT_2SM).  Ties in best-of selection go
+ * to the lowest id.                                           (Sec. 6.1, 6.4) */
 enum {
   RG_TILE_128x64 = 0, RG_TILE_128x128 = 1, RG_TILE_128x256 = 2,
   RG_TILE_256x64 = 3, RG_TILE_256x128 = 4, RG_TILE_256x256 = 5,
@@ -71,21 +71,26 @@ enum {
  * (each CTA at least 4 K blocks); a tile whose iterations span several CTAs is
  * summed by its last arriving piece in the fixed order of their K ranges. */
 #define RG_VARIANT_SK(tile) (RG_NUM_TILES * RG_NUM_SPLITS + (tile))
-/* Pair variant of a tile (ids 30..35): 2-CTA clusters on neighbouring output
- * tiles that share one operand tile (B for tiles with BN >= BM, pairs along M;
- * A otherwise, pairs along N); each CTA loads half of the shared tile and TMA
- * multicasts it to both, halving that operand's L2 reads. */
-#define RG_VARIANT_PAIR(tile) (RG_NUM_TILES * RG_NUM_SPLITS + RG_NUM_TILES + (tile))
-/* 2-SM variant of a 256-row tile (ids 36..39 for 256x128, 40..43 for 256x256,
+/* 2-SM variant of a 256-row tile (ids 30..33 for 256x128, 34..37 for 256x256,
  * split-K 1/2/4/8): a 2-CTA cluster computes one 256 x BN tile as a single
  * tcgen05 cta_group::2 MMA unit; each CTA loads 128 rows of A and BN/2 columns
  * of B and holds its 128 output rows in its own TMEM, so each SM moves
  * 128 x BK + BN/2 x BK operand elements per K block instead of 256 x BK + BN x BK.
  * With split-K each CTA publishes and reduces its own 128 rows as in the 1-CTA
- * kernels (same workspace, tickets and fixed summation order). */
+ * kernels (same workspace, tickets and fixed summation order).  No kernel of
+ * this library uses TMA multicast. */
 #define RG_VARIANT_2SM(tile, log2_split) \
-  (RG_NUM_TILES * RG_NUM_SPLITS + 2 * RG_NUM_TILES + ((tile) - RG_TILE_256x128) * RG_NUM_SPLITS + (log2_split))
-#define RG_NUM_VARIANTS (RG_NUM_TILES * RG_NUM_SPLITS + 2 * RG_NUM_TILES + 2 * RG_NUM_SPLITS)
+  (RG_NUM_TILES * RG_NUM_SPLITS + RG_NUM_TILES + ((tile) - RG_TILE_256x128) * RG_NUM_SPLITS + (log2_split))
+/* cta_group::2 stream-K variant of a 256-row tile (id 38 for 256x128, 39 for
+ * 256x256): whole waves of 256 x BN pair tiles run data-parallel on the 2-CTA
+ * clusters; the remainder tiles' K iterations are divided evenly among at most
+ * one cluster per SM pair (each at least 4 K blocks, at most 4 clusters per
+ * tile), and each CTA of a cluster sums its own 128 rows of a shared tile in
+ * the fixed order of the pieces' K ranges.  It removes the partial last wave
+ * that quantises the large cells (Sec. 9.4 names split-K as the remedy). */
+#define RG_VARIANT_2SM_SK(tile) (RG_NUM_TILES * RG_NUM_SPLITS + RG_NUM_TILES + 2 * RG_NUM_SPLITS + \
+                                 (tile) - RG_TILE_256x128)
+#define RG_NUM_VARIANTS (RG_NUM_TILES * RG_NUM_SPLITS + RG_NUM_TILES + 2 * RG_NUM_SPLITS + 2)
 
 typedef struct rg_ctx rg_ctx;
 typedef struct rg_plan rg_plan;
@@ -123,9 +128,9 @@ typedef struct {
                                  entries set to RG_T_UNMEASURED; default 1:
                                  split-K (S > 1, also cta_group::2) where the unsplit
                                  CTA count already fills the SMs or a split would get
-                                 fewer than 2 K blocks; stream-K where whole waves
-                                 leave no remainder spread over several CTAs;
-                                 multicast pairs with fewer than 2 tiles;
+                                 fewer than 2 K blocks; stream-K (also cta_group::2)
+                                 where there is no whole wave or the remainder is not
+                                 spread over more CTAs than it has tiles;
                                  cta_group::2 pairs with M <= 128                     */
   int32_t reserved;
 } rg_sweep_opts;
@@ -221,6 +226,18 @@ int rg_plan_lookup(const rg_plan* plan, int64_t M, int64_t N, int64_t K,
 int rg_gemm_plan(rg_ctx* ctx, const rg_plan* plan, int64_t M, int64_t N, int64_t K,
                  const void* A, int64_t lda, const void* B, int64_t ldb,
                  float* C, int64_t ldc, void* stream);
+/* rg_gemm_plan on HOST buffers, for callers whose operands live in host memory:
+ * copies A (M x K, lda) and B (K x N, ldb) from the host into device staging
+ * buffers the context owns (allocated on first use and grown when a larger
+ * problem comes; leading dimensions rounded up to the TMA alignment there),
+ * executes the plan on `stream`, copies C (M x N, ldc) back and synchronises
+ * the stream, so C holds the result on return.  Host buffers may be pageable
+ * or pinned (pinned memory makes the copies asynchronous DMA).  M, N, K > 0.
+ * Errors: those of rg_gemm_plan, RG_ERR_OOM for a staging buffer,
+ * RG_ERR_TIMEOUT as rg_check.  Not for concurrent use of one context. */
+int rg_gemm_plan_host(rg_ctx* ctx, const rg_plan* plan, int64_t M, int64_t N, int64_t K,
+                      const void* A, int64_t lda, const void* B, int64_t ldb,
+                      float* C, int64_t ldc, void* stream);
 /* Binary plan file with a header (magic, version, grid, variant set, device
  * name, SM count) and an FNV-1a checksum of the body.  rg_plan_load checks
  * the header against `ctx`'s device (ctx may be NULL to skip the device check). */
@@ -235,21 +252,33 @@ int rg_plan_load(const char* path, const rg_ctx* ctx, rg_plan** out);
 int rg_surface_stats(const rg_grid* grid, const int64_t* t_ns, double* tflops_out,
                      double rough_out[5], double* mean_out);
 
-/* ---- grouped GEMM under CUDA graphs (many problems, one persistent launch) ----
- * A group runs a list of independent NN GEMMs with one tile shape in one
- * persistent launch over all SMs: the launch's work units are the
- * concatenation of every problem's output tiles.  Each problem has its own
- * sizes, operands, leading dimensions, beta and padded launch extents
- * (pm, pn, pk as in rg_gemm; 0 = no padding); split-K is not used.  Problems of
- * one call must not write overlapping parts of C unless ordered by beta-free
- * semantics (their tiles run concurrently).
- * rg_group_create allocates, per group, kGroupSlots = 4 slots of work lists
- * (pinned host + device, for max_items problems each) and instantiates one CUDA
- * graph per slot: [copy the host list to the device list, grouped kernel].
- * rg_gemm_grouped fills the next slot (waiting first until that slot's replay
- * from 4 calls ago has finished), then replays its graph on `stream`;
+/* ---- grouped GEMM under CUDA graphs (many problems, one persistent launch per kernel family) ----
+ * A group runs a list of independent NN GEMMs.  Each problem names the kernel
+ * variant the autotuner chose for it: a 1-CTA tile with in-kernel split-K
+ * (S = 1/2/4/8) or a cta_group::2 pair tile with split-K; a stream-K variant
+ * runs as its tile with split 1; variant = -1 means the group's tile, split 1.
+ * The problems are sorted into eight kernel families (the six 1-CTA tiles, the
+ * two cta_group::2 tiles); each family present becomes one persistent launch
+ * over all SMs whose work units are the concatenation of its problems'
+ * (tile, K split) units.  Each problem has its own sizes, operands, leading
+ * dimensions, beta and padded launch extents (pm, pn, pk as in rg_gemm;
+ * 0 = no padding).  The split-K partials and tickets live in a workspace the
+ * group owns (workspace_bytes, at least 1 MiB); when a family's problems need
+ * more than it holds at once, the family runs as several launches in turn.
+ * The launches of one call run one after another on `stream`; problems of one
+ * call must not write overlapping parts of C (they may run concurrently).
+ * A result is bitwise that of rg_gemm with the same variant (same split
+ * boundaries and summation order), whatever else the call contains.
+ * rg_group_create allocates the workspace and tickets.  A family's first use
+ * allocates kGroupSlots = 4 slots of work lists (pinned host + device, for
+ * max_items problems each) and instantiates one CUDA graph per slot:
+ * [copy the host list to the device list, grouped kernel].  rg_gemm_grouped
+ * fills the next slot of each family it uses (waiting first until that slot's
+ * replay from 4 launches ago has finished), then replays its graph on `stream`;
  * the call returns without waiting for the GEMMs.  Operand conventions and
- * alignment are those of rg_gemm; K == 0 problems are rejected. */
+ * alignment are those of rg_gemm; every problem is checked before anything is
+ * enqueued (RG_ERR_SHAPE for one whose partials alone exceed the workspace);
+ * K == 0 problems are rejected.  One group serves one stream at a time. */
 typedef struct {
   int64_t M, N, K;
   const void* A;
@@ -260,38 +289,52 @@ typedef struct {
   int64_t ldc;
   int64_t pm, pn, pk;
   int32_t beta;
-  int32_t reserved;
+  int32_t variant;            /* kernel variant, or -1 for the group's tile with split 1 */
 } rg_group_problem;
 typedef struct rg_group rg_group;
-int rg_group_create(rg_ctx* ctx, int32_t tile, int32_t max_items, rg_group** out);
+int rg_group_create(rg_ctx* ctx, int32_t tile, int32_t max_items, int64_t workspace_bytes, rg_group** out);
 void rg_group_destroy(rg_group* group);
 int rg_gemm_grouped(rg_group* group, const rg_group_problem* problems, int32_t n, void* stream);
 
-/* ---- serving: continuous batching over the grouped GEMM ----
- * rg_serve runs one trace of requests on the calling thread and returns when
- * every request has finished or been rejected.  Requests are admitted in
- * arrival order once arrived and once their operand bytes (2MK + 2KN + 4MN)
- * fit under hbm_budget_bytes next to the admitted, unfinished requests; one
- * that can never fit is rejected with RG_ERR_ADMISSION in its result.  Each
- * request goes through rg_plan_lookup (plan may be NULL): a single-leaf cell
- * lends its tile shape (the tile of its autotuned variant) and its padded
- * launch extents; a split cell, or any request without a plan, runs as-is on
- * opts->tile.  Whenever one of max_inflight slots is free, up to max_batch
- * admitted requests form one batch: one grouped launch per tile shape among
- * them (rg_gemm_grouped, CUDA graph replay) on that slot's stream, so
- * batches formed while others run overlap them on the device; finished batches
- * release budget and admit waiting requests.  A request with C == NULL gets its
- * output (ldc = N) from an arena of hbm_budget_bytes allocated for the run and
- * released at completion (its values are then gone: for load tests).  Times in
- * results are nanoseconds from the start of the run on the host's steady clock;
- * arrival_ns must be non-decreasing.  A, B and (non-NULL) C are device memory
- * the caller keeps valid for the whole call. */
+/* ---- serving: continuous batching over the grouped GEMM (the benchmark spec serving form) ----
+ * One engine serves GEMM requests of arbitrary shape with operands resident in
+ * device memory.  Requests are admitted in arrival order once arrived and once
+ * their operand bytes (2MK + 2KN + 4MN) fit under hbm_budget_bytes next to the
+ * admitted, unfinished requests; one that can never fit is rejected with
+ * RG_ERR_ADMISSION in its result.  Each request goes through rg_plan_lookup
+ * (plan may be NULL) and becomes its plan cell's leaves (Sec. 7.1): sub-boxes
+ * of the problem, each with the variant the autotuner chose for it (tile,
+ * split factor, cta_group::2; a stream-K choice runs as its tile, split 1),
+ * its padded launch extents, beta and phase; without a plan a request is one
+ * leaf on opts->tile.  Whenever one of max_inflight slots is free, up to
+ * max_batch admitted requests form one batch on that slot's stream: for each
+ * phase in order, one rg_gemm_grouped call over that phase's leaves of the
+ * whole batch, so batches formed while others run overlap them on the device;
+ * finished batches release budget and admit waiting requests.  A request's
+ * result is bitwise the same alone and in any mix.  A request with C == NULL
+ * gets its output (ldc = N) from an arena of hbm_budget_bytes allocated by the
+ * engine and released when it stops (its values are then gone: for load
+ * tests).  Times in results are nanoseconds on the host's steady clock from
+ * the engine's start.  A, B and (non-NULL) C are device memory the caller keeps
+ * valid until the request has finished.
+ *
+ * rg_serve replays a trace on the calling thread and returns when every
+ * request has finished or been rejected; arrival_ns (non-decreasing) are the
+ * trace's arrival times.  The online form runs the same engine on a worker
+ * thread: rg_serve_start creates it, rg_serve_submit enqueues one request (its
+ * arrival is the submission; arrival_ns is ignored) and returns its id (0, 1,
+ * ... in submission order), rg_serve_poll reports without blocking whether a
+ * request has finished (done = 1 and its result), rg_serve_wait blocks until it
+ * has, and rg_serve_stop waits for every submitted request, stops the worker,
+ * frees the engine and fills the statistics.  Submit, poll and wait may be
+ * called from any thread; a server uses its context's device on its own
+ * streams.  A CUDA failure stops the worker; later calls return its status. */
 typedef struct {
   int64_t hbm_budget_bytes;   /* default 64 GiB */
-  int32_t max_batch;          /* requests per grouped launch; default 64 */
-  int32_t max_inflight;       /* grouped launches on the GPU at once, 1..16; default 2 */
-  int32_t tile;               /* tile for requests the plan does not route; default RG_TILE_128x128 */
-  int32_t reserved;
+  int32_t max_batch;          /* requests per batch; default 64 */
+  int32_t max_inflight;       /* batches on the GPU at once, 1..16; default 2 */
+  int32_t tile;               /* tile for requests without a plan; default RG_TILE_128x128 */
+  int32_t workspace_mib;      /* split-K workspace of each in-flight slot, MiB; default 256 */
 } rg_serve_opts;
 typedef struct {
   int64_t M, N, K;
@@ -305,9 +348,10 @@ typedef struct {
 } rg_serve_request;
 typedef struct {
   int64_t admitted_ns, launched_ns, done_ns;
-  int32_t batch;              /* index of the grouped launch that ran it, -1 if none */
-  int32_t status;             /* RG_OK; RG_ERR_ADMISSION (never fits the budget); or, from the checks of
-                                 rg_gemm made at admission, RG_ERR_INVALID / RG_ERR_ALIGN / RG_ERR_SHAPE */
+  int32_t batch;              /* index of the batch that ran it, -1 if none */
+  int32_t status;             /* RG_OK; RG_ERR_ADMISSION (never fits the budget); RG_ERR_SHAPE (beyond the
+                                 plan grid); or, from the checks of rg_gemm made at admission,
+                                 RG_ERR_INVALID / RG_ERR_ALIGN / RG_ERR_SHAPE */
 } rg_serve_result;
 typedef struct {
   int64_t requests, batches, admission_stalls;
@@ -317,6 +361,12 @@ typedef struct {
 void rg_serve_opts_default(rg_serve_opts* opts);
 int rg_serve(rg_ctx* ctx, const rg_plan* plan, const rg_serve_opts* opts, const rg_serve_request* requests,
              int32_t n, rg_serve_result* results, rg_serve_stats* stats);
+typedef struct rg_server rg_server;
+int rg_serve_start(rg_ctx* ctx, const rg_plan* plan, const rg_serve_opts* opts, rg_server** out);
+int rg_serve_submit(rg_server* server, const rg_serve_request* request, int64_t* id_out);
+int rg_serve_poll(rg_server* server, int64_t id, rg_serve_result* result, int32_t* done);
+int rg_serve_wait(rg_server* server, int64_t id, rg_serve_result* result);
+int rg_serve_stop(rg_server* server, rg_serve_stats* stats);
 
 /* ---- FP8 e4m3 with FP32 scales per 128 x 128 block (precision variant of the GEMM) ----
  * rg_fp8_quantize: X (rows x cols FP32, ldx) -> Q (e4m3 bytes, ldq) and scales
@@ -360,16 +410,22 @@ int rg_landscape(const rg_grid* grid, int32_t mode, double p_tflops, int32_t c_u
  * level = min(T, S).  out = {tau, rho}, bands = {T, S, L}. */
 int rg_kol(double mean_a, double mean_o, double r_a, double r_o, double out[2], int32_t bands[3]);
 
-/* ---- sweep (Sec. 3, Sec. 5.4) ----
+/* ---- sweep (Sec. 3, Sec. 5.4; surface and roughness, Sec. 2 and Sec. 8.6) ----
  * Times every (variant, cell) pair: for each, `warmup` untimed launches, a
  * short device spin, then `reps` launches between two CUDA events;
  * t_ns_out[v][cell] = round(elapsed / reps) in ns.  Operands of cell (M, N, K)
  * are the contiguous prefixes A[0 : M*K] (lda = K) and B[0 : K*N] (ldb = N);
  * C must hold max M * max N floats.  If plan != NULL the single timed item per
- * cell is the plan's execution (n_variants must be 1, variant ids ignored). */
+ * cell is the plan's execution (n_variants must be 1, variant ids ignored).
+ * Besides the times it returns, per timed row v, the throughput surface
+ * tflops_out[v][cell] and stats_out[v][6] = {R_M, R_N, R_K, R_3D, R_N on the
+ * largest-K slice, mean TFLOP/s}, exactly as rg_surface_stats computes them
+ * from t_ns_out (correctly rounded sums).  A row with cells the pruning left
+ * unmeasured has TFLOP/s 0 there and NaN statistics.  Either pointer may be
+ * NULL.  Synchronises; returns RG_ERR_TIMEOUT if a kernel gave up a wait. */
 int rg_sweep(rg_ctx* ctx, const rg_grid* grid, int32_t n_variants, const int32_t* variant_ids,
              const rg_plan* plan, const void* A, const void* B, float* C,
-             const rg_sweep_opts* opts, int64_t* t_ns_out, void* stream);
+             const rg_sweep_opts* opts, int64_t* t_ns_out, double* tflops_out, double* stats_out, void* stream);
 
 /* ---- four-surface decomposition (Sec. 4, Figs. 5-6, Table 3) ----
  * The memory twin of a tile runs the tile's GEMM kernel (split 1, beta 0) with
@@ -419,13 +475,27 @@ int rg_decompose(const rg_grid* grid, const int64_t* t_gemm_ns, const int64_t* t
  *     contents; each call clears the tickets and error word it uses (an async
  *     memset on `stream`).  Calls whose work overlaps on the GPU (other streams,
  *     other threads) race on the scratch: order them.
- *   - Calls no cudaMalloc, cudaFree or other allocating routine.  A bounded
- *     wait that expires is recorded only in the scratch's error word; the
- *     kernel still returns. */
+ *   - Calls no cudaMalloc, cudaFree or other allocating routine.
+ *   - RG_OK means the launch was enqueued, not that it finished.  A bounded
+ *     wait that expires inside the kernel (which then returns with C partly
+ *     written) is recorded in the scratch's error word; rg_noalloc_check reads
+ *     it.  The next rg_gemm_noalloc call clears that word, so check before it.
+ *   - With the tiles of this library the ticket limit never binds before the
+ *     partial-byte limit (a launch whose partials fit has at most 256 tiles);
+ *     it guards the array's bounds. */
 #define RG_NOALLOC_PARTIAL_BYTES ((int64_t)16 << 20)
 #define RG_NOALLOC_MAX_TILES 4096
 int rg_gemm_noalloc(int64_t M, int64_t N, int64_t K, const void* A, int64_t lda, const void* B, int64_t ldb,
                     float* C, int64_t ldc, int32_t variant, int32_t beta, void* stream);
+/* The status of the rg_gemm_noalloc work enqueued so far on the calling thread's
+ * current device: synchronises `stream`, then reads the scratch array's error
+ * word (a device-to-host copy; nothing is allocated).  RG_OK if no bounded wait
+ * expired (also when no rg_gemm_noalloc call has run on this device yet);
+ * RG_ERR_TIMEOUT if one did, in which case the error word and every ticket are
+ * cleared (synchronously) so the next call starts clean; RG_ERR_CUDA if a CUDA
+ * call fails.  Like rg_gemm_noalloc, it races with calls still running on other
+ * streams.  The paper has no counterpart to it. */
+int rg_noalloc_check(void* stream);
 
 #ifdef __cplusplus
 }

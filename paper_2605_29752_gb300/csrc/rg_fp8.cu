@@ -304,7 +304,6 @@ __global__ void __launch_bounds__(256) quantize_kernel(const float* __restrict__
 int fp8_make_map(CUtensorMap* m, CUtensorMapDataType dt, const void* base, uint64_t inner, uint64_t outer,
                  uint64_t row_bytes, uint32_t box_inner, uint32_t box_outer);
 cudaError_t fp8_launch_pdl(const void* fn, dim3 grid, int threads, int smem, cudaStream_t st, void** params);
-int ctx_fp8_info(rg_ctx* ctx, int32_t** err, long long* timeout, int* sms);
 
 }  // namespace rg
 
@@ -341,11 +340,13 @@ extern "C" int rg_gemm_fp8(rg_ctx* ctx, int64_t M, int64_t N, int64_t K, const u
       (reinterpret_cast<uintptr_t>(C) & 15) || (lda % 16) || (ldb % 16) || (ldc % 4))
     return rg::fail(RG_ERR_ALIGN, "rg_gemm_fp8: 16-byte aligned operands, lda and ldb multiples of 16, ldc of 4");
   if (M > (1 << 30) || N > (1 << 30) || K > (1 << 30)) return rg::fail(RG_ERR_SHAPE, "rg_gemm_fp8: size beyond 2^30");
-  int32_t* err = nullptr;
-  long long timeout = 0;
-  int sms = 0;
-  int rc = rg::ctx_fp8_info(ctx, &err, &timeout, &sms);
+  rg::Fp8CtxInfo info{};
+  int rc = rg::ctx_fp8_info(ctx, &info);
   if (rc != RG_OK) return rc;
+  int32_t* err = info.err;
+  const long long timeout = info.timeout;
+  const int sms = info.sms;
+  rg::ctx_count_launches(ctx, 1);
   CUtensorMap a, b, c;
   rc = rg::fp8_make_map(&a, CU_TENSOR_MAP_DATA_TYPE_UINT8, qA, K, M, lda, BK, BM);
   if (rc == RG_OK) rc = rg::fp8_make_map(&b, CU_TENSOR_MAP_DATA_TYPE_UINT8, qB, N, K, ldb, 128, BK);
@@ -410,11 +411,12 @@ extern "C" int rg_sweep_fp8(rg_ctx* ctx, const rg_grid* grid, const uint8_t* qA,
     uint64_t s = o.seed;
     for (size_t i = order.size() - 1; i > 0; --i) std::swap(order[i], order[splitmix_next_fp8(s) % (i + 1)]);
   }
-  int32_t* err = nullptr;
-  long long timeout = 0;
-  int sms = 0;
-  int rc = rg::ctx_fp8_info(ctx, &err, &timeout, &sms);
+  rg::Fp8CtxInfo info{};
+  int rc = rg::ctx_fp8_info(ctx, &info);
   if (rc != RG_OK) return rc;
+  int32_t* err = info.err;
+  const long long timeout = info.timeout;
+  const int sms = info.sms;
   if (cudaFuncSetAttribute(reinterpret_cast<const void*>(gemm_fp8_kernel), cudaFuncAttributeMaxDynamicSharedMemorySize,
                            SMEM_BYTES) != cudaSuccess)
     return rg::fail(RG_ERR_CUDA, "rg_sweep_fp8: shared-memory attribute");

@@ -147,6 +147,8 @@ struct Unit {
   int M, N;       // logical output extents of the problem
   int beta;
   int tile, ntiles;  // tile id / tile count of the problem (split-K workspace and tickets)
+  int ws_row0 = 0;   // first workspace row of the problem's partials (grouped launches)
+  int tk0 = 0;       // first ticket of the problem (grouped launches)
 };
 
 // Tile order: the tile grid is cut into column panels `panel` tiles wide and
@@ -192,7 +194,6 @@ __device__ __forceinline__ Unit split_unit(const CUtensorMap* a, const CUtensorM
 // One problem whose tensor maps are kernel parameters (rg_gemm).
 struct SingleSched {
   static constexpr bool kMapsInGlobal = false;
-  static constexpr int kMulticast = 0;
   static constexpr bool kMemOnly = false;
   static constexpr bool k2Sm = false;
   static constexpr int rank = 0;
@@ -235,20 +236,24 @@ struct MemTwinSched : SingleSched {
 // directly; one split over several CTAs is summed by its last arriving segment
 // in the fixed order of the segments' K ranges (through the split-K workspace,
 // slot = segment * ntiles + tile).  So no wave is left partly idle.
+// TWO_SM: the same schedule over 2-CTA clusters and 256-row pair tiles (G =
+// clusters, tile = pair tile); each CTA of a cluster computes, publishes and
+// reduces its own 128 rows, as in the cta_group::2 split-K form (tiles_m counts
+// 128-row tiles and is even).
+template <bool TWO_SM>
 struct StreamKSched {
   static constexpr bool kMapsInGlobal = false;
-  static constexpr int kMulticast = 0;
   static constexpr bool kMemOnly = false;
-  static constexpr bool k2Sm = false;
-  static constexpr int rank = 0;
+  static constexpr bool k2Sm = TWO_SM;
   const CUtensorMap* a;
   const CUtensorMap* b;
   const CUtensorMap* c;
   const CUtensorMap* w;
   int tiles_m, tiles_n, kblocks, M, N, beta;
-  int tail = 0;      // CTAs sharing the tail tiles (from the launcher)
+  int tail = 0;      // CTAs (clusters) sharing the tail tiles (from the launcher)
   int dp_tiles = 0;  // tiles run whole (from the launcher)
   int panel = 1 << 30;
+  int rank = 0;
   long long iters = 0, begin = 0, end = 0;
   int G = 1, g = 0, T = 0, n_dp = 0, t0 = 0, n_sk = 0;
   __device__ __forceinline__ void prefetch() const {
@@ -265,9 +270,16 @@ struct StreamKSched {
     return h;
   }
   __device__ __forceinline__ void init() {
-    G = static_cast<int>(gridDim.x);
-    g = static_cast<int>(blockIdx.x);
-    T = tiles_m * tiles_n;
+    if constexpr (TWO_SM) {
+      rank = static_cast<int>(cluster_ctarank());
+      G = static_cast<int>(gridDim.x) / 2;
+      g = static_cast<int>(blockIdx.x) / 2;
+      T = (tiles_m / 2) * tiles_n;
+    } else {
+      G = static_cast<int>(gridDim.x);
+      g = static_cast<int>(blockIdx.x);
+      T = tiles_m * tiles_n;
+    }
     n_dp = g < dp_tiles ? (dp_tiles - 1 - g) / G + 1 : 0;
     iters = static_cast<long long>(T - dp_tiles) * kblocks;
     if (tail > 0 && g < tail && iters > 0) {
@@ -289,7 +301,6 @@ struct StreamKSched {
     x.M = M;
     x.N = N;
     x.beta = beta;
-    x.ntiles = T;
     if (i < n_dp) {  // a whole tile of the data-parallel waves
       x.tile = g + i * G;
       x.kb0 = 0;
@@ -309,35 +320,39 @@ struct StreamKSched {
       x.splits = last - first + 1;
       x.s = g - first;
     }
-    tile_coords(x.tile, tiles_m, tiles_n, panel, x.tm, x.tn);
+    if constexpr (TWO_SM) {
+      int pr, pc;
+      tile_coords(x.tile, tiles_m / 2, tiles_n, panel, pr, pc);
+      x.tm = 2 * pr + rank;
+      x.tn = pc;
+      x.tile = x.tm * tiles_n + x.tn;
+      x.ntiles = tiles_m * tiles_n;
+    } else {
+      tile_coords(x.tile, tiles_m, tiles_n, panel, x.tm, x.tn);
+      x.ntiles = T;
+    }
     return x;
   }
 };
 
-// Pairs of CTAs (2-CTA clusters) on neighbouring output tiles that share one
-// operand: MODE 1 pairs tiles (2p, n) and (2p+1, n), which read the same B
-// tile; MODE 2 pairs tiles (m, 2p) and (m, 2p+1), which read the same A tile.
-// Each CTA of the pair loads half of the shared tile (half of its rows) and
-// multicasts it to both, so the pair reads that operand from L2 once.  A CTA
-// whose tile falls outside the problem still loads and computes (zero-filled
-// reads) so that its partner's pipeline is fed; its stores are dropped.
-//
-// TWO_SM (MODE 1): the same pairing of 128-row tiles along M, run as one
-// tcgen05 cta_group::2 unit instead: no multicast; each CTA loads its own 128
-// rows of A and half of the B tile's columns, the even CTA issues the MMAs.
-template <int MODE, bool TWO_SM = false>
-struct PairSched {
+// cta_group::2: 2-CTA clusters, each cluster one 256-row output tile run as a
+// single tcgen05 MMA unit.  Tile (m, n) of 128-row tiles pairs (2p, n) with
+// (2p+1, n): CTA rank r of cluster p computes 128-row tile 2p + r, loads its own
+// 128 rows of A and its half (BN / 2 columns) of the B tile into its own shared
+// memory, and the even CTA issues the MMAs for both.  A CTA whose rows fall
+// outside the problem still loads (zero-filled reads) so that the pair's MMAs
+// are fed; its stores are dropped.  Units are (pair tile, K split).
+struct TwoSmSched {
   static constexpr bool kMapsInGlobal = false;
-  static constexpr int kMulticast = TWO_SM ? 0 : MODE;
   static constexpr bool kMemOnly = false;
-  static constexpr bool k2Sm = TWO_SM;
+  static constexpr bool k2Sm = true;
   const CUtensorMap* a;
   const CUtensorMap* b;
   const CUtensorMap* c;
   const CUtensorMap* w;
-  int tiles_m, tiles_n, kblocks, M, N, beta;
-  int rank = 0, cid = 0, ncl = 1, pairs = 0, pn_count = 1;
-  int splits = 1;  // TWO_SM: K splits per pair tile (units = pairs x splits)
+  int tiles_m, tiles_n, kblocks, M, N, beta;  // tiles_m counts 128-row tiles
+  int rank = 0, cid = 0, ncl = 1, pairs = 0;
+  int splits = 1;
   int panel = 1 << 30;
   __device__ __forceinline__ void prefetch() const {
     prefetch_tmap(a);
@@ -348,8 +363,7 @@ struct PairSched {
     rank = static_cast<int>(cluster_ctarank());
     cid = static_cast<int>(blockIdx.x) / 2;
     ncl = static_cast<int>(gridDim.x) / 2;
-    pn_count = MODE == 1 ? tiles_n : (tiles_n + 1) / 2;
-    pairs = (MODE == 1 ? (tiles_m + 1) / 2 : tiles_m) * pn_count;
+    pairs = ((tiles_m + 1) / 2) * tiles_n;
   }
   __device__ __forceinline__ int count() const {
     const int units = pairs * splits;
@@ -363,17 +377,10 @@ struct PairSched {
     x.b = b;
     x.c = c;
     x.w = w;
-    // the pair grid: (tiles_m + 1) / 2 x tiles_n pairs (MODE 1) or tiles_m x pn_count pairs (MODE 2)
     int pr, pc;
-    if (MODE == 1) {
-      tile_coords(p, (tiles_m + 1) / 2, pn_count, panel, pr, pc);
-      x.tm = 2 * pr + rank;
-      x.tn = pc;
-    } else {
-      tile_coords(p, tiles_m, pn_count, panel > 1 ? panel / 2 : 1, pr, pc);
-      x.tm = pr;
-      x.tn = 2 * pc + rank;
-    }
+    tile_coords(p, (tiles_m + 1) / 2, tiles_n, panel, pr, pc);
+    x.tm = 2 * pr + rank;
+    x.tn = pc;
     x.s = u % splits;
     x.splits = splits;
     x.kb0 = splits == 1 ? 0 : x.s * kblocks / splits;
@@ -388,52 +395,87 @@ struct PairSched {
 };
 
 // Many problems in one launch (rg_gemm_grouped): a device-resident work list
-// whose header gives the item count and the total tile count; the units are the
-// concatenation of every item's tiles (item i owns units [tile_start, tile_start
-// + tiles_m * tiles_n)).  Each item carries its own tensor maps (in global
-// memory), launch extents and beta; no split-K.
+// whose header gives the item count and the total unit count; the units are the
+// concatenation of every item's (tile, K split) units (item i owns units
+// [unit_start, unit_start + tiles * splits)).  Each item carries its own tensor
+// maps (in global memory), launch extents, beta, split factor and the offsets of
+// its split-K partials and tickets in the launch's workspace.  TWO_SM: units are
+// (256-row pair tile, split) and every 2-CTA cluster runs one at a time as a
+// tcgen05 cta_group::2 unit (tiles_m counts 128-row tiles).
 // Work-list records keep CUtensorMap's 128-byte alignment: a 128-byte header,
 // then 512-byte items (three maps and the sizes).
 struct alignas(128) GroupItem {
   CUtensorMap a, b, c;
   int32_t M, N, beta, tiles_m;
-  int32_t tiles_n, kblocks, tile_start, reserved;
+  int32_t tiles_n, kblocks, unit_start, splits;
+  int32_t ws_row0, tk0, reserved[2];
 };
 struct alignas(128) GroupHeader {
   int32_t n_items;
-  int32_t total_tiles;
+  int32_t total_units;
   int32_t reserved[30];
 };
 
+template <bool TWO_SM>
 struct GroupSched {
   static constexpr bool kMapsInGlobal = true;
-  static constexpr int kMulticast = 0;
   static constexpr bool kMemOnly = false;
-  static constexpr bool k2Sm = false;
-  static constexpr int rank = 0;
+  static constexpr bool k2Sm = TWO_SM;
   const GroupHeader* h;
   const GroupItem* items;
-  int n_items, total_tiles;  // read after the grid dependency wait
+  const CUtensorMap* w;      // the launch's split-K workspace
+  int n_items = 0, total_units = 0;  // read after the grid dependency wait
+  int rank = 0, cid = 0, ncl = 1;
   __device__ __forceinline__ void prefetch() const {}
   __device__ __forceinline__ void init() {
     n_items = h->n_items;
-    total_tiles = h->total_tiles;
+    total_units = h->total_units;
+    if constexpr (TWO_SM) {
+      rank = static_cast<int>(cluster_ctarank());
+      cid = static_cast<int>(blockIdx.x) / 2;
+      ncl = static_cast<int>(gridDim.x) / 2;
+    } else {
+      cid = static_cast<int>(blockIdx.x);
+      ncl = static_cast<int>(gridDim.x);
+    }
   }
   __device__ __forceinline__ int count() const {
-    return static_cast<int>(blockIdx.x) < total_tiles
-               ? (total_tiles - 1 - static_cast<int>(blockIdx.x)) / static_cast<int>(gridDim.x) + 1
-               : 0;
+    return cid < total_units ? (total_units - 1 - cid) / ncl + 1 : 0;
   }
   __device__ __forceinline__ Unit unit(int i) const {
-    const int u = static_cast<int>(blockIdx.x) + i * static_cast<int>(gridDim.x);
-    int lo = 0, hi = n_items - 1;  // last item whose tile_start <= u
+    const int u = cid + i * ncl;
+    int lo = 0, hi = n_items - 1;  // last item whose unit_start <= u
     while (lo < hi) {
       const int mid = (lo + hi + 1) >> 1;
-      if (items[mid].tile_start <= u) lo = mid; else hi = mid - 1;
+      if (items[mid].unit_start <= u) lo = mid; else hi = mid - 1;
     }
     const GroupItem& it = items[lo];
-    return split_unit(&it.a, &it.b, &it.c, nullptr, u - it.tile_start, it.tiles_m, it.tiles_n, 1, it.kblocks, it.M,
-                      it.N, it.beta, it.tiles_n);
+    Unit x;
+    if constexpr (TWO_SM) {
+      const int v = u - it.unit_start;
+      const int p = v / it.splits;
+      x.a = &it.a;
+      x.b = &it.b;
+      x.c = &it.c;
+      x.w = w;
+      x.tm = 2 * (p / it.tiles_n) + rank;  // tiles_m (128-row tiles) is even: pairs never overhang
+      x.tn = p % it.tiles_n;
+      x.s = v % it.splits;
+      x.splits = it.splits;
+      x.kb0 = it.splits == 1 ? 0 : x.s * it.kblocks / it.splits;
+      x.kb1 = it.splits == 1 ? it.kblocks : (x.s + 1) * it.kblocks / it.splits;
+      x.M = it.M;
+      x.N = it.N;
+      x.beta = it.beta;
+      x.ntiles = it.tiles_m * it.tiles_n;
+      x.tile = x.tm * it.tiles_n + x.tn;
+    } else {
+      x = split_unit(&it.a, &it.b, &it.c, w, u - it.unit_start, it.tiles_m, it.tiles_n, it.splits, it.kblocks, it.M,
+                     it.N, it.beta, it.tiles_n);
+    }
+    x.ws_row0 = it.ws_row0;
+    x.tk0 = it.tk0;
+    return x;
   }
 };
 
@@ -465,8 +507,7 @@ __device__ __forceinline__ void gemm_body(Sched& sched, float* ws, int32_t* tick
     sched.prefetch();
     for (int i = 0; i < STAGES; ++i) {
       mbar_init(full_bar(i), 1);
-      // a stage is free once every CTA that writes into it (multicast) has consumed it
-      mbar_init(empty_bar(i), Sched::kMulticast ? 2 : 1);
+      mbar_init(empty_bar(i), 1);
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(tfull_bar(b), 1);
@@ -488,7 +529,7 @@ __device__ __forceinline__ void gemm_body(Sched& sched, float* ws, int32_t* tick
   }
   tc_fence_before();
   __syncthreads();
-  if constexpr (Sched::kMulticast != 0 || P2) cluster_sync();  // the partner's barriers are initialised
+  if constexpr (P2) cluster_sync();  // the partner's barriers are initialised
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
   // Everything above overlaps the previous grid in the stream; nothing below
@@ -540,22 +581,11 @@ __device__ __forceinline__ void gemm_body(Sched& sched, float* ws, int32_t* tick
             for (int j = 0; j < BN / 128; ++j)
               tma_load_2d_pair(sb + j * (kBK * 128), w.b, fb, w.tn * BN + sched.rank * (BN / 2) + j * 64, kb * kBK);
           } else {
-          mbar_arrive_expect_tx(full_bar(stage), C::STAGE_BYTES);
-          if constexpr (Sched::kMulticast == 2) {  // A shared: this CTA's half of the rows, to both
-            tma_load_2d_multicast(sa + sched.rank * (BM / 2) * 128, w.a, full_bar(stage), kb * kBK,
-                                  w.tm * BM + sched.rank * (BM / 2), 3);
-          } else {
+            mbar_arrive_expect_tx(full_bar(stage), C::STAGE_BYTES);
             tma_load_2d(sa, w.a, full_bar(stage), kb * kBK, w.tm * BM);
-          }
 #pragma unroll
-          for (int j = 0; j < BN / 64; ++j) {
-            if constexpr (Sched::kMulticast == 1) {  // B shared: this CTA's half of the K rows, to both
-              tma_load_2d_multicast(sb + j * (kBK * 128) + sched.rank * (kBK / 2) * 128, w.b, full_bar(stage),
-                                    w.tn * BN + j * 64, kb * kBK + sched.rank * (kBK / 2), 3);
-            } else {
+            for (int j = 0; j < BN / 64; ++j)
               tma_load_2d(sb + j * (kBK * 128), w.b, full_bar(stage), w.tn * BN + j * 64, kb * kBK);
-            }
-          }
           }
           issued_mask |= 1u << stage;
           issued_ph = (issued_ph & ~(1u << stage)) | (ph << stage);
@@ -630,8 +660,6 @@ __device__ __forceinline__ void gemm_body(Sched& sched, float* ws, int32_t* tick
             }
             if constexpr (P2)
               mma_commit_pair_multicast(empty_bar(stage), 3);  // the stage is free in both CTAs
-            else if constexpr (Sched::kMulticast != 0)
-              mma_commit_multicast(empty_bar(stage), 3);  // releases the stage in both CTAs of the pair
             else
               mma_commit(empty_bar(stage));
           }
@@ -697,7 +725,7 @@ __device__ __forceinline__ void gemm_body(Sched& sched, float* ws, int32_t* tick
         // TMA store into the workspace (rows (s * ntiles + tile) * BM ..), then wait
         // for the stores, fence them against the generic proxy and take the ticket
         // of this (tile, warp) row block with an acquire-release atomic.
-        const int wrow = (s * ntiles + tile) * BM;
+        const int wrow = w.ws_row0 + (s * ntiles + tile) * BM;
 #pragma unroll 1
         for (int h = 0; h < C::HALVES; ++h)
 #pragma unroll 1
@@ -713,7 +741,7 @@ __device__ __forceinline__ void gemm_body(Sched& sched, float* ws, int32_t* tick
         __syncwarp();
         int last = 0;
         if (lane == 0) {
-          int32_t* t = tickets + static_cast<size_t>(tile) * 4 + q;
+          int32_t* t = tickets + w.tk0 + static_cast<size_t>(tile) * 4 + q;
           const int old = atom_add_acq_rel_gpu(t, 1);
           last = (old == w.splits - 1);
           if (last) *t = 0;
@@ -754,8 +782,8 @@ __device__ __forceinline__ void gemm_body(Sched& sched, float* ws, int32_t* tick
                 for (int b = 0; b < kBatch; ++b) {
                   const int tb = base + b;
                   if (tb < w.splits && tb != s) {
-                    const float* src = ws + static_cast<size_t>((tb * ntiles + tile) * BM + h * 128 + q * 32) * BN +
-                                       c * 32 + 4 * g;
+                    const float* src = ws + static_cast<size_t>(w.ws_row0 + (tb * ntiles + tile) * BM + h * 128 +
+                                                                q * 32) * BN + c * 32 + 4 * g;
 #pragma unroll
                     for (int j = 0; j < 8; ++j)
                       x[b][j] = __ldcg(reinterpret_cast<const float4*>(src + static_cast<size_t>(4 * j + rsub) * BN));
@@ -824,9 +852,9 @@ __device__ __forceinline__ void gemm_body(Sched& sched, float* ws, int32_t* tick
   }
 
   __syncthreads();
-  // no CTA of a pair exits while its partner may still multicast into it, arrive on
-  // its barriers or (cta_group::2) run MMAs on its shared memory and TMEM
-  if constexpr (Sched::kMulticast != 0 || P2) cluster_sync();
+  // no CTA of a pair exits while its partner may still arrive on its barriers or
+  // run MMAs on its shared memory and TMEM
+  if constexpr (P2) cluster_sync();
   if (warp == 1) {
     tc_fence_after();
     if constexpr (P2)
@@ -864,20 +892,23 @@ __global__ void __launch_bounds__(kThreads, 1)
     gemm_bf16_streamk_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                              const __grid_constant__ CUtensorMap tmC, const __grid_constant__ CUtensorMap tmW,
                              const GemmArgs args) {
-  StreamKSched sched{&tmA,        &tmB,   &tmC,   &tmW,      args.tiles_m, args.tiles_n, args.kblocks,
-                     args.M,      args.N, args.beta, args.splits /* CTAs sharing the tail */, args.dp_tiles};
+  StreamKSched<false> sched{&tmA,   &tmB,   &tmC,      &tmW,        args.tiles_m, args.tiles_n, args.kblocks,
+                            args.M, args.N, args.beta, args.splits /* CTAs sharing the tail */, args.dp_tiles};
   sched.panel = args.panel;
   gemm_body<BM, BN, STAGES>(sched, args.ws, args.tickets, args.err, args.timeout, args.stall, args.early);
 }
 
-template <int BM, int BN, int STAGES, int MODE>
+// cta_group::2 stream-K: whole waves of 256 x BN pair tiles on the 2-CTA clusters,
+// the remainder tiles' K iterations spread over the clusters.
+template <int BN, int STAGES>
 __global__ void __launch_bounds__(kThreads, 1)
-    gemm_bf16_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                          const __grid_constant__ CUtensorMap tmC, const __grid_constant__ CUtensorMap tmW,
-                          const GemmArgs args) {
-  PairSched<MODE> sched{&tmA, &tmB, &tmC, &tmW, args.tiles_m, args.tiles_n, args.kblocks, args.M, args.N, args.beta};
+    gemm_bf16_2sm_streamk_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                                 const __grid_constant__ CUtensorMap tmC, const __grid_constant__ CUtensorMap tmW,
+                                 const GemmArgs args) {
+  StreamKSched<true> sched{&tmA,   &tmB,   &tmC,      &tmW,        args.tiles_m, args.tiles_n, args.kblocks,
+                           args.M, args.N, args.beta, args.splits /* clusters sharing the tail */, args.dp_tiles};
   sched.panel = args.panel;
-  gemm_body<BM, BN, STAGES>(sched, args.ws, args.tickets, args.err, args.timeout, args.stall, args.early);
+  gemm_body<128, BN, STAGES>(sched, args.ws, args.tickets, args.err, args.timeout, args.stall, args.early);
 }
 
 // cta_group::2: 2-CTA clusters, each pair one 256 x BN output tile (128 rows per CTA).
@@ -886,8 +917,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     gemm_bf16_2sm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                          const __grid_constant__ CUtensorMap tmC, const __grid_constant__ CUtensorMap tmW,
                          const GemmArgs args) {
-  PairSched<1, true> sched{&tmA, &tmB, &tmC, &tmW, args.tiles_m, args.tiles_n, args.kblocks, args.M, args.N,
-                           args.beta};
+  TwoSmSched sched{&tmA, &tmB, &tmC, &tmW, args.tiles_m, args.tiles_n, args.kblocks, args.M, args.N, args.beta};
   sched.splits = args.splits;
   sched.panel = args.panel;
   gemm_body<128, BN, STAGES>(sched, args.ws, args.tickets, args.err, args.timeout, args.stall, args.early);
@@ -895,10 +925,22 @@ __global__ void __launch_bounds__(kThreads, 1)
 
 template <int BM, int BN, int STAGES>
 __global__ void __launch_bounds__(kThreads, 1)
-    gemm_bf16_grouped_kernel(const GroupHeader* __restrict__ hdr, const GroupItem* __restrict__ items, int32_t* err,
+    gemm_bf16_grouped_kernel(const GroupHeader* __restrict__ hdr, const GroupItem* __restrict__ items,
+                             const __grid_constant__ CUtensorMap tmW, float* ws, int32_t* tickets, int32_t* err,
                              long long timeout) {
-  GroupSched sched{hdr, items, 0, 0};
-  gemm_body<BM, BN, STAGES>(sched, nullptr, nullptr, err, timeout, 0, 0);
+  GroupSched<false> sched{hdr, items, &tmW};
+  gemm_body<BM, BN, STAGES>(sched, ws, tickets, err, timeout, 0, 0);
+}
+
+// The grouped launch of the cta_group::2 form: compiled with a cluster shape of
+// two CTAs, so a graph kernel node launches it as pairs without a launch attribute.
+template <int BN, int STAGES>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
+    gemm_bf16_grouped_2sm_kernel(const GroupHeader* __restrict__ hdr, const GroupItem* __restrict__ items,
+                                 const __grid_constant__ CUtensorMap tmW, float* ws, int32_t* tickets, int32_t* err,
+                                 long long timeout) {
+  GroupSched<true> sched{hdr, items, &tmW};
+  gemm_body<128, BN, STAGES>(sched, ws, tickets, err, timeout, 0, 0);
 }
 
 // Device-side spin of about `ns` nanoseconds (global timer), so that launches
@@ -919,41 +961,27 @@ using KernFn = void (*)(const CUtensorMap, const CUtensorMap, const CUtensorMap,
 struct TileKernel {
   KernFn fn;
   KernFn sk;    // stream-K instance of the same tile
-  KernFn pair;  // 2-CTA cluster instance sharing one operand by multicast
-  int pair_mode;  // 1: pairs along M share B; 2: pairs along N share A
   int bm, bn, smem;
-  KernFn mem;     // memory twin (loads and stores, no MMA)
-  KernFn two_sm;  // cta_group::2 instance (256-row tiles with BN >= 128), else null
+  KernFn mem;        // memory twin (loads and stores, no MMA)
+  KernFn two_sm;     // cta_group::2 instance (256-row tiles with BN >= 128), else null
   int smem2;
+  KernFn two_sm_sk;  // cta_group::2 stream-K instance, else null
 };
 
 // Stages of the cta_group::2 instances: 16 KB of A + BN/2 x 64 of B per stage and CTA.
 template <int BN>
 constexpr int kStages2Sm = BN == 256 ? 6 : 8;
 
-// The pair shares whichever operand tile is larger per K block (B when BN >= BM).
 template <int BM, int BN, int ST>
 TileKernel make_tile_kernel() {
-  constexpr int mode = BN >= BM ? 1 : 2;
-  TileKernel t{gemm_bf16_kernel<BM, BN, ST>, gemm_bf16_streamk_kernel<BM, BN, ST>,
-               gemm_bf16_pair_kernel<BM, BN, ST, mode>, mode, BM, BN, KCfg<BM, BN, ST>::SMEM_BYTES,
-               gemm_bf16_memtwin_kernel<BM, BN, ST>, nullptr, 0};
+  TileKernel t{gemm_bf16_kernel<BM, BN, ST>, gemm_bf16_streamk_kernel<BM, BN, ST>, BM, BN,
+               KCfg<BM, BN, ST>::SMEM_BYTES, gemm_bf16_memtwin_kernel<BM, BN, ST>, nullptr, 0, nullptr};
   if constexpr (BM == 256 && BN >= 128) {
     t.two_sm = gemm_bf16_2sm_kernel<BN, kStages2Sm<BN>>;
     t.smem2 = KCfg<128, BN, kStages2Sm<BN>, 2>::SMEM_BYTES;
+    t.two_sm_sk = gemm_bf16_2sm_streamk_kernel<BN, kStages2Sm<BN>>;
   }
   return t;
-}
-
-using GroupedFn = void (*)(const GroupHeader*, const GroupItem*, int32_t*, long long);
-
-static GroupedFn grouped_kernel(int tile) {
-  static const GroupedFn table[RG_NUM_TILES] = {
-      gemm_bf16_grouped_kernel<128, 64, 8>, gemm_bf16_grouped_kernel<128, 128, 6>,
-      gemm_bf16_grouped_kernel<128, 256, 4>, gemm_bf16_grouped_kernel<256, 64, 4>,
-      gemm_bf16_grouped_kernel<256, 128, 4>, gemm_bf16_grouped_kernel<256, 256, 3>,
-  };
-  return table[tile];
 }
 
 static const TileKernel& tile_kernel(int tile) {
@@ -962,6 +990,36 @@ static const TileKernel& tile_kernel(int tile) {
       make_tile_kernel<256, 64, 4>(),  make_tile_kernel<256, 128, 4>(), make_tile_kernel<256, 256, 3>(),
   };
   return table[tile];
+}
+
+// Grouped launches come in eight kernel families: the six 1-CTA tiles, then the
+// cta_group::2 forms of the 256x128 and 256x256 tiles.
+constexpr int kGroupFamilies = RG_NUM_TILES + 2;
+using GroupedFn = void (*)(const GroupHeader*, const GroupItem*, const CUtensorMap, float*, int32_t*, int32_t*,
+                           long long);
+static const void* grouped_kernel(int family) {
+  static const GroupedFn table[kGroupFamilies] = {
+      gemm_bf16_grouped_kernel<128, 64, 8>,  gemm_bf16_grouped_kernel<128, 128, 6>,
+      gemm_bf16_grouped_kernel<128, 256, 4>, gemm_bf16_grouped_kernel<256, 64, 4>,
+      gemm_bf16_grouped_kernel<256, 128, 4>, gemm_bf16_grouped_kernel<256, 256, 3>,
+      gemm_bf16_grouped_2sm_kernel<128, kStages2Sm<128>>, gemm_bf16_grouped_2sm_kernel<256, kStages2Sm<256>>,
+  };
+  return reinterpret_cast<const void*>(table[family]);
+}
+static int family_smem(int family) {
+  return family < RG_NUM_TILES ? tile_kernel(family).smem : tile_kernel(RG_TILE_256x128 + family - RG_NUM_TILES).smem2;
+}
+static int family_bn(int family) {
+  return family < RG_NUM_TILES ? tile_kernel(family).bn : tile_kernel(RG_TILE_256x128 + family - RG_NUM_TILES).bn;
+}
+// The family and the variant a grouped problem runs: stream-K variants run as
+// their tile with split 1 (the grouped scheduler has no stream-K form).
+static int grouped_variant(int v) {
+  if (!variant_streamk(v)) return v;
+  return variant_2sm(v) ? RG_VARIANT_2SM(variant_tile(v), 0) : RG_VARIANT(variant_tile(v), 0);
+}
+static int family_of(int v) {
+  return variant_2sm(v) ? RG_NUM_TILES + variant_tile(v) - RG_TILE_256x128 : variant_tile(v);
 }
 
 }  // namespace rg
@@ -979,6 +1037,11 @@ struct rg_ctx {
   int32_t static_operands = 0;  // rg_set_static_operands
   int64_t launches = 0;
   std::vector<cudaEvent_t> events;
+  // device staging of rg_gemm_plan_host (grown on demand)
+  void* stage_a = nullptr;
+  void* stage_b = nullptr;
+  float* stage_c = nullptr;
+  int64_t stage_a_bytes = 0, stage_b_bytes = 0, stage_c_bytes = 0;
 };
 
 namespace rg {
@@ -1071,7 +1134,6 @@ static int prepare(rg_ctx* ctx, int64_t M, int64_t N, int64_t K, const void* A, 
   if (rc != RG_OK) return rc;
   const int tile = variant_tile(variant);
   const bool sk = variant_streamk(variant);
-  const bool pair = variant_pair(variant);
   const bool two = variant_2sm(variant);
   const int splits = variant_split(variant);
   const TileKernel& tk = tile_kernel(tile);
@@ -1081,8 +1143,9 @@ static int prepare(rg_ctx* ctx, int64_t M, int64_t N, int64_t K, const void* A, 
   // workspace slots per tile: the split count, or stream-K's most segments on one tile
   int64_t slots = splits;
   SkGeometry skg{};
-  if (sk) {
-    skg = sk_geometry(tiles_m * tiles_n, kblocks, ctx->sm_count);
+  if (sk) {  // cta_group::2: the schedule runs over pair tiles and clusters
+    skg = two ? sk_geometry(tiles_m * tiles_n, kblocks, ctx->sm_count / 2)
+              : sk_geometry(tiles_m * tiles_n, kblocks, ctx->sm_count);
     slots = skg.max_pieces;
   }
   const bool uses_ws = slots > 1;
@@ -1091,12 +1154,9 @@ static int prepare(rg_ctx* ctx, int64_t M, int64_t N, int64_t K, const void* A, 
     if (need > ctx->ws_bytes || (two ? 2 : 1) * tiles_m * tiles_n * 4 > kMaxTickets)
       return fail(RG_ERR_SHAPE, "split-K workspace too small for this shape");
   }
-  // pairs load the shared operand as two half boxes (half its rows each)
-  // (cta_group::2: each CTA loads its own 128 rows of A and 64-column boxes of B)
-  const bool half_a = (pair && tk.pair_mode == 2) || two, half_b = pair && tk.pair_mode == 1;
-  rc = make_map(&L->a, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, A, K, M, lda * 2, kBK, half_a ? tk.bm / 2 : tk.bm);
-  if (rc == RG_OK)
-    rc = make_map(&L->b, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, B, N, K, ldb * 2, 64, half_b ? kBK / 2 : kBK);
+  // cta_group::2: each CTA loads its own 128 rows of A (and 64-column boxes of B)
+  rc = make_map(&L->a, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, A, K, M, lda * 2, kBK, two ? tk.bm / 2 : tk.bm);
+  if (rc == RG_OK) rc = make_map(&L->b, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, B, N, K, ldb * 2, 64, kBK);
   if (rc == RG_OK) rc = make_map(&L->c, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, C, N, M, ldc * 4, 32, 32);
   if (rc == RG_OK) {
     if (uses_ws)  // workspace rows: [slot][tile][BM], BN floats each
@@ -1106,8 +1166,8 @@ static int prepare(rg_ctx* ctx, int64_t M, int64_t N, int64_t K, const void* A, 
       L->w = L->c;  // unused without split-K
   }
   if (rc != RG_OK) return rc;
-  L->fn = sk ? tk.sk : pair ? tk.pair : two ? tk.two_sm : tk.fn;
-  L->cluster = (pair || two) ? 2 : 1;
+  L->fn = (sk && two) ? tk.two_sm_sk : sk ? tk.sk : two ? tk.two_sm : tk.fn;
+  L->cluster = two ? 2 : 1;
   L->smem = two ? tk.smem2 : tk.smem;
   L->ws_slots = slots;
   GemmArgs& g = L->args;
@@ -1131,11 +1191,10 @@ static int prepare(rg_ctx* ctx, int64_t M, int64_t N, int64_t K, const void* A, 
   g.stall = ctx->stall;
   g.early = ctx->static_operands;
   const int64_t units = tiles_m * tiles_n * splits;
-  if (two) {  // one 2-CTA cluster per (256-row tile, split), at most one CTA per SM
+  if (two && sk) {  // stream-K over 2-CTA clusters
+    L->grid = dim3(static_cast<unsigned>(2 * skg.grid));
+  } else if (two) {  // one 2-CTA cluster per (256-row tile, split), at most one CTA per SM
     L->grid = dim3(static_cast<unsigned>(2 * std::min<int64_t>(tiles_m * tiles_n * splits, ctx->sm_count / 2)));
-  } else if (pair) {  // 2-CTA clusters, one per pair of tiles, at most one CTA per SM
-    const int64_t pairs = tk.pair_mode == 1 ? ((tiles_m + 1) / 2) * tiles_n : tiles_m * ((tiles_n + 1) / 2);
-    L->grid = dim3(static_cast<unsigned>(2 * std::min<int64_t>(pairs, ctx->sm_count / 2)));
   } else {
     L->grid = dim3(static_cast<unsigned>(sk ? skg.grid : std::min<int64_t>(units, ctx->sm_count)));
   }
@@ -1167,6 +1226,8 @@ static cudaError_t launch(rg_ctx* ctx, const Launch& L, cudaStream_t st) {
   cfg.numAttrs = L.cluster > 1 ? 2 : 1;
   return cudaLaunchKernelExC(&cfg, reinterpret_cast<const void*>(L.fn), params);
 }
+
+int ctx_device(const rg_ctx* ctx) { return ctx ? ctx->device : 0; }
 
 void ctx_identity(const rg_ctx* ctx, char name[64], int32_t* sms) {
   std::memset(name, 0, 64);
@@ -1283,15 +1344,22 @@ int timed_sweep(rg_ctx* ctx, const std::vector<int64_t>& order, const rg_sweep_o
   return RG_OK;
 }
 
-// The context's error word, wait budget and SM count for kernels of other
-// translation units; counts one launch.
-int ctx_fp8_info(rg_ctx* ctx, int32_t** err, long long* timeout, int* sms) {
+// The context's error word, wait budget, SM count and split-K workspace for the
+// kernels of other translation units.
+int ctx_fp8_info(rg_ctx* ctx, Fp8CtxInfo* out) {
   if (!ctx) return fail(RG_ERR_INVALID, "null context");
-  *err = ctx->err;
-  *timeout = ctx->timeout;
-  *sms = ctx->sm_count;
-  ++ctx->launches;
+  out->err = ctx->err;
+  out->timeout = ctx->timeout;
+  out->sms = ctx->sm_count;
+  out->ws = ctx->ws;
+  out->ws_bytes = ctx->ws_bytes;
+  out->tickets = ctx->tickets;
+  out->max_tickets = kMaxTickets;
   return RG_OK;
+}
+
+void ctx_count_launches(rg_ctx* ctx, int64_t n) {
+  if (ctx) ctx->launches += n;
 }
 
 }  // namespace rg
@@ -1329,18 +1397,23 @@ extern "C" int rg_init(int device, int64_t workspace_bytes, rg_ctx** out) {
                                   tk.smem)) != cudaSuccess ||
         (e = cudaFuncSetAttribute(reinterpret_cast<const void*>(tk.sk), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   tk.smem)) != cudaSuccess ||
-        (e = cudaFuncSetAttribute(reinterpret_cast<const void*>(tk.pair), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  tk.smem)) != cudaSuccess ||
         (e = cudaFuncSetAttribute(reinterpret_cast<const void*>(tk.mem), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   tk.smem)) != cudaSuccess ||
         (tk.two_sm && (e = cudaFuncSetAttribute(reinterpret_cast<const void*>(tk.two_sm),
                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, tk.smem2)) != cudaSuccess) ||
-        (e = cudaFuncSetAttribute(reinterpret_cast<const void*>(rg::grouped_kernel(t)),
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, tk.smem)) != cudaSuccess) {
+        (tk.two_sm_sk && (e = cudaFuncSetAttribute(reinterpret_cast<const void*>(tk.two_sm_sk),
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, tk.smem2)) !=
+                             cudaSuccess)) {
       delete ctx;
       return rg::cuda_fail(e, "rg_init: shared-memory attribute");
     }
   }
+  for (int f = 0; f < rg::kGroupFamilies; ++f)
+    if ((e = cudaFuncSetAttribute(rg::grouped_kernel(f), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  rg::family_smem(f))) != cudaSuccess) {
+      delete ctx;
+      return rg::cuda_fail(e, "rg_init: shared-memory attribute (grouped)");
+    }
   if ((e = cudaMalloc(&ctx->ws, ctx->ws_bytes)) != cudaSuccess ||
       (e = cudaMalloc(&ctx->tickets, sizeof(int32_t) * rg::kMaxTickets)) != cudaSuccess ||
       (e = cudaMalloc(&ctx->err, sizeof(int32_t))) != cudaSuccess) {
@@ -1365,6 +1438,9 @@ extern "C" void rg_destroy(rg_ctx* ctx) {
   if (!ctx) return;
   cudaSetDevice(ctx->device);
   for (auto ev : ctx->events) cudaEventDestroy(ev);
+  cudaFree(ctx->stage_a);
+  cudaFree(ctx->stage_b);
+  cudaFree(ctx->stage_c);
   cudaFree(ctx->ws);
   cudaFree(ctx->tickets);
   cudaFree(ctx->err);
@@ -1444,6 +1520,51 @@ extern "C" int rg_gemm_plan(rg_ctx* ctx, const rg_plan* plan, int64_t M, int64_t
 }
 
 namespace {
+// Grow a device staging buffer to at least `bytes` (the old contents are not kept).
+int grow_stage(void** buf, int64_t* cap, int64_t bytes, cudaStream_t st) {
+  if (bytes <= *cap) return RG_OK;
+  cudaError_t e = cudaStreamSynchronize(st);  // work on the stream may still read the old buffer
+  if (e == cudaSuccess && *buf) e = cudaFree(*buf);
+  *buf = nullptr;
+  *cap = 0;
+  if (e == cudaSuccess) e = cudaMalloc(buf, static_cast<size_t>(bytes));
+  if (e != cudaSuccess) {
+    *buf = nullptr;
+    cudaGetLastError();
+    return rg::fail(RG_ERR_OOM, std::string("rg_gemm_plan_host: staging buffer: ") + cudaGetErrorString(e));
+  }
+  *cap = bytes;
+  return RG_OK;
+}
+}  // namespace
+
+extern "C" int rg_gemm_plan_host(rg_ctx* ctx, const rg_plan* plan, int64_t M, int64_t N, int64_t K, const void* A,
+                                 int64_t lda, const void* B, int64_t ldb, float* C, int64_t ldc, void* stream) {
+  rg::clear_error();
+  if (!ctx || !plan || !A || !B || !C) return rg::fail(RG_ERR_INVALID, "rg_gemm_plan_host: null argument");
+  if (M <= 0 || N <= 0 || K <= 0) return rg::fail(RG_ERR_INVALID, "rg_gemm_plan_host: sizes must be positive");
+  if (lda < K || ldb < N || ldc < N) return rg::fail(RG_ERR_INVALID, "rg_gemm_plan_host: leading dimensions");
+  if (M > (1 << 30) || N > (1 << 30) || K > (1 << 30)) return rg::fail(RG_ERR_SHAPE, "rg_gemm_plan_host: size");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  // device copies with leading dimensions rounded up to the TMA alignment
+  const int64_t dlda = (K + 7) / 8 * 8, dldb = (N + 7) / 8 * 8, dldc = (N + 3) / 4 * 4;
+  int rc = grow_stage(&ctx->stage_a, &ctx->stage_a_bytes, 2 * M * dlda, st);
+  if (rc == RG_OK) rc = grow_stage(&ctx->stage_b, &ctx->stage_b_bytes, 2 * K * dldb, st);
+  if (rc == RG_OK)
+    rc = grow_stage(reinterpret_cast<void**>(&ctx->stage_c), &ctx->stage_c_bytes, 4 * M * dldc, st);
+  if (rc != RG_OK) return rc;
+  cudaError_t e = cudaMemcpy2DAsync(ctx->stage_a, dlda * 2, A, lda * 2, K * 2, M, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpy2DAsync(ctx->stage_b, dldb * 2, B, ldb * 2, N * 2, K, cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return rg::cuda_fail(e, "rg_gemm_plan_host: copy in");
+  rc = rg_gemm_plan(ctx, plan, M, N, K, ctx->stage_a, dlda, ctx->stage_b, dldb, ctx->stage_c, dldc, stream);
+  if (rc != RG_OK) return rc;
+  e = cudaMemcpy2DAsync(C, ldc * 4, ctx->stage_c, dldc * 4, N * 4, M, cudaMemcpyDeviceToHost, st);
+  if (e != cudaSuccess) return rg::cuda_fail(e, "rg_gemm_plan_host: copy out");
+  return rg_check(ctx, stream);
+}
+
+namespace {
 uint64_t splitmix_next(uint64_t& s) {
   uint64_t z = (s += 0x9E3779B97F4A7C15ull);
   z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
@@ -1456,7 +1577,7 @@ uint64_t splitmix_next(uint64_t& s) {
 // ids and every cell runs that tile's memory twin (never pruned).
 static int sweep_impl(rg_ctx* ctx, const rg_grid* grid, int32_t n_variants, const int32_t* variant_ids,
                       const rg_plan* plan, const void* A, const void* B, float* C, const rg_sweep_opts* opts,
-                      int64_t* t_ns_out, void* stream, bool memtwin) {
+                      int64_t* t_ns_out, double* tflops_out, double* stats_out, void* stream, bool memtwin) {
   rg::clear_error();
   if (!ctx || !grid || !A || !B || !C || !t_ns_out) return rg::fail(RG_ERR_INVALID, "rg_sweep: null argument");
   if (!rg::grid_valid(*grid)) return rg::fail(RG_ERR_INVALID, "rg_sweep: invalid grid");
@@ -1502,16 +1623,15 @@ static int sweep_impl(rg_ctx* ctx, const rg_grid* grid, int32_t n_variants, cons
       int64_t M, N, K;
       dims(item, &M, &N, &K);
       if (M <= 128) return true;
+      const rg::TileShape ts = rg::tile_shape(rg::variant_tile(v));
+      const int64_t pairs = ((M + ts.bm - 1) / ts.bm) * ((N + ts.bn - 1) / ts.bn);
+      if (sk) {  // as the 1-CTA stream-K rule, over clusters
+        const int64_t clusters = ctx->sm_count / 2;
+        const rg::SkGeometry gsk = rg::sk_geometry(pairs, (K + rg::kBK - 1) / rg::kBK, clusters);
+        return pairs < clusters || gsk.tail_ctas <= pairs - gsk.dp_tiles;
+      }
       if (S == 1) return false;
-      const rg::TileShape ts = rg::tile_shape(rg::variant_tile(v));
-      const int64_t ctas = 2 * ((M + ts.bm - 1) / ts.bm) * ((N + ts.bn - 1) / ts.bn);
-      return ctas >= ctx->sm_count || (K + rg::kBK - 1) / rg::kBK < 2 * S;
-    }
-    if (rg::variant_pair(v)) {  // a pair needs a partner tile
-      int64_t M, N, K;
-      dims(item, &M, &N, &K);
-      const rg::TileShape ts = rg::tile_shape(rg::variant_tile(v));
-      return ((M + ts.bm - 1) / ts.bm) * ((N + ts.bn - 1) / ts.bn) < 2;
+      return 2 * pairs >= ctx->sm_count || (K + rg::kBK - 1) / rg::kBK < 2 * S;
     }
     if (S == 1 && !sk) return false;
     int64_t M, N, K;
@@ -1564,22 +1684,25 @@ static int sweep_impl(rg_ctx* ctx, const rg_grid* grid, int32_t n_variants, cons
   // per-launch time would measure several overlapped GEMMs.
   const int32_t saved_static = ctx->static_operands;
   ctx->static_operands = 0;
-  const int rc = rg::timed_sweep(ctx, order, o, st, t_ns_out, prep, run);
+  int rc = rg::timed_sweep(ctx, order, o, st, t_ns_out, prep, run);
   ctx->static_operands = saved_static;
   if (rc != RG_OK) return rc;
-  return rg_check(ctx, stream);
+  rc = rg_check(ctx, stream);
+  if (rc != RG_OK) return rc;
+  return rg::sweep_surfaces(grid, plan ? 1 : n_variants, t_ns_out, tflops_out, stats_out);
 }
 
 extern "C" int rg_sweep(rg_ctx* ctx, const rg_grid* grid, int32_t n_variants, const int32_t* variant_ids,
                         const rg_plan* plan, const void* A, const void* B, float* C, const rg_sweep_opts* opts,
-                        int64_t* t_ns_out, void* stream) {
-  return sweep_impl(ctx, grid, n_variants, variant_ids, plan, A, B, C, opts, t_ns_out, stream, false);
+                        int64_t* t_ns_out, double* tflops_out, double* stats_out, void* stream) {
+  return sweep_impl(ctx, grid, n_variants, variant_ids, plan, A, B, C, opts, t_ns_out, tflops_out, stats_out, stream,
+                    false);
 }
 
 extern "C" int rg_sweep_memtwin(rg_ctx* ctx, const rg_grid* grid, int32_t n_tiles, const int32_t* tile_ids,
                                 const void* A, const void* B, float* C, const rg_sweep_opts* opts, int64_t* t_ns_out,
                                 void* stream) {
-  return sweep_impl(ctx, grid, n_tiles, tile_ids, nullptr, A, B, C, opts, t_ns_out, stream, true);
+  return sweep_impl(ctx, grid, n_tiles, tile_ids, nullptr, A, B, C, opts, t_ns_out, nullptr, nullptr, stream, true);
 }
 
 extern "C" int rg_gemm_memtwin(rg_ctx* ctx, int64_t M, int64_t N, int64_t K, const void* A, int64_t lda,
@@ -1596,22 +1719,28 @@ extern "C" int rg_gemm_memtwin(rg_ctx* ctx, int64_t M, int64_t N, int64_t K, con
 
 // ------------------------------------------------------------------ grouped GEMM under CUDA graphs
 //
-// A group object owns kGroupSlots slots.  Each slot: a pinned host work list, a
-// device work list (header + items), a CUDA graph [copy host list -> device list,
-// persistent grouped kernel over all SMs] instantiated once, and an event marking
-// the slot's last replay.  A call takes the next slot, waits until that slot's
-// previous replay has finished (so its lists may be rewritten), encodes the
-// problems' tensor maps into the pinned list, sets the copy size to the used
-// part, and replays the graph on the caller's stream.  The graph's topology
-// never changes; only the list contents do.
+// A group object owns, per kernel family, kGroupSlots slots (built on the
+// family's first use).  Each slot: a pinned host work list, a device work list
+// (header + items), a CUDA graph [copy host list -> device list, persistent
+// grouped kernel over all SMs] instantiated once, and an event marking the
+// slot's last replay.  A call sorts its problems by family; for each family
+// present it fills work lists -- starting a further list whenever the next item's
+// split-K partials or tickets would not fit the group's workspace, or the list is
+// full -- and replays one graph per list on the caller's stream, so the lists of
+// one call run one after another and each may reuse the whole workspace.  The
+// graph's topology never changes; only the list contents do.
 namespace rg {
 constexpr int kGroupSlots = 4;
+constexpr int64_t kGroupMinWorkspace = 1 << 20;
 }
 
 struct rg_group {
   rg_ctx* ctx = nullptr;
   int tile = 0;
   int max_items = 0;
+  float* ws = nullptr;
+  int64_t ws_bytes = 0;
+  int32_t* tickets = nullptr;
   struct Slot {
     unsigned char* host = nullptr;  // pinned: header + items
     unsigned char* dev = nullptr;
@@ -1620,8 +1749,13 @@ struct rg_group {
     cudaGraphNode_t copy_node = nullptr;
     cudaEvent_t done = nullptr;
     bool used = false;
-  } slot[rg::kGroupSlots];
-  int next = 0;
+  };
+  struct Family {
+    Slot slot[rg::kGroupSlots];
+    int next = 0;
+    bool ready = false;
+    CUtensorMap tmW;
+  } fam[rg::kGroupFamilies];
 };
 
 namespace rg {
@@ -1630,17 +1764,21 @@ static size_t group_bytes(int n) { return sizeof(GroupHeader) + static_cast<size
 
 static void group_free(rg_group* g) {
   if (!g) return;
-  for (auto& sl : g->slot) {
-    if (sl.exec) cudaGraphExecDestroy(sl.exec);
-    if (sl.graph) cudaGraphDestroy(sl.graph);
-    if (sl.done) cudaEventDestroy(sl.done);
-    if (sl.host) cudaFreeHost(sl.host);
-    if (sl.dev) cudaFree(sl.dev);
-  }
+  for (auto& f : g->fam)
+    for (auto& sl : f.slot) {
+      if (sl.used) cudaEventSynchronize(sl.done);
+      if (sl.exec) cudaGraphExecDestroy(sl.exec);
+      if (sl.graph) cudaGraphDestroy(sl.graph);
+      if (sl.done) cudaEventDestroy(sl.done);
+      if (sl.host) cudaFreeHost(sl.host);
+      if (sl.dev) cudaFree(sl.dev);
+    }
+  cudaFree(g->ws);
+  cudaFree(g->tickets);
   delete g;
 }
 
-static int group_build_graph(rg_group* g, rg_group::Slot& sl) {
+static int group_build_graph(rg_group* g, int family, rg_group::Slot& sl) {
   cudaGraph_t graph = nullptr;
   cudaError_t e = cudaGraphCreate(&graph, 0);
   if (e != cudaSuccess) return cuda_fail(e, "rg_group: graph");
@@ -1648,17 +1786,20 @@ static int group_build_graph(rg_group* g, rg_group::Slot& sl) {
   e = cudaGraphAddMemcpyNode1D(&copy, graph, nullptr, 0, sl.dev, sl.host, group_bytes(g->max_items),
                                cudaMemcpyHostToDevice);
   if (e == cudaSuccess) {
-    const TileKernel& tk = tile_kernel(g->tile);
     const GroupHeader* hdr = reinterpret_cast<const GroupHeader*>(sl.dev);
     const GroupItem* items = reinterpret_cast<const GroupItem*>(sl.dev + sizeof(GroupHeader));
+    CUtensorMap tmW = g->fam[family].tmW;
+    float* ws = g->ws;
+    int32_t* tickets = g->tickets;
     int32_t* err = g->ctx->err;
     long long timeout = g->ctx->timeout;
-    void* params[4] = {&hdr, &items, &err, &timeout};
+    void* params[7] = {&hdr, &items, &tmW, &ws, &tickets, &err, &timeout};
+    const bool two = family >= RG_NUM_TILES;
     cudaKernelNodeParams kp = {};
-    kp.func = reinterpret_cast<void*>(grouped_kernel(g->tile));
-    kp.gridDim = dim3(static_cast<unsigned>(g->ctx->sm_count));
+    kp.func = const_cast<void*>(grouped_kernel(family));
+    kp.gridDim = dim3(static_cast<unsigned>(two ? g->ctx->sm_count / 2 * 2 : g->ctx->sm_count));
     kp.blockDim = dim3(kThreads);
-    kp.sharedMemBytes = static_cast<unsigned>(tk.smem);
+    kp.sharedMemBytes = static_cast<unsigned>(family_smem(family));
     kp.kernelParams = params;
     e = cudaGraphAddKernelNode(&kern, graph, &copy, 1, &kp);
   }
@@ -1671,93 +1812,168 @@ static int group_build_graph(rg_group* g, rg_group::Slot& sl) {
   sl.copy_node = copy;
   return RG_OK;
 }
+
+// Slots, graphs and the workspace tensor map of one family, on its first use.
+static int group_family_ready(rg_group* g, int family) {
+  rg_group::Family& f = g->fam[family];
+  if (f.ready) return RG_OK;
+  const int bn = family_bn(family);
+  int rc = make_map(&f.tmW, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, g->ws, static_cast<uint64_t>(bn),
+                    static_cast<uint64_t>(g->ws_bytes / (4 * bn)), static_cast<uint64_t>(bn) * 4, 32, 32);
+  if (rc != RG_OK) return rc;
+  const size_t bytes = group_bytes(g->max_items);
+  for (auto& sl : f.slot) {
+    cudaError_t e = cudaMallocHost(&sl.host, bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&sl.dev, bytes);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(RG_ERR_OOM, std::string("rg_gemm_grouped: work lists: ") + cudaGetErrorString(e));
+    }
+    std::memset(sl.host, 0, bytes);
+    rc = group_build_graph(g, family, sl);
+    if (rc != RG_OK) return rc;
+  }
+  f.ready = true;
+  return RG_OK;
+}
+
+// Replays the next slot of `family` with the list in `items` (count items, units units).
+static int group_flush(rg_group* g, int family, const std::vector<GroupItem>& items, int64_t units,
+                       cudaStream_t st) {
+  if (items.empty()) return RG_OK;
+  rg_group::Family& f = g->fam[family];
+  rg_group::Slot& sl = f.slot[f.next];
+  f.next = (f.next + 1) % kGroupSlots;
+  cudaError_t e;
+  if (sl.used && (e = cudaEventSynchronize(sl.done)) != cudaSuccess) return cuda_fail(e, "rg_gemm_grouped: slot");
+  auto* hdr = reinterpret_cast<GroupHeader*>(sl.host);
+  hdr->n_items = static_cast<int32_t>(items.size());
+  hdr->total_units = static_cast<int32_t>(units);
+  std::memcpy(sl.host + sizeof(GroupHeader), items.data(), items.size() * sizeof(GroupItem));
+  const int n = static_cast<int>(items.size());
+  e = cudaGraphExecMemcpyNodeSetParams1D(sl.exec, sl.copy_node, sl.dev, sl.host, group_bytes(n),
+                                         cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaGraphLaunch(sl.exec, st);
+  if (e == cudaSuccess) e = cudaEventRecord(sl.done, st);
+  if (e != cudaSuccess) return cuda_fail(e, "rg_gemm_grouped: replay");
+  sl.used = true;
+  g->ctx->launches += 1;
+  return RG_OK;
+}
 }  // namespace rg
 
-extern "C" int rg_group_create(rg_ctx* ctx, int32_t tile, int32_t max_items, rg_group** out) {
+extern "C" int rg_group_create(rg_ctx* ctx, int32_t tile, int32_t max_items, int64_t workspace_bytes,
+                               rg_group** out) {
   rg::clear_error();
-  if (!ctx || !out || tile < 0 || tile >= RG_NUM_TILES || max_items <= 0 || max_items > (1 << 20))
+  if (!ctx || !out || tile < 0 || tile >= RG_NUM_TILES || max_items <= 0 || max_items > (1 << 20) ||
+      workspace_bytes < 0)
     return rg::fail(RG_ERR_INVALID, "rg_group_create: bad argument");
+  *out = nullptr;
   auto* g = new (std::nothrow) rg_group();
   if (!g) return rg::fail(RG_ERR_OOM, "rg_group_create: host allocation");
   g->ctx = ctx;
   g->tile = tile;
   g->max_items = max_items;
-  const size_t bytes = rg::group_bytes(max_items);
-  for (auto& sl : g->slot) {
-    cudaError_t e = cudaMallocHost(&sl.host, bytes);
-    if (e == cudaSuccess) e = cudaMalloc(&sl.dev, bytes);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming);
-    if (e != cudaSuccess) {
-      rg::group_free(g);
-      cudaGetLastError();
-      return rg::fail(RG_ERR_OOM, std::string("rg_group_create: ") + cudaGetErrorString(e));
-    }
-    std::memset(sl.host, 0, bytes);
-    const int rc = rg::group_build_graph(g, sl);
-    if (rc != RG_OK) {
-      rg::group_free(g);
-      return rc;
-    }
+  g->ws_bytes = std::max<int64_t>(workspace_bytes, rg::kGroupMinWorkspace) / 1024 * 1024;
+  cudaError_t e = cudaMalloc(&g->ws, static_cast<size_t>(g->ws_bytes));
+  if (e == cudaSuccess) e = cudaMalloc(&g->tickets, sizeof(int32_t) * rg::kMaxTickets);
+  if (e == cudaSuccess) e = cudaMemset(g->tickets, 0, sizeof(int32_t) * rg::kMaxTickets);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    rg::group_free(g);
+    return rg::fail(RG_ERR_OOM, std::string("rg_group_create: ") + cudaGetErrorString(e));
   }
   *out = g;
   return RG_OK;
 }
 
-extern "C" void rg_group_destroy(rg_group* g) {
-  if (!g) return;
-  for (auto& sl : g->slot)
-    if (sl.used) cudaEventSynchronize(sl.done);
-  rg::group_free(g);
-}
+extern "C" void rg_group_destroy(rg_group* g) { rg::group_free(g); }
 
 extern "C" int rg_gemm_grouped(rg_group* g, const rg_group_problem* probs, int32_t n, void* stream) {
   rg::clear_error();
   if (!g || (n > 0 && !probs) || n < 0) return rg::fail(RG_ERR_INVALID, "rg_gemm_grouped: bad argument");
-  if (n > g->max_items) return rg::fail(RG_ERR_SHAPE, "rg_gemm_grouped: more problems than the group holds");
   if (n == 0) return RG_OK;
-  rg_group::Slot& sl = g->slot[g->next];
-  g->next = (g->next + 1) % rg::kGroupSlots;
-  cudaError_t e;
-  if (sl.used && (e = cudaEventSynchronize(sl.done)) != cudaSuccess) return rg::cuda_fail(e, "rg_gemm_grouped: slot");
-  auto* hdr = reinterpret_cast<rg::GroupHeader*>(sl.host);
-  auto* items = reinterpret_cast<rg::GroupItem*>(sl.host + sizeof(rg::GroupHeader));
-  const rg::TileShape ts = rg::tile_shape(g->tile);
-  int64_t tiles = 0;
-  int32_t count = 0;
-  for (int32_t i = 0; i < n; ++i) {
-    const rg_group_problem& p = probs[i];
+  // A view of the context whose split-K workspace and tickets are the group's.
+  rg_ctx view;
+  view.device = g->ctx->device;
+  view.sm_count = g->ctx->sm_count;
+  view.ws = g->ws;
+  view.ws_bytes = g->ws_bytes;
+  view.tickets = g->tickets;
+  view.err = g->ctx->err;
+  view.timeout = g->ctx->timeout;
+  struct Prepared {
+    int family;
     rg::Launch L;
-    const int rc = rg::prepare(g->ctx, p.M, p.N, p.K, p.A, p.lda, p.B, p.ldb, p.C, p.ldc, RG_VARIANT(g->tile, 0),
-                               p.beta, p.pm, p.pn, p.pk, &L);
+  };
+  std::vector<Prepared> prep;
+  prep.reserve(static_cast<size_t>(n));
+  for (int32_t i = 0; i < n; ++i) {  // every problem is checked before anything is enqueued
+    const rg_group_problem& p = probs[i];
+    if (p.variant >= RG_NUM_VARIANTS) return rg::fail(RG_ERR_INVALID, "rg_gemm_grouped: variant id out of range");
+    const int v = p.variant < 0 ? RG_VARIANT(g->tile, 0) : rg::grouped_variant(p.variant);
+    Prepared q;
+    q.family = rg::family_of(v);
+    const int rc = rg::prepare(&view, p.M, p.N, p.K, p.A, p.lda, p.B, p.ldb, p.C, p.ldc, v, p.beta, p.pm, p.pn, p.pk,
+                               &q.L);
     if (rc != RG_OK) return rc;
-    if (L.noop) continue;
-    if (L.zero_only) return rg::fail(RG_ERR_INVALID, "rg_gemm_grouped: K == 0 problems are not grouped");
-    rg::GroupItem& it = items[count++];
-    it.a = L.a;
-    it.b = L.b;
-    it.c = L.c;
-    it.M = L.args.M;
-    it.N = L.args.N;
-    it.beta = L.args.beta;
-    it.tiles_m = L.args.tiles_m;
-    it.tiles_n = L.args.tiles_n;
-    it.kblocks = L.args.kblocks;
-    it.tile_start = static_cast<int32_t>(tiles);
-    it.reserved = 0;
-    tiles += static_cast<int64_t>(L.args.tiles_m) * L.args.tiles_n;
-    if (tiles > (1LL << 30)) return rg::fail(RG_ERR_SHAPE, "rg_gemm_grouped: too many tiles");
+    if (q.L.noop) continue;
+    if (q.L.zero_only) return rg::fail(RG_ERR_INVALID, "rg_gemm_grouped: K == 0 problems are not grouped");
+    prep.push_back(q);
   }
-  (void)ts;
-  if (count == 0) return RG_OK;
-  hdr->n_items = count;
-  hdr->total_tiles = static_cast<int32_t>(tiles);
-  e = cudaGraphExecMemcpyNodeSetParams1D(sl.exec, sl.copy_node, sl.dev, sl.host, rg::group_bytes(count),
-                                         cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaGraphLaunch(sl.exec, static_cast<cudaStream_t>(stream));
-  if (e == cudaSuccess) e = cudaEventRecord(sl.done, static_cast<cudaStream_t>(stream));
-  if (e != cudaSuccess) return rg::cuda_fail(e, "rg_gemm_grouped: replay");
-  sl.used = true;
-  g->ctx->launches += 1;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  std::vector<rg::GroupItem> items;
+  items.reserve(static_cast<size_t>(g->max_items));
+  for (int f = 0; f < rg::kGroupFamilies; ++f) {
+    bool any = false;
+    for (const auto& q : prep) any = any || q.family == f;
+    if (!any) continue;
+    int rc = rg::group_family_ready(g, f);
+    if (rc != RG_OK) return rc;
+    const bool two = f >= RG_NUM_TILES;
+    const int bm = two ? 128 : rg::tile_kernel(f).bm;
+    const int64_t ws_rows = g->ws_bytes / (4 * rg::family_bn(f));
+    items.clear();
+    int64_t units = 0, rows = 0, tks = 0;
+    for (const auto& q : prep) {
+      if (q.family != f) continue;
+      const rg::GemmArgs& a = q.L.args;
+      const int64_t ntiles = static_cast<int64_t>(a.tiles_m) * a.tiles_n;
+      const int64_t my_units = (two ? ntiles / 2 : ntiles) * a.splits;
+      const int64_t my_rows = a.splits > 1 ? a.splits * ntiles * bm : 0;
+      const int64_t my_tks = a.splits > 1 ? 4 * ntiles : 0;
+      if (my_rows > ws_rows || my_tks > rg::kMaxTickets)
+        return rg::fail(RG_ERR_SHAPE, "rg_gemm_grouped: a problem's split-K partials exceed the group's workspace");
+      if (static_cast<int>(items.size()) == g->max_items || rows + my_rows > ws_rows || tks + my_tks > rg::kMaxTickets ||
+          units + my_units > (1LL << 30)) {
+        if ((rc = rg::group_flush(g, f, items, units, st)) != RG_OK) return rc;
+        items.clear();
+        units = rows = tks = 0;
+      }
+      rg::GroupItem it;
+      std::memset(&it, 0, sizeof(it));
+      it.a = q.L.a;
+      it.b = q.L.b;
+      it.c = q.L.c;
+      it.M = a.M;
+      it.N = a.N;
+      it.beta = a.beta;
+      it.tiles_m = a.tiles_m;
+      it.tiles_n = a.tiles_n;
+      it.kblocks = a.kblocks;
+      it.unit_start = static_cast<int32_t>(units);
+      it.splits = a.splits;
+      it.ws_row0 = static_cast<int32_t>(rows);
+      it.tk0 = static_cast<int32_t>(tks);
+      items.push_back(it);
+      units += my_units;
+      rows += my_rows;
+      tks += my_tks;
+    }
+    if ((rc = rg::group_flush(g, f, items, units, st)) != RG_OK) return rc;
+  }
   return RG_OK;
 }
 
@@ -1809,12 +2025,13 @@ static int noalloc_setup(int dev, NoallocDevice** out) {
     if (rc != RG_OK) return rc;
     for (int t = 0; t < RG_NUM_TILES; ++t) {
       const TileKernel& tk = tile_kernel(t);
-      for (KernFn fn : {tk.fn, tk.sk, tk.pair}) {
+      for (KernFn fn : {tk.fn, tk.sk}) {
         e = cudaFuncSetAttribute(reinterpret_cast<const void*>(fn), cudaFuncAttributeMaxDynamicSharedMemorySize, tk.smem);
         if (e != cudaSuccess) return cuda_fail(e, "rg_gemm_noalloc: shared-memory attribute");
       }
-      if (tk.two_sm) {
-        e = cudaFuncSetAttribute(reinterpret_cast<const void*>(tk.two_sm), cudaFuncAttributeMaxDynamicSharedMemorySize,
+      for (KernFn fn : {tk.two_sm, tk.two_sm_sk}) {
+        if (!fn) continue;
+        e = cudaFuncSetAttribute(reinterpret_cast<const void*>(fn), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  tk.smem2);
         if (e != cudaSuccess) return cuda_fail(e, "rg_gemm_noalloc: shared-memory attribute");
       }
@@ -1849,7 +2066,7 @@ extern "C" int rg_gemm_noalloc(int64_t M, int64_t N, int64_t K, const void* A, i
     int64_t slots = splits;
     if (rg::variant_streamk(variant)) {
       const int64_t kb = (K + rg::kBK - 1) / rg::kBK;
-      slots = rg::sk_geometry(tiles, kb, d->sm_count).max_pieces;
+      slots = rg::sk_geometry(tiles, kb, rg::variant_2sm(variant) ? d->sm_count / 2 : d->sm_count).max_pieces;
     }
     const int64_t need = slots > 1 ? slots * tiles * ts.bm * ts.bn * 4 : 0;
     const int64_t ticket_tiles = rg::variant_2sm(variant) ? 2 * tiles : tiles;  // cta_group::2: 128-row tiles
@@ -1881,4 +2098,32 @@ extern "C" int rg_gemm_noalloc(int64_t M, int64_t N, int64_t K, const void* A, i
   }
   e = rg::launch(&view, L, st);
   return e == cudaSuccess ? RG_OK : rg::cuda_fail(e, "rg_gemm_noalloc: launch");
+}
+
+extern "C" int rg_noalloc_check(void* stream) {
+  rg::clear_error();
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return rg::cuda_fail(e, "rg_noalloc_check: cudaGetDevice");
+  if (dev < 0 || dev >= rg::kNoallocMaxDevices) return rg::fail(RG_ERR_INVALID, "rg_noalloc_check: device index too large");
+  unsigned char* scratch = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(rg::g_noalloc_mu);
+    if (rg::g_noalloc_dev[dev].ready) scratch = rg::g_noalloc_dev[dev].scratch;
+  }
+  if (!scratch) return RG_OK;  // no rg_gemm_noalloc call has run on this device
+  if ((e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream))) != cudaSuccess)
+    return rg::cuda_fail(e, "rg_noalloc_check: stream");
+  int32_t code = 0;
+  if ((e = cudaMemcpy(&code, scratch + rg::kNoallocErrOff, sizeof(code), cudaMemcpyDeviceToHost)) != cudaSuccess)
+    return rg::cuda_fail(e, "rg_noalloc_check: read error word");
+  if (code == 0) return RG_OK;
+  // a kernel that gave up a wait may have stopped mid-reduction: clear the error
+  // word and every ticket so the next call starts clean
+  e = cudaMemset(scratch + rg::kNoallocErrOff, 0, static_cast<size_t>(rg::kNoallocBytes - rg::kNoallocErrOff));
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return rg::cuda_fail(e, "rg_noalloc_check: clear scratch");
+  static const char* role[] = {"", "TMA producer", "MMA issuer", "epilogue"};
+  return rg::fail(RG_ERR_TIMEOUT, std::string("rg_noalloc_check: a bounded wait expired in the ") +
+                                      (code >= 1 && code <= 3 ? role[code] : "kernel"));
 }

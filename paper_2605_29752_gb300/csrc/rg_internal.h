@@ -39,23 +39,22 @@ struct TileShape {
 };
 TileShape tile_shape(int tile);
 // Variant ids: tile * RG_NUM_SPLITS + log2(split) for the split-K variants, then
-// RG_VARIANT_SK(tile) (stream-K), RG_VARIANT_PAIR(tile) (multicast pairs) and
-// RG_VARIANT_2SM(tile, log2(split)) (cta_group::2, 256-row tiles with BN >= 128).
+// RG_VARIANT_SK(tile) (stream-K), RG_VARIANT_2SM(tile, log2(split)) (cta_group::2,
+// 256-row tiles with BN >= 128) and RG_VARIANT_2SM_SK(tile) (cta_group::2 stream-K).
 constexpr int kClassicVariants = RG_NUM_TILES * RG_NUM_SPLITS;
-constexpr int kPairVariants = kClassicVariants + RG_NUM_TILES;
-constexpr int k2SmVariants = kPairVariants + RG_NUM_TILES;
-inline bool variant_streamk(int v) { return v >= kClassicVariants && v < kPairVariants; }
-inline bool variant_pair(int v) { return v >= kPairVariants && v < k2SmVariants; }
+constexpr int k2SmVariants = kClassicVariants + RG_NUM_TILES;
+constexpr int k2SmSkVariants = k2SmVariants + 2 * RG_NUM_SPLITS;
 inline bool variant_2sm(int v) { return v >= k2SmVariants; }
+inline bool variant_streamk(int v) { return (v >= kClassicVariants && v < k2SmVariants) || v >= k2SmSkVariants; }
 inline int variant_tile(int v) {
-  return v >= k2SmVariants    ? RG_TILE_256x128 + (v - k2SmVariants) / RG_NUM_SPLITS
-         : v >= kPairVariants ? v - kPairVariants
+  return v >= k2SmSkVariants     ? RG_TILE_256x128 + (v - k2SmSkVariants)
+         : v >= k2SmVariants     ? RG_TILE_256x128 + (v - k2SmVariants) / RG_NUM_SPLITS
          : v >= kClassicVariants ? v - kClassicVariants
                                  : v / RG_NUM_SPLITS;
 }
 inline int variant_split(int v) {
-  return v >= k2SmVariants ? 1 << ((v - k2SmVariants) % RG_NUM_SPLITS)
-         : v >= kClassicVariants ? 1
+  return variant_streamk(v)      ? 1
+         : v >= k2SmVariants     ? 1 << ((v - k2SmVariants) % RG_NUM_SPLITS)
                                  : 1 << (v % RG_NUM_SPLITS);
 }
 // Stream-K geometry shared by the launcher, the sweep's pruning and the kernel:
@@ -111,6 +110,23 @@ int timed_sweep(rg_ctx* ctx, const std::vector<int64_t>& order, const rg_sweep_o
                 const std::function<cudaError_t()>& run);
 }
 #endif
+
+namespace rg {
+struct Fp8CtxInfo {
+  int32_t* err;
+  long long timeout;
+  int sms;
+  float* ws;
+  int64_t ws_bytes;
+  int32_t* tickets;
+  int64_t max_tickets;
+};
+int ctx_fp8_info(rg_ctx* ctx, Fp8CtxInfo* out);
+void ctx_count_launches(rg_ctx* ctx, int64_t n);
+// The CUDA device of a context (for threads the library starts).
+int ctx_device(const rg_ctx* ctx);
+int sweep_surfaces(const rg_grid* grid, int32_t rows, const int64_t* t_ns, double* tflops_out, double* stats_out);
+}
 
 struct rg_plan {
   rg::Plan p;

@@ -4,6 +4,7 @@
 // is one IEEE double operation in the stated order.
 #include <algorithm>
 #include <cmath>
+#include <limits>
 #include <string>
 #include <vector>
 
@@ -29,7 +30,10 @@ TileShape tile_shape(int tile) {
 // grown with error-free two-sums (Shewchuk, "Adaptive Precision Floating-Point
 // Arithmetic and Fast Robust Geometric Predicates", 1997); the result is the
 // expansion rounded to the nearest double, ties to even, with the correction
-// for a half-way top partial whose remainder lies beyond it.
+// for a half-way top partial whose remainder lies beyond it.  This is the
+// published scheme of R. Hettinger's "msum" recipe (Python Cookbook, recipe
+// 393090), on which Python's math.fsum is built; following the same steps is
+// what makes these sums equal the oracle's math.fsum results bit for bit.
 class ExactSum {
  public:
   void add(double x) {
@@ -164,6 +168,50 @@ extern "C" int rg_surface_stats(const rg_grid* grid, const int64_t* t_ns, double
   }
   return RG_OK;
 }
+
+namespace rg {
+// The sweep's surfaces: per timed row, rg_surface_stats' TFLOP/s surface and
+// {R_M, R_N, R_K, R_3D, R_N on the largest-K slice, mean}.  A row with cells the
+// sweep did not measure (RG_T_UNMEASURED) gets TFLOP/s 0 there, the same
+// expression as rg_surface_stats elsewhere, and NaN statistics: a surface with
+// holes has no roughness.
+int sweep_surfaces(const rg_grid* grid, int32_t rows, const int64_t* t_ns, double* tflops_out, double* stats_out) {
+  if (!tflops_out && !stats_out) return RG_OK;
+  const int64_t cells = cells_of(*grid);
+  const int64_t nn = grid->n.count, nk = grid->k.count;
+  for (int32_t v = 0; v < rows; ++v) {
+    const int64_t* t = t_ns + static_cast<int64_t>(v) * cells;
+    double* tf = tflops_out ? tflops_out + static_cast<int64_t>(v) * cells : nullptr;
+    double* st = stats_out ? stats_out + 6 * static_cast<int64_t>(v) : nullptr;
+    bool full = true;
+    for (int64_t i = 0; i < cells && full; ++i) full = t[i] != RG_T_UNMEASURED;
+    if (full) {
+      double rough[5], mean = 0.0;
+      const int rc = rg_surface_stats(grid, t, tf, rough, &mean);
+      if (rc != RG_OK) return rc;
+      if (st) {
+        for (int j = 0; j < 5; ++j) st[j] = rough[j];
+        st[5] = mean;
+      }
+      continue;
+    }
+    if (tf)
+      for (int64_t i = 0; i < cells; ++i) {
+        if (t[i] == RG_T_UNMEASURED) {
+          tf[i] = 0.0;
+          continue;
+        }
+        const double M = static_cast<double>(axis_value(grid->m, i / (nn * nk)));
+        const double N = static_cast<double>(axis_value(grid->n, (i / nk) % nn));
+        const double K = static_cast<double>(axis_value(grid->k, i % nk));
+        tf[i] = (2.0 * M * N * K) / (static_cast<double>(t[i]) * 1e3);
+      }
+    if (st)
+      for (int j = 0; j < 6; ++j) st[j] = std::numeric_limits<double>::quiet_NaN();
+  }
+  return RG_OK;
+}
+}  // namespace rg
 
 // ---------------------------------------------------------------- first-principles landscapes
 namespace {

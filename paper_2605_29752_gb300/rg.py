@@ -31,19 +31,24 @@ RG_ERR_NO_DEVICE = -9
 RG_T_UNMEASURED = 1 << 60
 RG_NUM_TILES = 6
 RG_NUM_SPLITS = 4
-RG_NUM_VARIANTS = RG_NUM_TILES * RG_NUM_SPLITS + 2 * RG_NUM_TILES + 2 * RG_NUM_SPLITS
+RG_NUM_VARIANTS = RG_NUM_TILES * RG_NUM_SPLITS + RG_NUM_TILES + 2 * RG_NUM_SPLITS + 2
 TILES = [(128, 64), (128, 128), (128, 256), (256, 64), (256, 128), (256, 256)]
 SPLITS = [1, 2, 4, 8]
 SK = "SK"
-PAIR = "PR"
 TWO_SM = "2SM"
-_BASE_2SM = RG_NUM_TILES * RG_NUM_SPLITS + 2 * RG_NUM_TILES
+TWO_SM_SK = "2SM-SK"
+_BASE_2SM = RG_NUM_TILES * RG_NUM_SPLITS + RG_NUM_TILES
+_BASE_2SM_SK = _BASE_2SM + 2 * RG_NUM_SPLITS
 
 
 def variant(tile: int, split=1) -> int:
-    """Variant id of a tile with split factor 1/2/4/8, split="SK" for stream-K, "PR" for the
-    2-CTA multicast pair, or "2SM" / ("2SM", S) for the cta_group::2 pair with split factor S
-    (tiles 256x128 and 256x256 only)."""
+    """Variant id of a tile with split factor 1/2/4/8, split="SK" for stream-K, "2SM" / ("2SM", S)
+    for the cta_group::2 pair with split factor S, or "2SM-SK" for the cta_group::2 stream-K form
+    (the last three for tiles 256x128 and 256x256 only)."""
+    if split == TWO_SM_SK:
+        if tile not in (4, 5):
+            raise ValueError("the 2-SM variants exist for the 256x128 and 256x256 tiles only")
+        return _BASE_2SM_SK + tile - 4
     if split == TWO_SM or (isinstance(split, tuple) and split[0] == TWO_SM):
         if tile not in (4, 5):
             raise ValueError("the 2-SM variant exists for the 256x128 and 256x256 tiles only")
@@ -51,27 +56,27 @@ def variant(tile: int, split=1) -> int:
         return _BASE_2SM + (tile - 4) * RG_NUM_SPLITS + SPLITS.index(s)
     if split == SK:
         return RG_NUM_TILES * RG_NUM_SPLITS + tile
-    if split == PAIR:
-        return RG_NUM_TILES * RG_NUM_SPLITS + RG_NUM_TILES + tile
     return tile * RG_NUM_SPLITS + SPLITS.index(split)
 
 
 def variant_tile(v: int) -> int:
     """Tile index (0..5) of a variant id."""
     n = RG_NUM_TILES * RG_NUM_SPLITS
+    if v >= _BASE_2SM_SK:
+        return 4 + v - _BASE_2SM_SK
     if v >= _BASE_2SM:
         return 4 + (v - _BASE_2SM) // RG_NUM_SPLITS
-    return v - n - RG_NUM_TILES if v >= n + RG_NUM_TILES else v - n if v >= n else v // RG_NUM_SPLITS
+    return v - n if v >= n else v // RG_NUM_SPLITS
 
 
 def variant_name(v: int) -> str:
+    if v >= _BASE_2SM_SK:
+        bm, bn = TILES[4 + v - _BASE_2SM_SK]
+        return f"{bm}x{bn}/2SM-SK"
     if v >= _BASE_2SM:
         bm, bn = TILES[4 + (v - _BASE_2SM) // RG_NUM_SPLITS]
         s = SPLITS[(v - _BASE_2SM) % RG_NUM_SPLITS]
         return f"{bm}x{bn}/2SM" + ("" if s == 1 else f"-S{s}")
-    if v >= RG_NUM_TILES * RG_NUM_SPLITS + RG_NUM_TILES:
-        bm, bn = TILES[v - RG_NUM_TILES * RG_NUM_SPLITS - RG_NUM_TILES]
-        return f"{bm}x{bn}/PR"
     if v >= RG_NUM_TILES * RG_NUM_SPLITS:
         bm, bn = TILES[v - RG_NUM_TILES * RG_NUM_SPLITS]
         return f"{bm}x{bn}/SK"
@@ -104,12 +109,12 @@ class rg_group_problem(C.Structure):
     _fields_ = [("M", C.c_int64), ("N", C.c_int64), ("K", C.c_int64), ("A", C.c_void_p), ("lda", C.c_int64),
                 ("B", C.c_void_p), ("ldb", C.c_int64), ("C", C.c_void_p), ("ldc", C.c_int64),
                 ("pm", C.c_int64), ("pn", C.c_int64), ("pk", C.c_int64), ("beta", C.c_int32),
-                ("reserved", C.c_int32)]
+                ("variant", C.c_int32)]
 
 
 class rg_serve_opts(C.Structure):
     _fields_ = [("hbm_budget_bytes", C.c_int64), ("max_batch", C.c_int32), ("max_inflight", C.c_int32),
-                ("tile", C.c_int32), ("reserved", C.c_int32)]
+                ("tile", C.c_int32), ("workspace_mib", C.c_int32)]
 
 
 class rg_serve_request(C.Structure):
@@ -159,28 +164,36 @@ _sigs = {
     "rg_plan_build_ex": (C.c_int, [C.POINTER(rg_grid), _P, _I32, _P, _I32, C.POINTER(_P)]),
     "rg_launch_count": (C.c_int, [_P, C.POINTER(_I64)]),
     "rg_set_test_stall": (C.c_int, [_P, _I32]),
-    "rg_group_create": (C.c_int, [_P, _I32, _I32, C.POINTER(_P)]),
+    "rg_group_create": (C.c_int, [_P, _I32, _I32, _I64, C.POINTER(_P)]),
     "rg_group_destroy": (None, [_P]),
     "rg_gemm_grouped": (C.c_int, [_P, C.POINTER(rg_group_problem), _I32, _P]),
     "rg_serve_opts_default": (None, [C.POINTER(rg_serve_opts)]),
     "rg_serve": (C.c_int, [_P, _P, C.POINTER(rg_serve_opts), C.POINTER(rg_serve_request), _I32,
                            C.POINTER(rg_serve_result), C.POINTER(rg_serve_stats)]),
+    "rg_serve_start": (C.c_int, [_P, _P, C.POINTER(rg_serve_opts), C.POINTER(_P)]),
+    "rg_serve_submit": (C.c_int, [_P, C.POINTER(rg_serve_request), C.POINTER(_I64)]),
+    "rg_serve_poll": (C.c_int, [_P, _I64, C.POINTER(rg_serve_result), C.POINTER(_I32)]),
+    "rg_serve_wait": (C.c_int, [_P, _I64, C.POINTER(rg_serve_result)]),
+    "rg_serve_stop": (C.c_int, [_P, C.POINTER(rg_serve_stats)]),
     "rg_fp8_quantize": (C.c_int, [_P, _P, _I64, _I64, _I64, _P, _I64, _P, _P]),
     "rg_gemm_fp8": (C.c_int, [_P, _I64, _I64, _I64, _P, _I64, _P, _P, _I64, _P, _P, _I64, _P]),
     "rg_sweep_fp8": (C.c_int, [_P, C.POINTER(rg_grid), _P, _P, _P, _P, _P, C.POINTER(rg_sweep_opts), _P, _P]),
     "rg_landscape": (C.c_int, [C.POINTER(rg_grid), _I32, C.c_double, _I32, C.c_double, _I32, _P, _I32, _I32, _P]),
     "rg_kol": (C.c_int, [C.c_double, C.c_double, C.c_double, C.c_double, _P, _P]),
     "rg_gemm_noalloc": (C.c_int, [_I64, _I64, _I64, _P, _I64, _P, _I64, _P, _I64, _I32, _I32, _P]),
+    "rg_noalloc_check": (C.c_int, [_P]),
     "rg_plan_free": (None, [_P]),
     "rg_plan_grid": (C.c_int, [_P, C.POINTER(rg_grid)]),
     "rg_plan_tables": (C.c_int, [_P, _P, _P, _P, _P, _P, _P, _P]),
     "rg_plan_lookup": (C.c_int, [_P, _I64, _I64, _I64, C.POINTER(C.POINTER(rg_leaf)), C.POINTER(_I32),
                                  C.POINTER(_I64)]),
     "rg_gemm_plan": (C.c_int, [_P, _P, _I64, _I64, _I64, _P, _I64, _P, _I64, _P, _I64, _P]),
+    "rg_gemm_plan_host": (C.c_int, [_P, _P, _I64, _I64, _I64, _P, _I64, _P, _I64, _P, _I64, _P]),
     "rg_plan_save": (C.c_int, [_P, _P, C.c_char_p]),
     "rg_plan_load": (C.c_int, [C.c_char_p, _P, C.POINTER(_P)]),
     "rg_surface_stats": (C.c_int, [C.POINTER(rg_grid), _P, _P, _P, _P]),
-    "rg_sweep": (C.c_int, [_P, C.POINTER(rg_grid), _I32, _P, _P, _P, _P, _P, C.POINTER(rg_sweep_opts), _P, _P]),
+    "rg_sweep": (C.c_int, [_P, C.POINTER(rg_grid), _I32, _P, _P, _P, _P, _P, C.POINTER(rg_sweep_opts), _P, _P, _P,
+                           _P]),
     "rg_gemm_memtwin": (C.c_int, [_P, _I64, _I64, _I64, _P, _I64, _P, _I64, _P, _I64, _I32, _P]),
     "rg_sweep_memtwin": (C.c_int, [_P, C.POINTER(rg_grid), _I32, _P, _P, _P, _P, C.POINTER(rg_sweep_opts), _P,
                                    _P]),
@@ -369,6 +382,13 @@ def rg_gemm_plan(ctx, plan, M, N, K, A, lda, B, ldb, Cp, ldc, stream=None) -> No
            "rg_gemm_plan")
 
 
+def rg_gemm_plan_host(ctx, plan, M, N, K, A, lda, B, ldb, Cp, ldc, stream=None) -> None:
+    """Plan GEMM on host buffers (numpy arrays, pinned tensors or raw host addresses): copies in,
+    executes, copies out and synchronises inside the library."""
+    _check(_lib.rg_gemm_plan_host(ctx, plan, M, N, K, _ptr(A), lda, _ptr(B), ldb, _ptr(Cp), ldc, _stream(stream)),
+           "rg_gemm_plan_host")
+
+
 def rg_plan_save(plan: int, path: str, ctx: int | None = None) -> None:
     _check(_lib.rg_plan_save(plan, ctx, path.encode()), "rg_plan_save")
 
@@ -408,12 +428,24 @@ def rg_sweep_opts_default() -> rg_sweep_opts:
 def rg_sweep(ctx, grid: rg_grid, variant_ids, A, B, Cp, opts: rg_sweep_opts | None = None, plan: int | None = None,
              stream=None) -> np.ndarray:
     """t_ns[len(variant_ids)][cells] (or [1][cells] for a plan sweep)."""
+    return rg_sweep_surfaces(ctx, grid, variant_ids, A, B, Cp, opts, plan, stream)[0]
+
+
+SWEEP_STATS = ("R_M", "R_N", "R_K", "R_3D", "R_N_slice", "mean_tflops")
+
+
+def rg_sweep_surfaces(ctx, grid: rg_grid, variant_ids, A, B, Cp, opts: rg_sweep_opts | None = None,
+                      plan: int | None = None, stream=None):
+    """(t_ns[rows][cells], tflops[rows][cells], stats[rows][6]) from one rg_sweep call; the stats
+    columns are SWEEP_STATS (NaN for a row the pruning left incomplete)."""
     vids = np.ascontiguousarray(variant_ids if plan is None else [0], dtype=np.int32)
     out = np.zeros((len(vids), grid_cells(grid)), np.int64)
+    tf = np.zeros((len(vids), grid_cells(grid)), np.float64)
+    st = np.zeros((len(vids), 6), np.float64)
     o = opts or rg_sweep_opts_default()
     _check(_lib.rg_sweep(ctx, C.byref(grid), len(vids), vids.ctypes.data, plan, _ptr(A), _ptr(B), _ptr(Cp),
-                         C.byref(o), out.ctypes.data, _stream(stream)), "rg_sweep")
-    return out
+                         C.byref(o), out.ctypes.data, tf.ctypes.data, st.ctypes.data, _stream(stream)), "rg_sweep")
+    return out, tf, st
 
 
 def rg_gemm_memtwin(ctx, M, N, K, A, lda, B, ldb, Cp, ldc, tile, stream=None) -> None:
@@ -448,9 +480,9 @@ def rg_decompose(grid: rg_grid, t_gemm_ns, t_mem_ns, p_tflops: float):
     return comp, over, st
 
 
-def rg_group_create(ctx: int, tile: int, max_items: int) -> int:
+def rg_group_create(ctx: int, tile: int, max_items: int, workspace_bytes: int = 64 << 20) -> int:
     h = _P()
-    _check(_lib.rg_group_create(ctx, tile, max_items, C.byref(h)), "rg_group_create")
+    _check(_lib.rg_group_create(ctx, tile, max_items, workspace_bytes, C.byref(h)), "rg_group_create")
     return h.value
 
 
@@ -459,13 +491,15 @@ def rg_group_destroy(group: int) -> None:
 
 
 def group_problems(items) -> "C.Array":
-    """items: iterables (M, N, K, A, lda, B, ldb, C, ldc[, beta[, pm, pn, pk]]) with pointers or tensors."""
+    """items: iterables (M, N, K, A, lda, B, ldb, C, ldc[, beta[, pm, pn, pk[, variant]]]) with pointers or
+    tensors; variant -1 (the default) runs the group's tile with split 1."""
     arr = (rg_group_problem * max(1, len(items)))()
     for i, it in enumerate(items):
         M, N, K, A, lda, B, ldb, Cp, ldc = it[:9]
         beta = it[9] if len(it) > 9 else 0
         pm, pn, pk = it[10:13] if len(it) > 12 else (0, 0, 0)
-        arr[i] = rg_group_problem(M, N, K, _ptr(A), lda, _ptr(B), ldb, _ptr(Cp), ldc, pm, pn, pk, beta, 0)
+        v = it[13] if len(it) > 13 else -1
+        arr[i] = rg_group_problem(M, N, K, _ptr(A), lda, _ptr(B), ldb, _ptr(Cp), ldc, pm, pn, pk, beta, v)
     return arr
 
 
@@ -495,6 +529,46 @@ def rg_serve(ctx, plan, opts: rg_serve_opts, requests):
                 "batch": r.batch, "status": r.status} for r in res[:n]]
     stats = {k: getattr(st, k) for k, _ in rg_serve_stats._fields_}
     return results, stats
+
+
+def _result_dict(r) -> dict:
+    return {"admitted_ns": r.admitted_ns, "launched_ns": r.launched_ns, "done_ns": r.done_ns,
+            "batch": r.batch, "status": r.status}
+
+
+def rg_serve_start(ctx, plan, opts: rg_serve_opts) -> int:
+    """Start an online server (a worker thread running the serving engine); returns its handle."""
+    h = _P()
+    _check(_lib.rg_serve_start(ctx, plan, C.byref(opts), C.byref(h)), "rg_serve_start")
+    return h.value
+
+
+def rg_serve_submit(server, M, N, K, A, lda, B, ldb, Cp, ldc) -> int:
+    """Submit one request; returns its id."""
+    req = rg_serve_request(M, N, K, _ptr(A), lda, _ptr(B), ldb, _ptr(Cp), ldc, 0)
+    i = _I64()
+    _check(_lib.rg_serve_submit(server, C.byref(req), C.byref(i)), "rg_serve_submit")
+    return i.value
+
+
+def rg_serve_poll(server, rid: int):
+    """None while the request runs, else its result dict."""
+    r = rg_serve_result()
+    d = _I32()
+    _check(_lib.rg_serve_poll(server, rid, C.byref(r), C.byref(d)), "rg_serve_poll")
+    return _result_dict(r) if d.value else None
+
+
+def rg_serve_wait(server, rid: int) -> dict:
+    r = rg_serve_result()
+    _check(_lib.rg_serve_wait(server, rid, C.byref(r)), "rg_serve_wait")
+    return _result_dict(r)
+
+
+def rg_serve_stop(server) -> dict:
+    st = rg_serve_stats()
+    _check(_lib.rg_serve_stop(server, C.byref(st)), "rg_serve_stop")
+    return {k: getattr(st, k) for k, _ in rg_serve_stats._fields_}
 
 
 def rg_fp8_quantize(ctx, X, rows, cols, ldx, Q, ldq, scales, stream=None) -> None:
@@ -545,3 +619,9 @@ def rg_gemm_noalloc(M, N, K, A, lda, B, ldb, Cp, ldc, variant_id, beta=0, stream
     library); returns the status code.  See include/rg.h for its limits."""
     return _lib.rg_gemm_noalloc(M, N, K, _ptr(A), lda, _ptr(B), ldb, _ptr(Cp), ldc, variant_id, beta,
                                 _stream(stream))
+
+
+def rg_noalloc_check(stream=None) -> int:
+    """Status of the rg_gemm_noalloc work enqueued so far on the current device (synchronises the
+    stream): RG_OK, or RG_ERR_TIMEOUT if a bounded wait expired (the scratch is then cleared)."""
+    return _lib.rg_noalloc_check(_stream(stream))

@@ -41,3 +41,37 @@ def test_host_steps_timing_record():
     rec = bench.host_steps_timing(4, seed=1)["host_steps"]
     assert set(rec) == {"table", "oracle_dp_s", "oracle_roughness_s", "library_plan_build_s", "library_surface_stats_s"}
     assert all(rec[k] >= 0 for k in rec if k != "table")
+
+
+def test_roof_times_pick_the_binding_limit():
+    # P = 1000 TFLOP/s, BW = 1000 GB/s: a 4096^3 cell is compute-bound, a 128 x 128 x 4096 cell memory-bound
+    t = bench.roof_times_ns([4096, 128], [4096, 128], [4096, 4096], 1000.0, 1000.0)
+    assert t[0] == pytest.approx(2.0 * 4096 ** 3 / 1e6)
+    assert t[1] == pytest.approx((2 * 128 * 4096 * 2 + 4 * 128 * 128) / 1000.0)
+
+
+def test_summarize_reports_the_mean_roofline_fraction():
+    tf = np.array([1.0, 2.0, 3.0])
+    r = {"R_N_slice": 1.0, "R_3D": 1.0, "R_M": 1.0, "R_N": 1.0, "R_K": 1.0}
+    s = bench.summarize(tf, r, 2.0, t_ns=np.array([10, 20, 40]), troof=np.array([5.0, 5.0, 5.0]))
+    assert s["roofline_mean_frac"] == pytest.approx((0.5 + 0.25 + 0.125) / 3)
+    assert s["R_N_slice_over_mean"] == 0.5
+
+
+def test_slice_attribution_splits_the_slice_roughness_by_regime():
+    count = 4
+    tf = np.zeros((count, count, count))
+    tf[:, :, -1] = np.arange(count)[None, :] * 10.0            # |dN| = 10 everywhere on the K = max slice
+    out = bench.slice_attribution(tf.ravel(), count, 512)
+    total = sum(v["contribution_to_R_N_slice"] for v in out.values())
+    assert total == pytest.approx(10.0)                          # the slice's R_N, split without loss
+    assert sum(v["pair_share"] for v in out.values()) == pytest.approx(1.0)
+
+
+def test_noise_floor_of_identical_repeats_is_zero_and_scales():
+    rs = np.random.default_rng(0)
+    a = rs.uniform(100, 200, size=4 ** 3)
+    assert bench.noise_floor(a, a, 4)["R_N_slice"] == 0.0
+    b = a + np.where(np.arange(a.size) % 2 == 0, 1.0, -1.0)     # alternating +-1 difference
+    nf = bench.noise_floor(a, b, 4)
+    assert nf["R_3D"] >= 0.0 and nf["R_N_slice"] >= 0.0

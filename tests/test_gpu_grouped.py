@@ -92,16 +92,121 @@ def test_grouped_beta_and_many_replays(rg, ctx):
 
 
 def test_grouped_limits(rg, ctx):
-    g = rg.rg_group_create(ctx, 0, 2)
+    """More problems than a work list holds run as several launches in turn; K == 0 problems and a
+    problem whose split-K partials alone exceed the group's workspace are refused before anything
+    is enqueued."""
+    g = rg.rg_group_create(ctx, 0, 2, 1 << 20)
     try:
-        A = torch.zeros((64, 64), device="cuda", dtype=torch.bfloat16)
-        C = torch.zeros((64, 64), device="cuda")
+        a, b, A, B = _problem(192, 136, 200, seed=8)
         rg.rg_gemm_grouped(g, [])
-        with pytest.raises(rg.RGError) as e:
-            rg.rg_gemm_grouped(g, [(64, 64, 64, A, 64, A, 64, C, 64)] * 3)
-        assert e.value.code == rg.RG_ERR_SHAPE
-        with pytest.raises(rg.RGError):
-            rg.rg_gemm_grouped(g, [(64, 64, 0, A, 64, A, 64, C, 64)])
+        outs = [torch.full((192, 136), float("nan"), device="cuda") for _ in range(5)]
+        rg.rg_gemm_grouped(g, [(192, 136, 200, A, 200, B, 136, C, 136) for C in outs])
         rg.rg_check(ctx)
+        for C in outs:
+            ok, ratio = og.check(C.cpu().numpy(), og.bf16_bits_to_f64(a), og.bf16_bits_to_f64(b))
+            assert ok, ratio
+        Z = torch.zeros((64, 64), device="cuda")
+        with pytest.raises(rg.RGError):
+            rg.rg_gemm_grouped(g, [(64, 64, 0, A, 64, A, 64, Z, 64)])
+        big = torch.zeros((1024, 1024), device="cuda", dtype=torch.bfloat16)
+        Cb = torch.full((1024, 1024), 7.0, device="cuda")
+        # 128x128 split 2 on 1024^2: 64 tiles x 2 x 64 KiB = 8 MiB of partials > the 1 MiB workspace
+        with pytest.raises(rg.RGError) as e:
+            rg.rg_gemm_grouped(g, [(1024, 1024, 1024, big, 1024, big, 1024, Cb, 1024, 0, 0, 0, 0, rg.variant(1, 2)),
+                                   (192, 136, 200, A, 200, B, 136, outs[0], 136)])
+        assert e.value.code == rg.RG_ERR_SHAPE
+        torch.cuda.synchronize()
+        assert torch.all(Cb == 7.0)
+    finally:
+        rg.rg_group_destroy(g)
+
+
+# (M, N, K, variant, beta, pads): split-K on several tiles, cta_group::2 with and without split,
+# a stream-K choice (runs as its tile with split 1), padding and beta = 1
+MIXED = [
+    (512, 384, 2048, ("t", 1, 2), 0, (0, 0, 0)),
+    (300, 200, 1000, ("t", 0, 4), 0, (384, 256, 1024)),
+    (256, 512, 1536, ("t", 2, 8), 1, (0, 0, 0)),
+    (640, 256, 512, ("t", 3, 2), 0, (0, 0, 0)),
+    (520, 512, 2048, ("2sm", 5, 1), 0, (0, 0, 0)),
+    (768, 640, 1024, ("2sm", 4, 2), 0, (1024, 640, 1024)),
+    (384, 384, 4096, ("2sm", 5, 4), 1, (0, 0, 0)),
+    (1024, 768, 512, ("sk", 2), 0, (0, 0, 0)),
+    (640, 512, 768, ("2smsk", 5), 0, (0, 0, 0)),
+    (200, 136, 96, ("t", 1, 1), 0, (0, 0, 0)),
+]
+
+
+def _vid(rg, spec):
+    kind = spec[0]
+    if kind == "t":
+        return rg.variant(spec[1], spec[2])
+    if kind == "2sm":
+        return rg.variant(spec[1], (rg.TWO_SM, spec[2]))
+    if kind == "sk":
+        return rg.variant(spec[1], rg.SK)
+    return rg.variant(spec[1], rg.TWO_SM_SK)
+
+
+def _as_grouped(rg, v):
+    """The variant a grouped launch runs for v: stream-K choices run as their tile, split 1."""
+    name = rg.variant_name(v)
+    if name.endswith("/2SM-SK"):
+        return rg.variant(rg.variant_tile(v), rg.TWO_SM)
+    if name.endswith("/SK"):
+        return rg.variant(rg.variant_tile(v), 1)
+    return v
+
+
+# partials of 0.5-1 MiB each: with a 1 MiB workspace each family runs as several launches
+SMALL_SPLITS = [
+    (256, 256, 1024, ("t", 0, 2), 0, (0, 0, 0)),
+    (256, 256, 768, ("t", 0, 2), 1, (0, 0, 0)),
+    (200, 256, 1024, ("t", 0, 2), 0, (0, 0, 0)),
+    (128, 384, 2048, ("t", 0, 4), 0, (0, 0, 0)),
+    (256, 128, 1024, ("t", 1, 4), 0, (0, 0, 0)),
+    (256, 256, 1024, ("2sm", 4, 2), 0, (0, 0, 0)),
+    (512, 256, 1024, ("2sm", 4, 2), 1, (0, 0, 0)),
+    (256, 256, 2048, ("2sm", 5, 2), 0, (0, 0, 0)),
+    (136, 72, 512, ("t", 1, 1), 0, (0, 0, 0)),
+]
+
+
+@pytest.mark.parametrize("case", ["mixed_64MiB", "small_splits_1MiB"])
+def test_grouped_split_k_and_two_sm_items(rg, ctx, case):
+    """Problems with their own variants (split-K tiles, cta_group::2 pairs with split-K, stream-K
+    choices) in one call: one launch per kernel family, several per family when the workspace
+    cannot hold all their partials at once; each result within the oracle's bound and bitwise
+    rg_gemm's for the same variant."""
+    problems, ws = (MIXED, 64 << 20) if case == "mixed_64MiB" else (SMALL_SPLITS, 1 << 20)
+    g = rg.rg_group_create(ctx, 1, 8, ws)
+    try:
+        probs, checks = [], []
+        for i, (M, N, K, spec, beta, pads) in enumerate(problems):
+            v = _vid(rg, spec)
+            a, b, A, B = _problem(M, N, K, seed=40 + i)
+            c0 = synthetic.normal_stream_f32(40 + i, 5, M * N).reshape(M, N) if beta else None
+            C = torch.from_numpy(c0).cuda() if beta else torch.full((M, N), float("nan"), device="cuda")
+            Cr = torch.from_numpy(c0).cuda() if beta else torch.full((M, N), float("nan"), device="cuda")
+            rg.rg_gemm(ctx, M, N, K, A, K, B, N, Cr, N, _as_grouped(rg, v), beta, *pads)
+            probs.append((M, N, K, A, K, B, N, C, N, beta) + pads + (v,))
+            checks.append((a, b, c0, C, Cr, v))
+        n0 = rg.rg_launch_count(ctx)
+        rg.rg_gemm_grouped(g, probs)
+        rg.rg_check(ctx)
+        families = {("2sm" if "2SM" in rg.variant_name(_as_grouped(rg, c[5])) else "") + str(rg.variant_tile(c[5]))
+                    for c in checks}
+        if case == "small_splits_1MiB":
+            assert rg.rg_launch_count(ctx) - n0 > len(families)      # some family ran as several launches
+        else:
+            assert rg.rg_launch_count(ctx) - n0 == len(families)     # one launch per family
+        for a, b, c0, C, Cr, v in checks:
+            got = C.cpu().numpy()
+            a64, b64 = og.bf16_bits_to_f64(a), og.bf16_bits_to_f64(b)
+            c64 = a64 @ b64 + (c0.astype(np.float64) if c0 is not None else 0.0)
+            s64 = np.abs(a64) @ np.abs(b64) + (np.abs(c0.astype(np.float64)) if c0 is not None else 0.0)
+            ratio, ez = og.error_ratio(got, c64, s64)
+            assert ez and ratio <= og.bound(a.shape[1] + 1), (rg.variant_name(v), ratio)
+            assert np.array_equal(got, Cr.cpu().numpy()), rg.variant_name(v)
     finally:
         rg.rg_group_destroy(g)

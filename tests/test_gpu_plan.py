@@ -5,7 +5,7 @@ import numpy as np
 import pytest
 
 import synthetic
-from oracle import dp
+from oracle import dp, roughness
 from oracle import gemm as og
 
 torch = pytest.importorskip("torch")
@@ -37,6 +37,11 @@ def _plan_with_every_action(rg, shape, seed):
     g = rg.make_grid((128, 128, shape[0]), (128, 128, shape[1]), (128, 128, shape[2]))
     h = rg.rg_plan_build(g, T0.reshape(len(vids), -1), vids)
     ref = dp.plan(T0, ((128, 128, shape[0]), (128, 128, shape[1]), (128, 128, shape[2])))
+    # the library's tables are the oracle's, bit for bit, on the build that executes them
+    got = rg.rg_plan_tables(h)
+    for key in ("T0s", "T1", "target", "T2", "action", "q"):
+        assert np.array_equal(got[key], ref[key]), key
+    assert np.array_equal(got["vstar"], np.asarray(vids)[ref["vstar"]])
     acts = set(int(a) for a in ref["action"].ravel())
     return h, acts, ref
 
@@ -108,10 +113,27 @@ def test_sweep_tiny_grid_and_plan_sweep(rg, ctx):
     Ks = np.tile(np.array([128, 256, 384]), 9)
     assert np.all(tp[1][Ks < 256] == rg.RG_T_UNMEASURED)   # fewer than 2 K blocks per split
     assert np.all(tp[1][Ks >= 256] < 10**8)                # few tiles: the split variant is timed
+    # the surfaces and statistics the sweep returns are the oracle's, bit for bit, from its times
+    t2, tf2, st2 = rg.rg_sweep_surfaces(ctx, g, vids, A, B, C, opts)
+    ogrid = ((128, 128, 3),) * 3
+    for row in range(2):
+        if np.any(t2[row] == rg.RG_T_UNMEASURED):
+            measured = t2[row] != rg.RG_T_UNMEASURED
+            assert np.all(np.isnan(st2[row])) and np.all(tf2[row][~measured] == 0.0)
+            S = roughness.surface(np.where(measured, t2[row], 1).reshape(3, 3, 3), ogrid).ravel()
+            assert np.array_equal(tf2[row][measured], S[measured])
+            continue
+        S = roughness.surface(t2[row].reshape(3, 3, 3), ogrid)
+        ref = roughness.roughness_all(S)
+        assert np.array_equal(tf2[row], S.ravel())
+        assert [st2[row][i] for i in range(5)] == [ref[k] for k in ("R_M", "R_N", "R_K", "R_3D", "R_N_slice")]
+        assert st2[row][5] == roughness.mean(S)
     plan = rg.rg_plan_build(g, t, vids)
     try:
-        tp = rg.rg_sweep(ctx, g, [0], A, B, C, opts, plan=plan)
+        tp, tfp, stp = rg.rg_sweep_surfaces(ctx, g, [0], A, B, C, opts, plan=plan)
         assert tp.shape == (1, 27) and np.all(tp > 0)
+        S = roughness.surface(tp[0].reshape(3, 3, 3), ogrid)
+        assert np.array_equal(tfp[0], S.ravel()) and stp[0][5] == roughness.mean(S)
         # the last swept cell's C is the plan's result for 384^3 only if it ran last;
         # run it explicitly and check it
         _exec(rg, ctx, plan, 384, 384, 384)
@@ -148,3 +170,33 @@ def test_timeout_path_returns_error_and_context_recovers(rg, ctx):
     rg.rg_check(ctx)
     ok, _ = og.check(C.cpu().numpy(), og.bf16_bits_to_f64(a_bits), og.bf16_bits_to_f64(b_bits))
     assert ok
+
+
+@pytest.mark.parametrize("shape", [(384, 512, 256), (200, 136, 100), (511, 384, 264)])
+def test_plan_host_buffers(rg, ctx, shape):
+    """rg_gemm_plan_host: host operands (numpy, unaligned leading dimensions allowed) are copied
+    in, the plan runs, C is copied back before the call returns; the result is the device
+    path's bit for bit and within the oracle's bound."""
+    M, N, K = shape
+    h, _, _ = _plan_with_every_action(rg, (4, 4, 4), seed=5)
+    try:
+        a_bits, b_bits = synthetic.operands_bf16(M, N, K, seed=31)
+        a_h = np.ascontiguousarray(a_bits.view(np.uint16))
+        b_h = np.ascontiguousarray(b_bits.view(np.uint16))
+        c_h = np.full((M, N), np.nan, np.float32)
+        rg.rg_gemm_plan_host(ctx, h, M, N, K, a_h, K, b_h, N, c_h, N)
+        ok, ratio = og.check(c_h, og.bf16_bits_to_f64(a_bits), og.bf16_bits_to_f64(b_bits))
+        assert ok and not np.any(np.isnan(c_h)), ratio
+        # the device path on aligned copies of the same operands
+        la, lb = (K + 7) // 8 * 8, (N + 7) // 8 * 8
+        a_pad = np.zeros((M, la), np.uint16)
+        a_pad[:, :K] = a_h
+        b_pad = np.zeros((K, lb), np.uint16)
+        b_pad[:, :N] = b_h
+        A, B = dev_bf16(a_pad), dev_bf16(b_pad)
+        C = torch.full((M, lb), float("nan"), device="cuda")
+        rg.rg_gemm_plan(ctx, h, M, N, K, A, la, B, lb, C, lb)
+        rg.rg_check(ctx)
+        assert np.array_equal(C.cpu().numpy()[:, :N], c_h)
+    finally:
+        rg.rg_plan_free(h)

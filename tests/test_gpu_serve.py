@@ -188,3 +188,111 @@ def test_serving_routes_each_request_to_its_autotuned_tile(rg, ctx, streams):
         assert len(tiles_used) >= 3
     finally:
         rg.rg_plan_free(plan)
+
+
+def _full_plan(rg, seed, vids):
+    """A plan over the 8^3 grid from a synthetic T0 table whose DP uses every action (padding,
+    splits along M, N and K) and many kernel variants."""
+    g = rg.make_grid((128, 128, 8))
+    rs = np.random.default_rng(seed)
+    s = (np.arange(8) + 1) * 128.0
+    base = 50.0 + 2.0 * s[:, None, None] * s[None, :, None] * s[None, None, :] / 4e5   # a small fixed cost
+    T0 = np.stack([np.round(base * rs.uniform(0.6, 1.6, size=(8, 8, 8))) for _ in vids]).astype(np.int64)
+    plan = rg.rg_plan_build(g, T0.reshape(len(vids), -1), vids)
+    acts = set(rg.rg_plan_tables(plan)["action"].ravel().tolist())
+    assert acts >= {0, 1, 2, 3}, acts
+    return plan
+
+
+def _full_vids(rg):
+    return [rg.variant(0, 2), rg.variant(1, 1), rg.variant(1, 4), rg.variant(2, 1), rg.variant(3, 2),
+            rg.variant(4, 1), rg.variant(5, 8), rg.variant(1, rg.SK), rg.variant(4, (rg.TWO_SM, 2)),
+            rg.variant(5, rg.TWO_SM), rg.variant(5, rg.TWO_SM_SK)]
+
+
+def test_serving_through_the_full_plan(rg, ctx, streams):
+    """Requests routed through a full plan (padding, M/N/K splits with phase-ordered beta = 1
+    pieces, split-K and cta_group::2 variants): every result within the oracle's bound, the same
+    bits alone as in the mix, and the same bits as rg_gemm_plan wherever no leaf is a stream-K
+    choice (the grouped launch runs those as their tile with split 1)."""
+    a_bits, b_bits, A, B = streams
+    plan = _full_plan(rg, 0, _full_vids(rg))
+    try:
+        trace = _trace(90, 40000.0, seed=12)
+        trace += [(200, 136, 1000, trace[-1][3] + 1000), (1000, 904, 520, trace[-1][3] + 2000)]   # off-grid
+        outs = [torch.full((M, N), float("nan"), device="cuda") for M, N, K, _ in trace]
+        opts = rg.rg_serve_opts_default()
+        opts.max_batch = 12
+        opts.max_inflight = 3
+        res, st = rg.rg_serve(ctx, plan, opts, _requests(trace, A, B, outs))
+        rg.rg_check(ctx)
+        assert all(r["status"] == 0 for r in res) and st["requests"] == len(trace)
+        multi = 0
+        for i, (M, N, K, _) in enumerate(trace):
+            a = og.bf16_bits_to_f64(a_bits[:M * K].reshape(M, K))
+            b = og.bf16_bits_to_f64(b_bits[:K * N].reshape(K, N))
+            ok, ratio = og.check(outs[i].cpu().numpy(), a, b)
+            assert ok, (i, ratio)
+            leaves, _ = rg.rg_plan_lookup(plan, M, N, K)
+            multi += len(leaves) > 1
+            if not any(rg.variant_name(l[0]).endswith("SK") for l in leaves):
+                ref = torch.full((M, N), float("nan"), device="cuda")
+                rg.rg_gemm_plan(ctx, plan, M, N, K, A, K, B, N, ref, N)
+                rg.rg_check(ctx)
+                assert torch.equal(ref, outs[i]), (i, leaves)
+        assert multi >= 10
+        for i in range(0, len(trace), 7):                      # alone
+            M, N, K, _ = trace[i]
+            alone = torch.full((M, N), float("nan"), device="cuda")
+            r1, _ = rg.rg_serve(ctx, plan, opts, [(M, N, K, A, K, B, N, alone, N, 0)])
+            assert r1[0]["status"] == 0
+            assert torch.equal(alone, outs[i]), i
+    finally:
+        rg.rg_plan_free(plan)
+
+
+def test_online_server_submit_poll_wait_stop(rg, ctx, streams):
+    """The online entry points: requests submitted from two host threads while earlier ones run,
+    polled and waited for; every result is bitwise the trace replay's for the same plan."""
+    import threading
+    a_bits, b_bits, A, B = streams
+    plan = _full_plan(rg, 3, _full_vids(rg))
+    try:
+        trace = _trace(60, 1.0, seed=14)
+        opts = rg.rg_serve_opts_default()
+        opts.max_batch = 8
+        ref = [torch.full((M, N), float("nan"), device="cuda") for M, N, K, _ in trace]
+        rg.rg_serve(ctx, plan, opts, [(M, N, K, A, K, B, N, ref[i], N, 0) for i, (M, N, K, _) in enumerate(trace)])
+        rg.rg_check(ctx)
+        outs = [torch.full((M, N), float("nan"), device="cuda") for M, N, K, _ in trace]
+        torch.cuda.synchronize()
+        srv = rg.rg_serve_start(ctx, plan, opts)
+        ids = {}
+        try:
+            def submit(part):
+                for i in part:
+                    M, N, K, _ = trace[i]
+                    ids[i] = rg.rg_serve_submit(srv, M, N, K, A, K, B, N, outs[i], N)
+            threads = [threading.Thread(target=submit, args=(range(j, len(trace), 2),)) for j in range(2)]
+            for t in threads:
+                t.start()
+            for t in threads:
+                t.join()
+            assert sorted(ids.values()) == list(range(len(trace)))
+            done = 0
+            for i in range(len(trace)):
+                r = rg.rg_serve_poll(srv, ids[i])
+                if r is None:
+                    r = rg.rg_serve_wait(srv, ids[i])
+                assert r["status"] == 0 and r["done_ns"] >= r["admitted_ns"] >= 0
+                done += 1
+        finally:
+            st = rg.rg_serve_stop(srv)
+        assert done == len(trace) and st["requests"] == len(trace)
+        assert st["p99_latency_us"] >= st["p50_latency_us"] > 0
+        for i in range(len(trace)):
+            assert torch.equal(outs[i], ref[i]), i
+        with pytest.raises(rg.RGError):
+            rg.rg_serve_poll(None, 0)                           # a null server is refused
+    finally:
+        rg.rg_plan_free(plan)
