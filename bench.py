@@ -50,16 +50,97 @@ def parse():
                    help="CSV file for the nvidia-smi clock samples of the timed region (default: a temp file)")
     p.add_argument("--shape", type=int, nargs=3, default=None, metavar=("M", "N", "K"),
                    help="time one GEMM shape with --variant instead of the landscape (profiling aid)")
-    p.add_argument("--variant", default="256x256/S1", help="variant for --shape, e.g. 128x256/S1")
+    p.add_argument("--variant", default="256x256/S1",
+                   help="variant for --shape, e.g. 128x256/S1, or an FP8 variant such as 'fp8 128x256/S1'")
     p.add_argument("--reps", type=int, default=20, help="timed launches for --shape")
+    p.add_argument("--phase-timers", action="store_true",
+                   help="with --shape: load the phase-timer build (librg_timers.so, built with "
+                        "`python -m paper_2605_29752_gb300.build --phase-timers`) and report per-CTA phase times")
     return p.parse_args()
 
 
+def phase_summary(rec):
+    """Medians over CTAs of each phase of one traced launch, in ns (SM-clock stamps converted with each
+    CTA's own globaltimer / clock ratio); a phase's median is taken over the CTAs that reached both of
+    its stamps (the odd CTA of a cta_group::2 pair issues no MMAs, only some CTAs run a fixup)."""
+    rec = rec.astype(np.float64)
+    f = {n: i for i, n in enumerate(("gt_entry", "gt_exit", "exit", "dep_wait", "first_stage", "last_mma_commit",
+                                     "first_acc_ready", "epilogue_done", "fixup_start", "fixup_end", "units"))}
+    rec = rec[rec[:, f["exit"]] > 0]
+    ns_per_cycle = (rec[:, f["gt_exit"]] - rec[:, f["gt_entry"]]) / rec[:, f["exit"]]
+
+    def span(a, b):
+        sel = (rec[:, f[b]] > 0) & ((rec[:, f[a]] > 0) if a != "entry" else True)
+        start = rec[sel, f[a]] if a != "entry" else 0.0
+        x = (rec[sel, f[b]] - start) * ns_per_cycle[sel]
+        return (float(np.median(x)), int(sel.sum())) if sel.any() else (None, 0)
+    out = {"ctas": int(len(rec)), "units_per_cta": float(np.median(rec[:, f["units"]])),
+           "launch_span_ns": float(rec[:, f["gt_exit"]].max() - rec[:, f["gt_entry"]].min())}
+    # launch-level: when the CTAs passed the dependency wait (on the global clock) and when they exited
+    rel = rec[:, f["gt_entry"]] + rec[:, f["dep_wait"]] * ns_per_cycle
+    out["release_skew_ns"] = float(rel.max() - rel.min())
+    out["first_release_to_last_exit_ns"] = float(rec[:, f["gt_exit"]].max() - rel.min())
+    out["exit_skew_ns"] = float(rec[:, f["gt_exit"]].max() - rec[:, f["gt_exit"]].min())
+    for name, a, b in (("entry_to_dep_wait", "entry", "dep_wait"), ("dep_wait_to_first_stage", "dep_wait", "first_stage"),
+                       ("first_stage_to_last_mma_commit", "first_stage", "last_mma_commit"),
+                       ("last_mma_commit_to_epilogue_done", "last_mma_commit", "epilogue_done"),
+                       ("first_acc_ready_to_epilogue_done", "first_acc_ready", "epilogue_done"),
+                       ("dep_wait_to_epilogue_done", "dep_wait", "epilogue_done"),
+                       ("fixup", "fixup_start", "fixup_end"), ("cta_total", "entry", "exit")):
+        v, n = span(a, b)
+        out[name + "_ns"] = v
+        out[name + "_ctas"] = n
+    return out
+
+
+def single_shape_fp8(args, rg, torch):
+    """One FP8 GEMM configuration (N(0,1) operands block-quantised on the GPU): `reps` back-to-back
+    launches between CUDA events."""
+    M, N, K = args.shape
+    names = {rg.fp8_variant_name(v): v for v in range(rg.RG_FP8_VARIANT_BASE,
+                                                        rg.RG_FP8_VARIANT_BASE + rg.RG_FP8_NUM_VARIANTS)}
+    v = names[args.variant]
+    ctx = rg.rg_init(0)
+    xa = torch.from_numpy(synthetic.normal_stream_f32(0, synthetic.TAG_A, M * K)).cuda()
+    xb = torch.from_numpy(synthetic.normal_stream_f32(0, synthetic.TAG_B, K * N)).cuda()
+    qa = torch.empty(M * K, dtype=torch.uint8, device="cuda")
+    qb = torch.empty(K * N, dtype=torch.uint8, device="cuda")
+    sa = torch.empty(-(-M // 128) * -(-K // 128), device="cuda")
+    sb = torch.empty(-(-K // 128) * -(-N // 128), device="cuda")
+    rg.rg_fp8_quantize(ctx, xa, M, K, K, qa, K, sa)
+    rg.rg_fp8_quantize(ctx, xb, K, N, N, qb, N, sb)
+    C = torch.zeros((M, N), device="cuda")
+
+    def once():
+        rg.rg_gemm_fp8_ex(ctx, M, N, K, qa, K, sa, -(-K // 128), qb, N, sb, -(-N // 128), C, N, v)
+    for _ in range(3):
+        once()
+    rg.rg_check(ctx)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.reps):
+        once()
+    e1.record()
+    torch.cuda.synchronize()
+    rg.rg_check(ctx)
+    rg.rg_destroy(ctx)
+    us = e0.elapsed_time(e1) / args.reps * 1e3
+    print(json.dumps({"shape": [M, N, K], "variant": args.variant, "us_per_launch": us,
+                      "tflops": 2.0 * M * N * K / (us * 1e-6) / 1e12, "algorithmic_bytes": M * K + K * N + 4 * M * N,
+                      "algorithmic_flops": 2 * M * N * K}), flush=True)
+    return 0
+
+
 def single_shape(args):
-    """Time one GEMM configuration: `reps` back-to-back launches between CUDA events."""
+    """Time one GEMM configuration: `reps` back-to-back launches between CUDA events (and, with
+    --phase-timers, one traced launch of the phase-timer build)."""
+    if args.phase_timers:
+        os.environ["RG_LIBRARY"] = os.path.join(ROOT, "paper_2605_29752_gb300", "librg_timers.so")
     import torch
     from paper_2605_29752_gb300 import rg
     M, N, K = args.shape
+    if args.variant.startswith("fp8"):
+        return single_shape_fp8(args, rg, torch)
     names = {rg.variant_name(v): v for v in range(rg.RG_NUM_VARIANTS)}
     v = names[args.variant]
     a, b = synthetic.operands_bf16(M, N, K, seed=0)
@@ -79,12 +160,24 @@ def single_shape(args):
     torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     rg.rg_check(ctx)
+    phases = None
+    if args.phase_timers:
+        rg.rg_phase_trace(ctx, True)
+        for _ in range(5):          # back to back, as the sweep times them: the buffer keeps the last launch's
+            rg.rg_gemm(ctx, M, N, K, A, K, B, N, C, N, v)
+        torch.cuda.synchronize()
+        phases = phase_summary(rg.rg_phase_trace_read(ctx))
+        rg.rg_phase_trace(ctx, False)
     rg.rg_destroy(ctx)
     us = e0.elapsed_time(e1) / args.reps * 1e3
     tf = 2.0 * M * N * K / (us * 1e-6) / 1e12
     byts = 2 * M * K + 2 * K * N + 4 * M * N
-    print(json.dumps({"shape": [M, N, K], "variant": args.variant, "us_per_launch": us, "tflops": tf,
-                      "algorithmic_bytes": byts, "algorithmic_flops": 2 * M * N * K}), flush=True)
+    line = {"shape": [M, N, K], "variant": args.variant, "us_per_launch": us, "tflops": tf,
+            "algorithmic_bytes": byts, "algorithmic_flops": 2 * M * N * K}
+    if phases is not None:
+        line["phase_times"] = phases
+        line["library"] = "librg_timers.so (phase stamps compiled in; the timed launches carry them too)"
+    print(json.dumps(line), flush=True)
     return 0
 
 
@@ -176,6 +269,41 @@ def mean_over_ranks(value: float, dist=None, device=None) -> float:
     t = torch.tensor([float(value)], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.SUM)
     return float(t.item()) / dist.get_world_size()
+
+
+def device_header(device_name, sms, grid_counts, variant_ids, version):
+    """int64 header a rank sends beside its T0 shard: the merged table is valid only when every rank
+    swept the same grid and variants on the same kind of GPU with the same library."""
+    import hashlib
+
+    def h63(x):
+        return int.from_bytes(hashlib.sha256(str(x).encode()).digest()[:8], "little") >> 1
+    return np.array([h63(device_name), int(sms), *[int(c) for c in grid_counts], len(variant_ids),
+                     h63(list(variant_ids)), h63(version)], dtype=np.int64)
+
+
+def merge_t0_shards(local, header, dist, device=None, unmeasured=1 << 60, other=0):
+    """The exchange step of the sharded autotune sweep: all-gather every rank's header and int64 T0
+    shard, check that the headers agree, and merge.  Each (variant, cell) entry is measured on exactly
+    one rank (`other` elsewhere) or pruned on every rank (`unmeasured` everywhere)."""
+    import torch
+    world = dist.get_world_size()
+    h = torch.as_tensor(np.asarray(header, dtype=np.int64), device=device)
+    hs = [torch.empty_like(h) for _ in range(world)]
+    dist.all_gather(hs, h)
+    if any(not torch.equal(x, hs[0]) for x in hs):
+        raise RuntimeError("sharded sweep: the ranks' headers differ (GPU model, SM count, grid, variants or "
+                           "library); their timings cannot form one table")
+    t = torch.as_tensor(np.ascontiguousarray(local, dtype=np.int64), device=device)
+    ts = [torch.empty_like(t) for _ in range(world)]
+    dist.all_gather(ts, t)
+    stack = torch.stack(ts).cpu().numpy()
+    pruned = (stack == unmeasured).all(axis=0)
+    measured = (stack != other) & (stack != unmeasured)
+    count = measured.sum(axis=0)
+    if np.any((count != 1) & ~pruned):
+        raise RuntimeError("sharded sweep: some entries were measured on no rank or on several")
+    return np.where(pruned, unmeasured, np.where(measured, stack, 0).sum(axis=0)).astype(np.int64)
 
 
 def stats_of(rg, grid, t_ns):
@@ -459,10 +587,18 @@ def main():
     ctx = rg.rg_init(local)
     sms = rg.rg_sm_count(ctx)
 
-    # ---------------- offline autotune (setup)
+    # ---------------- offline autotune (setup); on several GPUs each rank times a shard of the
+    # (variant, cell) items and one all-gather of the int64 tables merges them
     t_setup = time.perf_counter()
     all_v = list(range(rg.RG_NUM_VARIANTS))
-    T0v = rg.rg_sweep(ctx, grid, all_v, A, B, C)
+    if world > 1:
+        o = rg.rg_sweep_opts_default()
+        o.shard_index, o.shard_count = rank, world
+        local_t = rg.rg_sweep(ctx, grid, all_v, A, B, C, o)
+        hdr = device_header(torch.cuda.get_device_name(dev), sms, (count, count, count), all_v, rg.rg_version())
+        T0v = merge_t0_shards(local_t, hdr, dist, dev, rg.RG_T_UNMEASURED, rg.RG_T_OTHER_SHARD)
+    else:
+        T0v = rg.rg_sweep(ctx, grid, all_v, A, B, C)
     s1_rows = [rg.variant(t, 1) for t in range(rg.RG_NUM_TILES)]
     plan_smooth = rg.rg_plan_build(grid, T0v, all_v)
     setup_s = time.perf_counter() - t_setup
@@ -555,7 +691,9 @@ def main():
                              "across their 5 launches, no flush); between timed steps: inputs larger than L2 (each "
                              "step reads all of A and B, 2 x 32 MiB, and writes all of C, 64 MiB: 134 MB against "
                              "the 129 MB L2, across 65,536 cell measurements)",
-                   "parallelism": "single GPU" if world == 1 else f"{world} independent replicas"},
+                   "parallelism": "single GPU" if world == 1 else
+                                  f"autotune sweep sharded over {world} GPUs (one int64 T0 all-gather); the timed "
+                                  f"landscape steps as {world} independent replicas"},
         "plain": {k: float(np.mean([p[k] for p in plain])) for k in plain[0]},
         "smoothed": {k: float(np.mean([s[k] for s in smooth])) for k in smooth[0]},
         "roughness_cut_pct": 100.0 * (1 - np.mean([s["R_N_slice"] for s in smooth]) /
@@ -727,8 +865,8 @@ def extras(args, rg, ctx, grid, T0v, plan_smooth, A, B, C, flops, Mv, Nv, Kv, de
     out["methodology"] = methodology(rg, ctx, grid, T0v, fixed_v, plan_smooth, A, B, C, dev, count)
     # ---- serving (continuous batching over the grouped GEMM), at half the saturated capacity
     out["serving"] = serving(rg, ctx, plan_smooth, A, B, count)
-    # ---- FP8 e4m3 block-scaled GEMM on the {512..4096 step 512}^3 subgrid
-    out["fp8"] = fp8_landscape(rg, ctx, dev, count)
+    # ---- FP8 e4m3 block-scaled GEMM on the {512..4096 step 512}^3 subgrid: autotune, plan, re-measure
+    out["fp8"], fp8_state = fp8_landscape(rg, ctx, dev, count, p_burst)
     # ---- e2e: host buffers through the public API (H2D, plan GEMM, D2H per cell)
     out["e2e"] = e2e(rg, ctx, plan_smooth, a_bits, b_bits, dev, count)
     # ---- the small sweep {128..512}^3 on the fixed tile (its own configuration)
@@ -741,6 +879,9 @@ def extras(args, rg, ctx, grid, T0v, plan_smooth, A, B, C, flops, Mv, Nv, Kv, de
         return Cc.cpu().numpy()
     # ---- CPU oracle baseline on this host (and the small sweep's full-matrix errors against it)
     out["cpu_baseline"] = cpu_baseline(count, gpu_config1=gpu_config1 if count >= 4 else None)
+    if fp8_state is not None:     # the FP8 plan's per-shape error against the oracle (CPU-baseline leg)
+        out["fp8"]["error_per_shape"] = fp8_errors(rg, ctx, fp8_state, dev)
+        rg.rg_plan_free(fp8_state["plan"])
     if count >= 4:
         out["small_sweep_config"]["max_error_ratio_vs_oracle"] = \
             out["cpu_baseline"]["small_sweep_64_cells"]["gpu_plain_max_error_ratio"]
@@ -946,11 +1087,14 @@ def serving(rg, ctx, plan, A, B, count, n_req=20000, n_warm=1000, tile=1):
             "note": "latency = host-observed completion - arrival; outputs from a 64 GB arena"}
 
 
-def fp8_landscape(rg, ctx, dev, count):
+def fp8_landscape(rg, ctx, dev, count, p_bf16):
+    """FP8 e4m3 block-scaled GEMM on the {512..4096 step 512}^3 subgrid: the autotune table over the
+    eight FP8 variants (128x256 and 128x128 tiles x split-K 1/2/4/8), the DP plan built from it, and
+    the plan re-measured.  Returns the report block and the state the error check needs."""
     import torch
     Mx = STEP * count
     if Mx < 512:
-        return None
+        return None, None
     xa = torch.from_numpy(synthetic.normal_stream_f32(0, synthetic.TAG_A, Mx * Mx)).to(dev)
     xb = torch.from_numpy(synthetic.normal_stream_f32(0, synthetic.TAG_B, Mx * Mx)).to(dev)
     nb = Mx // 128
@@ -960,13 +1104,89 @@ def fp8_landscape(rg, ctx, dev, count):
     sb = torch.empty(nb * nb, dtype=torch.float32, device=dev)
     rg.rg_fp8_quantize(ctx, xa, Mx, Mx, Mx, qa, Mx, sa)
     rg.rg_fp8_quantize(ctx, xb, Mx, Mx, Mx, qb, Mx, sb)
+    del xa, xb
     C = torch.empty(Mx * Mx, dtype=torch.float32, device=dev)
     g = rg.make_grid((512, 512, Mx // 512))
-    t = rg.rg_sweep_fp8(ctx, g, qa, sa, qb, sb, C)
-    tf, r, mean = rg.rg_surface_stats(g, t)
-    return {"grid": f"{{512..{Mx} step 512}}^3", "cells": int(t.size), **summarize(tf, r, mean),
-            "error": "per-shape error vs the FP64 oracle on the dequantised operands is checked in "
-                     "tests/test_gpu_fp8.py (observed max |C - C64| / sum|a||b| about 3e-8)"}
+    vids = [rg.fp8_variant(t, s) for t in range(rg.RG_FP8_NUM_TILES) for s in rg.SPLITS]
+    t, tf, st = rg.rg_sweep_fp8_surfaces(ctx, g, vids, qa, sa, qb, sb, C)
+    plan = rg.rg_plan_build(g, t, vids)
+    tp, tfp, stp = rg.rg_sweep_fp8_surfaces(ctx, g, [0], qa, sa, qb, sb, C, plan=plan)
+    cnt = Mx // 512
+    sizes = (np.arange(1, cnt + 1) * 512).astype(np.int64)
+    Mv, Nv, Kv = (x.ravel() for x in np.meshgrid(sizes, sizes, sizes, indexing="ij"))
+    p_fp8 = 2.0 * p_bf16                  # no measured FP8 peak: the nominal 2x of the measured BF16 burst
+    t_roof = 2.0 * Mv * Nv * Kv / (p_fp8 * 1e3)
+
+    def block(row_t, row_tf, row_st):
+        out = {k: float(row_st[i]) for i, k in enumerate(rg.SWEEP_STATS)}
+        out.update({"p50_tflops": float(np.percentile(row_tf, 50)), "max_tflops": float(row_tf.max()),
+                    "roofline_mean_frac_of_2x_bf16": float(np.mean(t_roof / row_t.astype(np.float64)))})
+        return out
+    tb = rg.rg_plan_tables(plan)
+    fixed = vids.index(rg.fp8_variant(0, 1))
+    best = t.min(axis=0)
+    _, btf, bst = rg.rg_surface_stats(g, best)
+    i4096 = int(np.argmax(Mv * Nv * Kv))
+    out = {"grid": f"{{512..{Mx} step 512}}^3", "cells": int(t.shape[1]),
+           "variants": [rg.fp8_variant_name(v) for v in vids],
+           "fixed_128x256": block(t[fixed], tf[fixed], st[fixed]),
+           "best_of_8_table": {"mean_tflops": float(bst), "R_N_slice": float(btf["R_N_slice"]),
+                               "R_3D": float(btf["R_3D"])},
+           "plan_measured": block(tp[0], tfp[0], stp[0]),
+           "winners": {rg.fp8_variant_name(v): float(np.mean(tb["vstar"].ravel() == v))
+                       for v in sorted(set(tb["vstar"].ravel().tolist()))},
+           "dp_actions": {a: float(np.mean(tb["action"] == i)) for i, a in enumerate(("keep", "M", "N", "K"))},
+           "tflops_4096cube": {"fixed_128x256": float(tf[fixed][i4096]), "plan": float(tfp[0][i4096])},
+           "peak_note": "FP8 roofline = 2 x the measured BF16 burst peak (the nominal ratio; no FP8 peak measured)",
+           "scales": "per-128x128-block FP32 scales; the sweep reads compact scale arrays for each cell's "
+                     "contiguous operand prefixes (timing only)"}
+    state = {"plan": plan, "qa": qa, "qb": qb, "sa": sa, "sb": sb, "Mx": Mx, "cells": list(zip(Mv, Nv, Kv)), "C": C}
+    return out, state
+
+
+def fp8_errors(rg, ctx, state, dev, rows_per_cell=16):
+    """Per-shape error of the FP8 plan against the oracle on every cell of the subgrid (CPU-baseline
+    leg).  Cell (M, N, K) is the top-left M x K block of the quantised 4096^2 A and K x N block of B
+    (lda = ldb = 4096, the whole scale arrays), so its 128 x 128 blocks and scales are exactly those
+    of quantising that block; max |C - C64| / sum|a||b| over the whole matrix for cells up to 1024^3,
+    over 16 seeded rows and 16 columns for larger ones."""
+    import torch
+    from oracle import fp8 as of
+    from oracle import gemm as og
+    Mx, plan = state["Mx"], state["plan"]
+    nb = Mx // 128
+    A = of.dequantize(state["qa"].cpu().numpy().reshape(Mx, Mx), state["sa"].cpu().numpy().reshape(nb, nb))
+    B = of.dequantize(state["qb"].cpu().numpy().reshape(Mx, Mx), state["sb"].cpu().numpy().reshape(nb, nb))
+    C = state["C"]
+    rs = np.random.default_rng(0)
+    ratios, worst = [], (0.0, None)
+    for M, N, K in state["cells"]:
+        M, N, K = int(M), int(N), int(K)
+        Cv = C[:M * N].view(M, N)
+        rg.rg_gemm_fp8_plan(ctx, plan, M, N, K, state["qa"], Mx, state["sa"], nb, state["qb"], Mx, state["sb"], nb,
+                            Cv, N)
+        rg.rg_check(ctx)
+        a, b = A[:M, :K], B[:K, :N]
+        if M * N * K <= 1024 ** 3:
+            ratio, ez = og.error_ratio(Cv.cpu().numpy(), a @ b, np.abs(a) @ np.abs(b))
+        else:
+            rows = rs.choice(M, rows_per_cell, replace=False)
+            cols = rs.choice(N, rows_per_cell, replace=False)
+            cr, sr, cc, sc = og.sampled_rows_cols(a, b, rows, cols)
+            r1, e1 = og.error_ratio(Cv[torch.as_tensor(rows, device=dev)].cpu().numpy(), cr, sr)
+            r2, e2 = og.error_ratio(Cv[:, torch.as_tensor(cols, device=dev)].cpu().numpy(), cc, sc)
+            ratio, ez = max(r1, r2), e1 and e2
+        ratio = ratio if ez else float("inf")
+        ratios.append(ratio)
+        if ratio > worst[0]:
+            worst = (ratio, [M, N, K])
+    ratios = np.array(ratios)
+    return {"cells": len(ratios), "max": float(ratios.max()), "median": float(np.median(ratios)),
+            "p99": float(np.percentile(ratios, 99)), "worst_shape": worst[1],
+            "bound_used_in_tests": "4 K 2^-24", "max_over_K_2^-24": float(max(
+                r / (int(K) * 2.0 ** -24) for r, (_, _, K) in zip(ratios, state["cells"]))),
+            "definition": "max |C - C64| / sum_k |a_ik||b_kj| against the float64 product of the dequantised "
+                          "operands; whole matrix up to 1024^3, else 16 seeded rows and 16 columns"}
 
 
 def e2e(rg, ctx, plan, a_bits, b_bits, dev, count, ncells=96):

@@ -66,10 +66,11 @@ enum {
 };
 #define RG_NUM_SPLITS 4
 #define RG_VARIANT(tile, log2_split) ((tile) * RG_NUM_SPLITS + (log2_split))
-/* Stream-K variant of a tile (ids 24..29, after the split-K ids): the launch's
- * tiles x K-blocks iterations are divided evenly among at most one CTA per SM
- * (each CTA at least 4 K blocks); a tile whose iterations span several CTAs is
- * summed by its last arriving piece in the fixed order of their K ranges. */
+/* Stream-K variant of a tile (ids 24..29, after the split-K ids): whole waves of
+ * tiles run data-parallel; the remainder tiles' K iterations are divided evenly
+ * among at most one CTA per SM (each CTA at least 4 K blocks, at most 2 CTAs per
+ * tile); a tile whose iterations span two CTAs is summed by its last arriving
+ * piece in the fixed order of their K ranges. */
 #define RG_VARIANT_SK(tile) (RG_NUM_TILES * RG_NUM_SPLITS + (tile))
 /* 2-SM variant of a 256-row tile (ids 30..33 for 256x128, 34..37 for 256x256,
  * split-K 1/2/4/8): a 2-CTA cluster computes one 256 x BN tile as a single
@@ -84,7 +85,7 @@ enum {
 /* cta_group::2 stream-K variant of a 256-row tile (id 38 for 256x128, 39 for
  * 256x256): whole waves of 256 x BN pair tiles run data-parallel on the 2-CTA
  * clusters; the remainder tiles' K iterations are divided evenly among at most
- * one cluster per SM pair (each at least 4 K blocks, at most 4 clusters per
+ * one cluster per SM pair (each at least 4 K blocks, at most 2 clusters per
  * tile), and each CTA of a cluster sums its own 128 rows of a shared tile in
  * the fixed order of the pieces' K ranges.  It removes the partial last wave
  * that quantises the large cells (Sec. 9.4 names split-K as the remedy). */
@@ -132,8 +133,18 @@ typedef struct {
                                  where there is no whole wave or the remainder is not
                                  spread over more CTAs than it has tiles;
                                  cta_group::2 pairs with M <= 128                     */
+  int32_t shard_index;        /* with shard_count > 1: this call times only the items at
+                                 positions shard_index, shard_index + shard_count, ... of
+                                 the randomised, pruned order (identical on identical GPUs
+                                 with the same seed) and sets every other measured entry
+                                 to RG_T_OTHER_SHARD, so the shards of several GPUs merge
+                                 into the whole table (Sec. 3 sweep split over GPUs);
+                                 default 0                                             */
+  int32_t shard_count;        /* default 1 (no sharding)                             */
   int32_t reserved;
 } rg_sweep_opts;
+/* Entry of a (variant, cell) pair another shard of a sharded sweep times. */
+#define RG_T_OTHER_SHARD ((int64_t)0)
 /* Time entry of a (variant, cell) pair the sweep did not measure: larger than
  * any real time, so best-of selection never picks it. */
 #define RG_T_UNMEASURED ((int64_t)1 << 60)
@@ -176,6 +187,21 @@ int rg_set_static_operands(rg_ctx* ctx, int32_t enable);
  * lets its in-flight copies land, releases TMEM and returns, and rg_check
  * reports RG_ERR_TIMEOUT.  Off by default. */
 int rg_set_test_stall(rg_ctx* ctx, int32_t enable);
+/* Phase timers, a compile-time option of the library (built with RG_PHASE_TIMERS=1,
+ * e.g. `python -m paper_2605_29752_gb300.build --phase-timers`): while enabled,
+ * every BF16 GEMM launch of this context writes per-CTA stamps into a buffer the
+ * context owns (each launch overwrites it), kTraceFields = 12 uint64 per CTA:
+ *   0 globaltimer at entry (ns), 1 globaltimer at exit (ns), 2 SM clock at exit,
+ *   3 dependency wait done, 4 first operand stage landed, 5 last MMA commit,
+ *   6 first accumulator ready in the epilogue, 7 epilogue done,
+ *   8 first split-K fixup start, 9 split-K fixup end, 10 work units of the CTA,
+ * SM-clock fields counted in cycles from the CTA's entry (0 = not reached).
+ * rg_phase_trace_read synchronises the device, copies the records of up to
+ * max_ctas CTAs (the SM count at most) to `out` and clears the buffer.  In a
+ * library built without the option both return RG_ERR_INVALID. */
+#define RG_TRACE_FIELDS 12
+int rg_phase_trace(rg_ctx* ctx, int32_t enable);
+int rg_phase_trace_read(rg_ctx* ctx, uint64_t* out, int32_t max_ctas, int32_t* n_ctas);
 /* Number of kernel launches this context has enqueued so far (GEMM kernels and
  * the sweep's spin kernels). */
 int rg_launch_count(const rg_ctx* ctx, int64_t* out);
@@ -195,7 +221,8 @@ int rg_gemm(rg_ctx* ctx, int64_t M, int64_t N, int64_t K,
 
 /* ---- plan table (Sec. 7.1, host) ----
  * T0_ns: [n_variants][cells] int64 nanoseconds (cells in the grid's linear
- * order), variant_ids[v] the library variant measured in row v.  Builds
+ * order), variant_ids[v] the library variant measured in row v: BF16 ids
+ * (0..RG_NUM_VARIANTS-1) or FP8 ids (RG_FP8_VARIANT_BASE..), not both.  Builds
  * best-of selection, T1 (padding), T2 (splitting) and every cell's leaf list.
  * The grid must have start == step on every axis (whole multiples of the step),
  * except with RG_PLAN_PAD_ONLY, where any grid is accepted (padding moves to a
@@ -269,10 +296,10 @@ int rg_surface_stats(const rg_grid* grid, const int64_t* t_ns, double* tflops_ou
  * call must not write overlapping parts of C (they may run concurrently).
  * A result is bitwise that of rg_gemm with the same variant (same split
  * boundaries and summation order), whatever else the call contains.
- * rg_group_create allocates the workspace and tickets.  A family's first use
- * allocates kGroupSlots = 4 slots of work lists (pinned host + device, for
- * max_items problems each) and instantiates one CUDA graph per slot:
- * [copy the host list to the device list, grouped kernel].  rg_gemm_grouped
+ * rg_group_create allocates the workspace and tickets and, for each family,
+ * kGroupSlots = 4 slots of work lists (pinned host + device, for max_items
+ * problems each), instantiating one CUDA graph per slot: [copy the host list
+ * to the device list, grouped kernel].  rg_gemm_grouped allocates nothing: it
  * fills the next slot of each family it uses (waiting first until that slot's
  * replay from 4 launches ago has finished), then replays its graph on `stream`;
  * the call returns without waiting for the GEMMs.  Operand conventions and
@@ -335,7 +362,15 @@ typedef struct {
   int32_t max_inflight;       /* batches on the GPU at once, 1..16; default 2 */
   int32_t tile;               /* tile for requests without a plan; default RG_TILE_128x128 */
   int32_t workspace_mib;      /* split-K workspace of each in-flight slot, MiB; default 256 */
+  const rg_plan* fp8_plan;    /* plan for FP8 requests (FP8 variant ids), or NULL: one 128x256 leaf */
 } rg_serve_opts;
+/* Request precision: BF16 operands A, B (the default), or FP8 e4m3 operands with
+ * per-128x128-block FP32 scales (A = qA, B = qB; sA, sB and their leading
+ * dimensions as rg_gemm_fp8_ex).  An FP8 request goes through opts->fp8_plan and
+ * its leaves run on the batch's stream after that phase's grouped BF16 launch;
+ * its operand bytes are MK + KN + 4MN plus the scales. */
+#define RG_DTYPE_BF16 0
+#define RG_DTYPE_FP8 1
 typedef struct {
   int64_t M, N, K;
   const void* A;
@@ -345,6 +380,12 @@ typedef struct {
   float* C;
   int64_t ldc;
   int64_t arrival_ns;
+  int32_t dtype;              /* RG_DTYPE_BF16 or RG_DTYPE_FP8 */
+  int32_t reserved;
+  const float* sA;            /* FP8 only */
+  int64_t lds_a;
+  const float* sB;            /* FP8 only */
+  int64_t lds_b;
 } rg_serve_request;
 typedef struct {
   int64_t admitted_ns, launched_ns, done_ns;
@@ -373,23 +414,54 @@ int rg_serve_stop(rg_server* server, rg_serve_stats* stats);
  * [ceil(rows/128)][ceil(cols/128)] (row-major, FP32): per block amax, s = amax / 448
  * (IEEE division; s = 1 for an all-zero block), Q = e4m3(x / s) rounded to nearest
  * even with saturation to +-448.
- * rg_gemm_fp8: C (M x N FP32, ldc) = sum over 128-deep K blocks kb of
+ * FP8 GEMM: C (M x N FP32, ldc) = sum over 128-deep K blocks kb of
  * sA[i/128][kb] * sB[kb][j/128] * (qA * qB restricted to kb), FP32 accumulation;
- * qA M x K e4m3 (lda), sA [ceil(M/128)][ceil(K/128)], qB K x N e4m3 (ldb),
- * sB [ceil(K/128)][ceil(N/128)], as produced by rg_fp8_quantize.  qA, qB, C 16-byte
- * aligned; lda, ldb multiples of 16; ldc a multiple of 4.  Device pointers, stream-ordered. */
+ * qA M x K e4m3 (lda), sA [ceil(M/128)] rows of lds_a >= ceil(K/128) scales,
+ * qB K x N e4m3 (ldb), sB [ceil(K/128)] rows of lds_b >= ceil(N/128) scales, as
+ * produced by rg_fp8_quantize.  qA, qB, C 16-byte aligned; lda, ldb multiples of
+ * 16; ldc a multiple of 4.  Device pointers, stream-ordered.
+ * FP8 kernel variants (ids in their own range, RG_FP8_VARIANT_BASE + ...): the
+ * 128 x 256 and 128 x 128 output tiles (FP8 tile 0 and 1), each with in-kernel
+ * split-K S = 1/2/4/8, id = RG_FP8_VARIANT(tile, log2(S)).  Split-K partials go
+ * through the context's workspace and are summed by the last arriving split in
+ * the fixed order 0..S-1, so results are deterministic.
+ * rg_gemm_fp8_ex: one launch of `variant`, beta = 0 writes C, beta = 1 adds into
+ * it; (pm, pn, pk) >= (M, N, K) run it as the zero-padded problem of that size (0
+ * = same), never materialised (zero-filled reads, clipped stores, scales of
+ * padding blocks read as 0).  Errors as rg_gemm (RG_ERR_SHAPE when split-K
+ * partials exceed the workspace).  rg_gemm_fp8 = rg_gemm_fp8_ex with variant
+ * RG_FP8_VARIANT(0, 0), compact scales (lds_a = ceil(K/128), lds_b = ceil(N/128)),
+ * beta 0 and no padding.
+ * rg_gemm_fp8_plan: the O(1) plan lookup (Sec. 7.1) of an FP8 plan (a plan built
+ * by rg_plan_build from FP8 variant ids), then the cell's leaves in order, each
+ * on the sub-views of qA, sA, qB, sB and C its box selects; the boxes' offsets
+ * must be multiples of 128 (grid steps that are), else RG_ERR_SHAPE.  A BF16
+ * plan is refused (RG_ERR_INVALID), as rg_gemm_plan refuses an FP8 plan. */
+#define RG_FP8_VARIANT_BASE 64
+#define RG_FP8_NUM_TILES 2
+#define RG_FP8_VARIANT(tile, log2_split) (RG_FP8_VARIANT_BASE + (tile) * RG_NUM_SPLITS + (log2_split))
+#define RG_FP8_NUM_VARIANTS (RG_FP8_NUM_TILES * RG_NUM_SPLITS)
 int rg_fp8_quantize(rg_ctx* ctx, const float* X, int64_t rows, int64_t cols, int64_t ldx, uint8_t* Q,
                     int64_t ldq, float* scales, void* stream);
 int rg_gemm_fp8(rg_ctx* ctx, int64_t M, int64_t N, int64_t K, const uint8_t* qA, int64_t lda, const float* sA,
                 const uint8_t* qB, int64_t ldb, const float* sB, float* C, int64_t ldc, void* stream);
-/* Times rg_gemm_fp8 on every cell of `grid` with the sweep protocol of rg_sweep
- * (same options; split pruning does not apply).  Cell (M, N, K) uses the
- * contiguous prefixes qA[0 : M*K] (lda = K) and qB[0 : K*N] (ldb = N) with
+int rg_gemm_fp8_ex(rg_ctx* ctx, int64_t M, int64_t N, int64_t K, const uint8_t* qA, int64_t lda, const float* sA,
+                   int64_t lds_a, const uint8_t* qB, int64_t ldb, const float* sB, int64_t lds_b, float* C,
+                   int64_t ldc, int32_t variant, int32_t beta, int64_t pm, int64_t pn, int64_t pk, void* stream);
+int rg_gemm_fp8_plan(rg_ctx* ctx, const rg_plan* plan, int64_t M, int64_t N, int64_t K, const uint8_t* qA,
+                     int64_t lda, const float* sA, int64_t lds_a, const uint8_t* qB, int64_t ldb, const float* sB,
+                     int64_t lds_b, float* C, int64_t ldc, void* stream);
+/* Times FP8 GEMMs on every cell of `grid` with the sweep protocol and outputs of
+ * rg_sweep (same options; split pruning as rg_sweep's for split-K): n_variants
+ * FP8 variant ids, or a plan (n_variants = 1, ids ignored).  Cell (M, N, K) uses
+ * the contiguous prefixes qA[0 : M*K] (lda = K) and qB[0 : K*N] (ldb = N) with
  * compact scale arrays read from sA and sB (they must hold the largest cell's
  * blocks); C holds max M * max N floats.  Grid sizes must be multiples of 16.
- * t_ns_out[cell] as in rg_sweep. */
-int rg_sweep_fp8(rg_ctx* ctx, const rg_grid* grid, const uint8_t* qA, const float* sA, const uint8_t* qB,
-                 const float* sB, float* C, const rg_sweep_opts* opts, int64_t* t_ns_out, void* stream);
+ * t_ns_out[v][cell], tflops_out[v][cell] and stats_out[v][6] as in rg_sweep. */
+int rg_sweep_fp8(rg_ctx* ctx, const rg_grid* grid, int32_t n_variants, const int32_t* variant_ids,
+                 const rg_plan* plan, const uint8_t* qA, const float* sA, const uint8_t* qB, const float* sB,
+                 float* C, const rg_sweep_opts* opts, int64_t* t_ns_out, double* tflops_out, double* stats_out,
+                 void* stream);
 
 /* ---- first-principles landscapes (Sec. 9.1, 9.2) and kernel grading (Sec. 10; host) ----
  * out[cell] = achieved TFLOP/s of the analytic landscape on `grid`:
@@ -421,7 +493,7 @@ int rg_kol(double mean_a, double mean_o, double r_a, double r_o, double out[2], 
  * tflops_out[v][cell] and stats_out[v][6] = {R_M, R_N, R_K, R_3D, R_N on the
  * largest-K slice, mean TFLOP/s}, exactly as rg_surface_stats computes them
  * from t_ns_out (correctly rounded sums).  A row with cells the pruning left
- * unmeasured has TFLOP/s 0 there and NaN statistics.  Either pointer may be
+ * unmeasured (or another shard times) has TFLOP/s 0 there and NaN statistics.  Either pointer may be
  * NULL.  Synchronises; returns RG_ERR_TIMEOUT if a kernel gave up a wait. */
 int rg_sweep(rg_ctx* ctx, const rg_grid* grid, int32_t n_variants, const int32_t* variant_ids,
              const rg_plan* plan, const void* A, const void* B, float* C,

@@ -20,6 +20,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "librg.so")
+LIB_TIMERS = os.path.join(PKG, "librg_timers.so")
 
 CUDA_SOURCES = ["rg_gemm.cu", "rg_fp8.cu", "rg_grouped.cu"]
 CXX_SOURCES = ["rg_plan.cpp", "rg_stats.cpp", "rg_serve.cpp"]
@@ -37,35 +38,39 @@ def _cuda_include(nvcc: str) -> str:
     return os.path.join(os.path.dirname(os.path.dirname(os.path.realpath(nvcc))), "include")
 
 
-def commands(debug: bool = False):
+def commands(debug: bool = False, phase_timers: bool = False):
     nvcc = _nvcc()
     cinc = _cuda_include(nvcc)
     opt = ["-O0", "-g"] if debug else ["-O3"]
+    build_dir = BUILD + ("_timers" if phase_timers else "")
+    lib = LIB_TIMERS if phase_timers else LIB
+    defs = ["-DRG_PHASE_TIMERS=1"] if phase_timers else []
     cmds = []
     objs = []
     for src in CUDA_SOURCES:
         path = os.path.join(CSRC, src)
         if not os.path.exists(path):
             continue
-        obj = os.path.join(BUILD, src + ".o")
-        cmds.append([nvcc, *ARCH, *opt, "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
+        obj = os.path.join(build_dir, src + ".o")
+        cmds.append([nvcc, *ARCH, *opt, *defs, "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
                      "-Xcompiler", "-ffp-contract=off", "-I", INCLUDE, "-I", CSRC, "-c", path, "-o", obj])
         objs.append(obj)
     for src in CXX_SOURCES:
         path = os.path.join(CSRC, src)
         if not os.path.exists(path):
             continue
-        obj = os.path.join(BUILD, src + ".o")
+        obj = os.path.join(build_dir, src + ".o")
         cmds.append(["g++", *opt, "-std=c++17", "-fPIC", "-ffp-contract=off", "-fno-fast-math", "-Wall",
                      "-I", INCLUDE, "-I", CSRC, "-I", cinc, "-pthread", "-c", path, "-o", obj])
         objs.append(obj)
-    link = [nvcc, *ARCH, "-shared", "-cudart", "static", "-o", LIB, *objs, "-lpthread", "-ldl", "-lrt"]
-    return cmds, link
+    link = [nvcc, *ARCH, "-shared", "-cudart", "static", "-o", lib, *objs, "-lpthread", "-ldl", "-lrt"]
+    return cmds, link, build_dir, lib
 
 
-def build(verbose: bool = False, debug: bool = False) -> str:
-    os.makedirs(BUILD, exist_ok=True)
-    cmds, link = commands(debug)
+def build(verbose: bool = False, debug: bool = False, phase_timers: bool = False) -> str:
+    """Build librg.so (or, with phase_timers, the instrumented librg_timers.so beside it)."""
+    cmds, link, build_dir, lib = commands(debug, phase_timers)
+    os.makedirs(build_dir, exist_ok=True)
     procs = []
     for c in cmds:
         if verbose:
@@ -81,14 +86,14 @@ def build(verbose: bool = False, debug: bool = False) -> str:
     if failed:
         msg = "\n\n".join(" ".join(c) + "\n" + out for c, out in failed)
         raise RuntimeError("librg build failed:\n" + msg)
-    tmp = LIB + ".tmp"
-    link = [tmp if x == LIB else x for x in link]
+    tmp = lib + ".tmp"
+    link = [tmp if x == lib else x for x in link]
     r = subprocess.run(link, stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True)
     if r.returncode != 0:
         raise RuntimeError("librg link failed:\n" + " ".join(link) + "\n" + r.stdout)
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(verbose="-v" in sys.argv, debug="--debug" in sys.argv))
+    print(build(verbose="-v" in sys.argv, debug="--debug" in sys.argv, phase_timers="--phase-timers" in sys.argv))

@@ -53,6 +53,33 @@ constexpr long long kDrainCycles = 1LL << 30;
 
 enum : int { kErrProducer = 1, kErrMma = 2, kErrEpilogue = 3 };
 
+// Phase stamps, a compile-time option (RG_PHASE_TIMERS=1): per CTA, fields
+//   0 globaltimer at entry (ns)     1 globaltimer at exit (ns)     2 clock64 at exit
+//   3 dependency wait done          4 first operand stage landed   5 last MMA commit
+//   6 first accumulator ready       7 epilogue done                8 first split-K fixup start
+//   9 last split-K fixup end        10 work units of the CTA
+// with every clock64 field counted from the CTA's entry.  Without the option the
+// stamps compile to nothing.
+constexpr int kTraceFields = 12;
+#ifndef RG_PHASE_TIMERS
+#define RG_PHASE_TIMERS 0
+#endif
+#if RG_PHASE_TIMERS
+#define RG_STAMP(f)                                                                       \
+  do {                                                                                    \
+    if (trace_row) trace_row[f] = static_cast<unsigned long long>(clock64() - t_entry);   \
+  } while (0)
+#else
+#define RG_STAMP(f) \
+  do {              \
+  } while (0)
+#endif
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
 struct GemmArgs {
   int32_t M, N;             // logical output extents
   int32_t tiles_m, tiles_n; // tiles of the (padded) launch
@@ -68,6 +95,7 @@ struct GemmArgs {
   int32_t* tickets;         // [tile][4], zero between launches
   int32_t* err;
   long long timeout;        // cycles per wait
+  unsigned long long* trace;  // phase stamps [CTA][kTraceFields] (RG_PHASE_TIMERS builds), or null
 };
 
 // CTAS = 2: one CTA of a cta_group::2 pair (BM = 128 rows of its own, BN / 2
@@ -191,11 +219,15 @@ __device__ __forceinline__ Unit split_unit(const CUtensorMap* a, const CUtensorM
   return x;
 }
 
-// One problem whose tensor maps are kernel parameters (rg_gemm).
+// One problem whose tensor maps are kernel parameters (rg_gemm).  SPLIT: the
+// instance for split-K launches (S > 1); without it the kernel carries no
+// reduction path (and none of its register pressure).
+template <bool SPLIT>
 struct SingleSched {
   static constexpr bool kMapsInGlobal = false;
   static constexpr bool kMemOnly = false;
   static constexpr bool k2Sm = false;
+  static constexpr bool kSplit = SPLIT;
   static constexpr int rank = 0;
   const CUtensorMap* a;
   const CUtensorMap* b;
@@ -224,7 +256,7 @@ struct SingleSched {
 // The memory twin of SingleSched: the same units, loads and stores, with the
 // MMAs replaced by no-ops (the memory surface of the four-surface decomposition,
 // Sec. 4).  Its output is whatever the accumulators held: timing only.
-struct MemTwinSched : SingleSched {
+struct MemTwinSched : SingleSched<false> {
   static constexpr bool kMemOnly = true;
 };
 
@@ -245,6 +277,7 @@ struct StreamKSched {
   static constexpr bool kMapsInGlobal = false;
   static constexpr bool kMemOnly = false;
   static constexpr bool k2Sm = TWO_SM;
+  static constexpr bool kSplit = true;
   const CUtensorMap* a;
   const CUtensorMap* b;
   const CUtensorMap* c;
@@ -342,10 +375,12 @@ struct StreamKSched {
 // memory, and the even CTA issues the MMAs for both.  A CTA whose rows fall
 // outside the problem still loads (zero-filled reads) so that the pair's MMAs
 // are fed; its stores are dropped.  Units are (pair tile, K split).
+template <bool SPLIT>
 struct TwoSmSched {
   static constexpr bool kMapsInGlobal = false;
   static constexpr bool kMemOnly = false;
   static constexpr bool k2Sm = true;
+  static constexpr bool kSplit = SPLIT;
   const CUtensorMap* a;
   const CUtensorMap* b;
   const CUtensorMap* c;
@@ -421,6 +456,7 @@ struct GroupSched {
   static constexpr bool kMapsInGlobal = true;
   static constexpr bool kMemOnly = false;
   static constexpr bool k2Sm = TWO_SM;
+  static constexpr bool kSplit = true;
   const GroupHeader* h;
   const GroupItem* items;
   const CUtensorMap* w;      // the launch's split-K workspace
@@ -481,7 +517,14 @@ struct GroupSched {
 
 template <int BM, int BN, int STAGES, class Sched>
 __device__ __forceinline__ void gemm_body(Sched& sched, float* ws, int32_t* tickets, int32_t* err, long long timeout,
-                                          int stall, int early) {
+                                          int stall, int early, unsigned long long* trace = nullptr) {
+#if RG_PHASE_TIMERS
+  const long long t_entry = clock64();
+  unsigned long long* trace_row = trace ? trace + static_cast<size_t>(blockIdx.x) * kTraceFields : nullptr;
+  if (trace_row && threadIdx.x == 0) trace_row[0] = global_ns();
+#else
+  (void)trace;
+#endif
   constexpr bool P2 = Sched::k2Sm;  // one CTA of a cta_group::2 pair
   using C = KCfg<BM, BN, STAGES, P2 ? 2 : 1>;
   extern __shared__ uint8_t smem_raw[];
@@ -549,6 +592,12 @@ __device__ __forceinline__ void gemm_body(Sched& sched, float* ws, int32_t* tick
   grid_launch_dependents();
   if constexpr (Sched::kMapsInGlobal) sched.init();
   const int nunits = sched.count();
+  if (threadIdx.x == 0) {
+    RG_STAMP(3);
+#if RG_PHASE_TIMERS
+    if (trace_row) trace_row[10] = static_cast<unsigned long long>(nunits);
+#endif
+  }
 
   if (warp == 0) {
     // ------------------------------------------------ TMA producer (one thread)
@@ -634,6 +683,7 @@ __device__ __forceinline__ void gemm_body(Sched& sched, float* ws, int32_t* tick
         for (int kb = kb0; kb < kb1; ++kb) {
           ok = mbar_wait(full_bar(stage), ph, timeout, abort_flag);
           if (!ok) break;
+          if (i == 0 && kb == kb0) RG_STAMP(4);
           tc_fence_after();
           if constexpr (Sched::kMemOnly) {
             mbar_arrive(empty_bar(stage));  // no MMA reads the stage: it is free once its bytes have landed
@@ -679,6 +729,7 @@ __device__ __forceinline__ void gemm_body(Sched& sched, float* ws, int32_t* tick
           acc = 0;
           aph ^= 1u;
         }
+        if (i + 1 == issue_units) RG_STAMP(5);
       }
       if (!ok) {
         atomicExch(err, kErrMma);
@@ -696,6 +747,9 @@ __device__ __forceinline__ void gemm_body(Sched& sched, float* ws, int32_t* tick
     if (early) grid_dependency_wait();
     const int q = warp & 3;  // TMEM lanes 32q..32q+31 are the ones this warp may read
     const uint32_t stg0 = sbase + C::STAGING_OFF + (warp - 2) * kStagingPerWarp;
+#if RG_PHASE_TIMERS
+    bool fixup_seen = false;  // this launch has stamped its first split-K fixup
+#endif
     int acc = 0, sbuf = 0;
     uint32_t aph = 0;
     bool ok = true;
@@ -707,10 +761,11 @@ __device__ __forceinline__ void gemm_body(Sched& sched, float* ws, int32_t* tick
       }
       ok = __all_sync(FULL, mbar_wait(tfull_bar(acc), aph, timeout, abort_flag));
       if (!ok) break;
+      if (i == 0 && warp == 2 && lane == 0) RG_STAMP(6);
       tc_fence_after();
       const bool have = kb1 > kb0;
       const uint32_t tacc = tmem_base + (static_cast<uint32_t>(q * 32) << 16) + static_cast<uint32_t>(acc * C::ACC_COLS);
-      if (w.splits == 1) {
+      if (!Sched::kSplit || w.splits == 1) {
 #pragma unroll 1
         for (int h = 0; h < C::HALVES; ++h)
 #pragma unroll 1
@@ -720,7 +775,7 @@ __device__ __forceinline__ void gemm_body(Sched& sched, float* ws, int32_t* tick
             store_block(w.c, v, tm * BM + h * 128 + q * 32, tn * BN + c * 32, w.M, w.N, w.beta, stg0, sbuf,
                         lane);
           }
-      } else {
+      } else if constexpr (Sched::kSplit) {
         // Split-K.  Publish this split's FP32 partial tile: TMEM -> swizzled staging ->
         // TMA store into the workspace (rows (s * ntiles + tile) * BM ..), then wait
         // for the stores, fence them against the generic proxy and take the ticket
@@ -747,6 +802,12 @@ __device__ __forceinline__ void gemm_body(Sched& sched, float* ws, int32_t* tick
           if (last) *t = 0;
         }
         last = __shfl_sync(FULL, last, 0);
+#if RG_PHASE_TIMERS
+        if (last && warp == 2 && lane == 0 && !fixup_seen) {
+          RG_STAMP(8);
+          fixup_seen = true;
+        }
+#endif
         if (last) {
           // The last arriver sums the S partials of each 32 x 32 block in the fixed
           // order 0..S-1.  Lane l holds block rows 4j + l/8 (j = 0..7), columns
@@ -755,6 +816,73 @@ __device__ __forceinline__ void gemm_body(Sched& sched, float* ws, int32_t* tick
           // one row per lane) is brought into that layout through the staging buffer.
           constexpr int kBatch = 3;
           const int rsub = lane >> 3, g = lane & 7;
+          if (w.splits == 2) {
+            // Two pieces (split 2, every stream-K tail tile): the other piece's partial of the
+            // next 32 x 32 block is loaded while this block is reduced, hiding the load latency;
+            // own + other is the same sum in either order, so the result is that of the fixed order.
+            const int other = 1 - s;
+            constexpr int kChunks = C::HALVES * (BN / 32);
+            auto src_of = [&](int ch) {
+              return ws + static_cast<size_t>(w.ws_row0 + (other * ntiles + tile) * BM + (ch / (BN / 32)) * 128 +
+                                              q * 32) * BN + (ch % (BN / 32)) * 32 + 4 * g;
+            };
+            float4 nxt[8];
+            {
+              const float* src = src_of(0);
+#pragma unroll
+              for (int j = 0; j < 8; ++j)
+                nxt[j] = __ldcg(reinterpret_cast<const float4*>(src + static_cast<size_t>(4 * j + rsub) * BN));
+            }
+#pragma unroll 1
+            for (int ch = 0; ch < kChunks; ++ch) {
+              const int h = ch / (BN / 32), c = ch % (BN / 32);
+              float4 cur[8];
+#pragma unroll
+              for (int j = 0; j < 8; ++j) cur[j] = nxt[j];
+              if (ch + 1 < kChunks) {
+                const float* src = src_of(ch + 1);
+#pragma unroll
+                for (int j = 0; j < 8; ++j)
+                  nxt[j] = __ldcg(reinterpret_cast<const float4*>(src + static_cast<size_t>(4 * j + rsub) * BN));
+              }
+              float own[32];
+              load_acc(tacc + h * BN + c * 32, have, own);
+              if (lane == 0) bulk_wait_read<1>();
+              __syncwarp();
+              const uint32_t buf = stg0 + sbuf * 4096;
+#pragma unroll
+              for (int j = 0; j < 8; ++j)
+                st_shared_v4(buf + lane * 128 + ((j ^ (lane & 7)) << 4), own[4 * j], own[4 * j + 1], own[4 * j + 2],
+                             own[4 * j + 3]);
+              __syncwarp();
+              float4 sum[8];
+#pragma unroll
+              for (int j = 0; j < 8; ++j) {
+                const int r = 4 * j + rsub;
+                const float4 o = ld_shared_v4(buf + r * 128 + ((g ^ (r & 7)) << 4));
+                sum[j] = make_float4(o.x + cur[j].x, o.y + cur[j].y, o.z + cur[j].z, o.w + cur[j].w);
+              }
+              __syncwarp();
+#pragma unroll
+              for (int j = 0; j < 8; ++j) {
+                const int r = 4 * j + rsub;
+                st_shared_v4(buf + r * 128 + ((g ^ (r & 7)) << 4), sum[j].x, sum[j].y, sum[j].z, sum[j].w);
+              }
+              fence_proxy_async_smem();
+              __syncwarp();
+              const int row0 = tm * BM + h * 128 + q * 32, col0 = tn * BN + c * 32;
+              if (row0 < w.M && col0 < w.N) {
+                if (lane == 0) {
+                  if (w.beta)
+                    tma_reduce_add_2d(w.c, buf, col0, row0);
+                  else
+                    tma_store_2d(w.c, buf, col0, row0);
+                  bulk_commit();
+                }
+                sbuf ^= 1;
+              }
+            }
+          } else
 #pragma unroll 1
           for (int h = 0; h < C::HALVES; ++h)
 #pragma unroll 1
@@ -828,6 +956,9 @@ __device__ __forceinline__ void gemm_body(Sched& sched, float* ws, int32_t* tick
             }
         }
       }
+#if RG_PHASE_TIMERS
+      if (w.splits > 1 && warp == 2 && lane == 0 && fixup_seen) RG_STAMP(9);
+#endif
       tc_fence_before();
       __syncwarp();
       if (lane == 0) {
@@ -849,9 +980,16 @@ __device__ __forceinline__ void gemm_body(Sched& sched, float* ws, int32_t* tick
     // themselves complete with the grid (a dependent grid's griddepcontrol.wait sees them)
     if (lane == 0) bulk_wait_read<0>();
     __syncwarp();
+    if (warp == 2 && lane == 0) RG_STAMP(7);
   }
 
   __syncthreads();
+#if RG_PHASE_TIMERS
+  if (trace_row && threadIdx.x == 0) {
+    trace_row[1] = global_ns();
+    RG_STAMP(2);
+  }
+#endif
   // no CTA of a pair exits while its partner may still arrive on its barriers or
   // run MMAs on its shared memory and TMEM
   if constexpr (P2) cluster_sync();
@@ -865,15 +1003,15 @@ __device__ __forceinline__ void gemm_body(Sched& sched, float* ws, int32_t* tick
 }
 
 
-template <int BM, int BN, int STAGES>
+template <int BM, int BN, int STAGES, bool SPLIT>
 __global__ void __launch_bounds__(kThreads, 1)
     gemm_bf16_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                      const __grid_constant__ CUtensorMap tmC, const __grid_constant__ CUtensorMap tmW,
                      const GemmArgs args) {
-  SingleSched sched{&tmA,        &tmB,          &tmC,   &tmW,  args.tiles_m, args.tiles_n,
-                    args.splits, args.kblocks, args.M, args.N, args.beta};
+  SingleSched<SPLIT> sched{&tmA,        &tmB,          &tmC,   &tmW,  args.tiles_m, args.tiles_n,
+                           args.splits, args.kblocks, args.M, args.N, args.beta};
   sched.panel = args.panel;
-  gemm_body<BM, BN, STAGES>(sched, args.ws, args.tickets, args.err, args.timeout, args.stall, args.early);
+  gemm_body<BM, BN, STAGES>(sched, args.ws, args.tickets, args.err, args.timeout, args.stall, args.early, args.trace);
 }
 
 template <int BM, int BN, int STAGES>
@@ -884,7 +1022,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   MemTwinSched sched{{&tmA,        &tmB,          &tmC,   &tmW,  args.tiles_m, args.tiles_n,
                       args.splits, args.kblocks, args.M, args.N, args.beta}};
   sched.panel = args.panel;
-  gemm_body<BM, BN, STAGES>(sched, args.ws, args.tickets, args.err, args.timeout, args.stall, args.early);
+  gemm_body<BM, BN, STAGES>(sched, args.ws, args.tickets, args.err, args.timeout, args.stall, args.early, args.trace);
 }
 
 template <int BM, int BN, int STAGES>
@@ -895,7 +1033,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   StreamKSched<false> sched{&tmA,   &tmB,   &tmC,      &tmW,        args.tiles_m, args.tiles_n, args.kblocks,
                             args.M, args.N, args.beta, args.splits /* CTAs sharing the tail */, args.dp_tiles};
   sched.panel = args.panel;
-  gemm_body<BM, BN, STAGES>(sched, args.ws, args.tickets, args.err, args.timeout, args.stall, args.early);
+  gemm_body<BM, BN, STAGES>(sched, args.ws, args.tickets, args.err, args.timeout, args.stall, args.early, args.trace);
 }
 
 // cta_group::2 stream-K: whole waves of 256 x BN pair tiles on the 2-CTA clusters,
@@ -908,19 +1046,19 @@ __global__ void __launch_bounds__(kThreads, 1)
   StreamKSched<true> sched{&tmA,   &tmB,   &tmC,      &tmW,        args.tiles_m, args.tiles_n, args.kblocks,
                            args.M, args.N, args.beta, args.splits /* clusters sharing the tail */, args.dp_tiles};
   sched.panel = args.panel;
-  gemm_body<128, BN, STAGES>(sched, args.ws, args.tickets, args.err, args.timeout, args.stall, args.early);
+  gemm_body<128, BN, STAGES>(sched, args.ws, args.tickets, args.err, args.timeout, args.stall, args.early, args.trace);
 }
 
 // cta_group::2: 2-CTA clusters, each pair one 256 x BN output tile (128 rows per CTA).
-template <int BN, int STAGES>
+template <int BN, int STAGES, bool SPLIT>
 __global__ void __launch_bounds__(kThreads, 1)
     gemm_bf16_2sm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                          const __grid_constant__ CUtensorMap tmC, const __grid_constant__ CUtensorMap tmW,
                          const GemmArgs args) {
-  TwoSmSched sched{&tmA, &tmB, &tmC, &tmW, args.tiles_m, args.tiles_n, args.kblocks, args.M, args.N, args.beta};
+  TwoSmSched<SPLIT> sched{&tmA, &tmB, &tmC, &tmW, args.tiles_m, args.tiles_n, args.kblocks, args.M, args.N, args.beta};
   sched.splits = args.splits;
   sched.panel = args.panel;
-  gemm_body<128, BN, STAGES>(sched, args.ws, args.tickets, args.err, args.timeout, args.stall, args.early);
+  gemm_body<128, BN, STAGES>(sched, args.ws, args.tickets, args.err, args.timeout, args.stall, args.early, args.trace);
 }
 
 template <int BM, int BN, int STAGES>
@@ -959,13 +1097,15 @@ __global__ void spin_kernel(long long ns) {
 using KernFn = void (*)(const CUtensorMap, const CUtensorMap, const CUtensorMap, const CUtensorMap, const GemmArgs);
 
 struct TileKernel {
-  KernFn fn;
-  KernFn sk;    // stream-K instance of the same tile
+  KernFn fn;        // split 1
+  KernFn fn_split;  // split-K (S > 1)
+  KernFn sk;        // stream-K instance of the same tile
   int bm, bn, smem;
-  KernFn mem;        // memory twin (loads and stores, no MMA)
-  KernFn two_sm;     // cta_group::2 instance (256-row tiles with BN >= 128), else null
+  KernFn mem;           // memory twin (loads and stores, no MMA)
+  KernFn two_sm;        // cta_group::2 instance (256-row tiles with BN >= 128), split 1, else null
+  KernFn two_sm_split;  // cta_group::2 split-K instance, else null
   int smem2;
-  KernFn two_sm_sk;  // cta_group::2 stream-K instance, else null
+  KernFn two_sm_sk;     // cta_group::2 stream-K instance, else null
 };
 
 // Stages of the cta_group::2 instances: 16 KB of A + BN/2 x 64 of B per stage and CTA.
@@ -974,10 +1114,12 @@ constexpr int kStages2Sm = BN == 256 ? 6 : 8;
 
 template <int BM, int BN, int ST>
 TileKernel make_tile_kernel() {
-  TileKernel t{gemm_bf16_kernel<BM, BN, ST>, gemm_bf16_streamk_kernel<BM, BN, ST>, BM, BN,
-               KCfg<BM, BN, ST>::SMEM_BYTES, gemm_bf16_memtwin_kernel<BM, BN, ST>, nullptr, 0, nullptr};
+  TileKernel t{gemm_bf16_kernel<BM, BN, ST, false>, gemm_bf16_kernel<BM, BN, ST, true>,
+               gemm_bf16_streamk_kernel<BM, BN, ST>, BM, BN, KCfg<BM, BN, ST>::SMEM_BYTES,
+               gemm_bf16_memtwin_kernel<BM, BN, ST>, nullptr, nullptr, 0, nullptr};
   if constexpr (BM == 256 && BN >= 128) {
-    t.two_sm = gemm_bf16_2sm_kernel<BN, kStages2Sm<BN>>;
+    t.two_sm = gemm_bf16_2sm_kernel<BN, kStages2Sm<BN>, false>;
+    t.two_sm_split = gemm_bf16_2sm_kernel<BN, kStages2Sm<BN>, true>;
     t.smem2 = KCfg<128, BN, kStages2Sm<BN>, 2>::SMEM_BYTES;
     t.two_sm_sk = gemm_bf16_2sm_streamk_kernel<BN, kStages2Sm<BN>>;
   }
@@ -1037,6 +1179,8 @@ struct rg_ctx {
   int32_t static_operands = 0;  // rg_set_static_operands
   int64_t launches = 0;
   std::vector<cudaEvent_t> events;
+  unsigned long long* trace = nullptr;  // phase stamps of the last traced launch (RG_PHASE_TIMERS builds)
+  int32_t trace_on = 0;
   // device staging of rg_gemm_plan_host (grown on demand)
   void* stage_a = nullptr;
   void* stage_b = nullptr;
@@ -1166,7 +1310,10 @@ static int prepare(rg_ctx* ctx, int64_t M, int64_t N, int64_t K, const void* A, 
       L->w = L->c;  // unused without split-K
   }
   if (rc != RG_OK) return rc;
-  L->fn = (sk && two) ? tk.two_sm_sk : sk ? tk.sk : two ? tk.two_sm : tk.fn;
+  L->fn = (sk && two) ? tk.two_sm_sk
+          : sk        ? tk.sk
+          : two       ? (splits > 1 ? tk.two_sm_split : tk.two_sm)
+                      : (splits > 1 ? tk.fn_split : tk.fn);
   L->cluster = two ? 2 : 1;
   L->smem = two ? tk.smem2 : tk.smem;
   L->ws_slots = slots;
@@ -1190,6 +1337,7 @@ static int prepare(rg_ctx* ctx, int64_t M, int64_t N, int64_t K, const void* A, 
   g.timeout = ctx->timeout;
   g.stall = ctx->stall;
   g.early = ctx->static_operands;
+  g.trace = ctx->trace_on ? ctx->trace : nullptr;
   const int64_t units = tiles_m * tiles_n * splits;
   if (two && sk) {  // stream-K over 2-CTA clusters
     L->grid = dim3(static_cast<unsigned>(2 * skg.grid));
@@ -1237,8 +1385,6 @@ void ctx_identity(const rg_ctx* ctx, char name[64], int32_t* sms) {
   *sms = ctx->sm_count;
 }
 
-int plan_cell(const Plan& P, int64_t M, int64_t N, int64_t K, int64_t* cell);
-
 // Leaves of the plan cell covering (M, N, K), clipped to the problem.
 static int plan_launches(rg_ctx* ctx, const rg_plan* plan, int64_t M, int64_t N, int64_t K, const void* A,
                          int64_t lda, const void* B, int64_t ldb, float* C, int64_t ldc, std::vector<Launch>& out) {
@@ -1248,6 +1394,8 @@ static int plan_launches(rg_ctx* ctx, const rg_plan* plan, int64_t M, int64_t N,
   int64_t cell = 0;
   if (plan_cell(plan->p, M, N, K, &cell) != RG_OK) return fail(RG_ERR_SHAPE, "shape beyond the plan grid");
   const Plan& P = plan->p;
+  if (!P.variant_ids.empty() && variant_fp8(P.variant_ids[0]))
+    return fail(RG_ERR_INVALID, "an FP8 plan runs through rg_gemm_fp8_plan");
   for (int64_t i = P.leaf_off[cell]; i < P.leaf_off[cell + 1]; ++i) {
     const rg_leaf& lf = P.leaves[i];
     if (lf.m0 >= M || lf.n0 >= N || lf.k0 >= K) continue;  // wholly in the padding
@@ -1395,6 +1543,11 @@ extern "C" int rg_init(int device, int64_t workspace_bytes, rg_ctx** out) {
     const rg::TileKernel& tk = rg::tile_kernel(t);
     if ((e = cudaFuncSetAttribute(reinterpret_cast<const void*>(tk.fn), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   tk.smem)) != cudaSuccess ||
+        (e = cudaFuncSetAttribute(reinterpret_cast<const void*>(tk.fn_split),
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, tk.smem)) != cudaSuccess ||
+        (tk.two_sm_split && (e = cudaFuncSetAttribute(reinterpret_cast<const void*>(tk.two_sm_split),
+                                                      cudaFuncAttributeMaxDynamicSharedMemorySize, tk.smem2)) !=
+                                cudaSuccess) ||
         (e = cudaFuncSetAttribute(reinterpret_cast<const void*>(tk.sk), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   tk.smem)) != cudaSuccess ||
         (e = cudaFuncSetAttribute(reinterpret_cast<const void*>(tk.mem), cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1438,6 +1591,7 @@ extern "C" void rg_destroy(rg_ctx* ctx) {
   if (!ctx) return;
   cudaSetDevice(ctx->device);
   for (auto ev : ctx->events) cudaEventDestroy(ev);
+  cudaFree(ctx->trace);
   cudaFree(ctx->stage_a);
   cudaFree(ctx->stage_b);
   cudaFree(ctx->stage_c);
@@ -1462,6 +1616,41 @@ extern "C" int rg_set_test_stall(rg_ctx* ctx, int32_t enable) {
 extern "C" int rg_launch_count(const rg_ctx* ctx, int64_t* out) {
   if (!ctx || !out) return rg::fail(RG_ERR_INVALID, "rg_launch_count: null argument");
   *out = ctx->launches;
+  return RG_OK;
+}
+
+extern "C" int rg_phase_trace(rg_ctx* ctx, int32_t enable) {
+  rg::clear_error();
+  if (!ctx) return rg::fail(RG_ERR_INVALID, "rg_phase_trace: null context");
+  if (!RG_PHASE_TIMERS)
+    return rg::fail(RG_ERR_INVALID, "rg_phase_trace: this library was built without phase timers "
+                                    "(build with RG_PHASE_TIMERS=1)");
+  if (enable && !ctx->trace) {
+    const size_t bytes = sizeof(unsigned long long) * rg::kTraceFields * static_cast<size_t>(ctx->sm_count);
+    cudaError_t e = cudaMalloc(&ctx->trace, bytes);
+    if (e == cudaSuccess) e = cudaMemset(ctx->trace, 0, bytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      ctx->trace = nullptr;
+      return rg::fail(RG_ERR_OOM, "rg_phase_trace: trace buffer");
+    }
+  }
+  ctx->trace_on = enable ? 1 : 0;
+  return RG_OK;
+}
+
+extern "C" int rg_phase_trace_read(rg_ctx* ctx, uint64_t* out, int32_t max_ctas, int32_t* n_ctas) {
+  rg::clear_error();
+  if (!ctx || !out || !n_ctas || max_ctas <= 0) return rg::fail(RG_ERR_INVALID, "rg_phase_trace_read: bad argument");
+  if (!ctx->trace) return rg::fail(RG_ERR_INVALID, "rg_phase_trace_read: tracing was never enabled");
+  const int32_t n = std::min(max_ctas, ctx->sm_count);
+  const size_t bytes = sizeof(unsigned long long) * rg::kTraceFields * static_cast<size_t>(n);
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemcpy(out, ctx->trace, bytes, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess)
+    e = cudaMemset(ctx->trace, 0, sizeof(unsigned long long) * rg::kTraceFields * static_cast<size_t>(ctx->sm_count));
+  if (e != cudaSuccess) return rg::cuda_fail(e, "rg_phase_trace_read");
+  *n_ctas = n;
   return RG_OK;
 }
 
@@ -1590,7 +1779,8 @@ static int sweep_impl(rg_ctx* ctx, const rg_grid* grid, int32_t n_variants, cons
   rg_sweep_opts o;
   rg_sweep_opts_default(&o);
   if (opts) o = *opts;
-  if (o.reps <= 0 || o.warmup < 0 || o.global_warmup < 0 || o.spin_ns < 0)
+  if (o.reps <= 0 || o.warmup < 0 || o.global_warmup < 0 || o.spin_ns < 0 || o.shard_count < 1 ||
+      o.shard_index < 0 || o.shard_index >= o.shard_count)
     return rg::fail(RG_ERR_INVALID, "rg_sweep: options");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const int64_t cells = rg::cells_of(*grid);
@@ -1655,6 +1845,17 @@ static int sweep_impl(rg_ctx* ctx, const rg_grid* grid, int32_t n_variants, cons
         keep.push_back(it);
     }
     order.swap(keep);
+  }
+  if (o.shard_count > 1) {  // this shard's share of the common order; the others' entries marked
+    std::vector<int64_t> mine;
+    mine.reserve(order.size() / o.shard_count + 1);
+    for (size_t p = 0; p < order.size(); ++p) {
+      if (static_cast<int32_t>(p % o.shard_count) == o.shard_index)
+        mine.push_back(order[p]);
+      else
+        t_ns_out[order[p]] = RG_T_OTHER_SHARD;
+    }
+    order.swap(mine);
   }
   auto prep = [&](int64_t item, int* launches) -> int {
     int64_t M, N, K;
@@ -1885,11 +2086,29 @@ extern "C" int rg_group_create(rg_ctx* ctx, int32_t tile, int32_t max_items, int
     rg::group_free(g);
     return rg::fail(RG_ERR_OOM, std::string("rg_group_create: ") + cudaGetErrorString(e));
   }
+  // every family's work lists and graphs now, so that no call allocates or
+  // instantiates on the serving path
+  for (int f = 0; f < rg::kGroupFamilies; ++f) {
+    const int rc = rg::group_family_ready(g, f);
+    if (rc != RG_OK) {
+      rg::group_free(g);
+      return rc;
+    }
+  }
   *out = g;
   return RG_OK;
 }
 
 extern "C" void rg_group_destroy(rg_group* g) { rg::group_free(g); }
+
+namespace rg {
+void group_workspace(rg_group* g, float** ws, int64_t* ws_bytes, int32_t** tickets, int64_t* max_tickets) {
+  *ws = g->ws;
+  *ws_bytes = g->ws_bytes;
+  *tickets = g->tickets;
+  *max_tickets = kMaxTickets;
+}
+}  // namespace rg
 
 extern "C" int rg_gemm_grouped(rg_group* g, const rg_group_problem* probs, int32_t n, void* stream) {
   rg::clear_error();
@@ -2025,11 +2244,11 @@ static int noalloc_setup(int dev, NoallocDevice** out) {
     if (rc != RG_OK) return rc;
     for (int t = 0; t < RG_NUM_TILES; ++t) {
       const TileKernel& tk = tile_kernel(t);
-      for (KernFn fn : {tk.fn, tk.sk}) {
+      for (KernFn fn : {tk.fn, tk.fn_split, tk.sk}) {
         e = cudaFuncSetAttribute(reinterpret_cast<const void*>(fn), cudaFuncAttributeMaxDynamicSharedMemorySize, tk.smem);
         if (e != cudaSuccess) return cuda_fail(e, "rg_gemm_noalloc: shared-memory attribute");
       }
-      for (KernFn fn : {tk.two_sm, tk.two_sm_sk}) {
+      for (KernFn fn : {tk.two_sm, tk.two_sm_split, tk.two_sm_sk}) {
         if (!fn) continue;
         e = cudaFuncSetAttribute(reinterpret_cast<const void*>(fn), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  tk.smem2);

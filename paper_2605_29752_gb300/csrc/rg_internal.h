@@ -52,6 +52,8 @@ inline int variant_tile(int v) {
          : v >= kClassicVariants ? v - kClassicVariants
                                  : v / RG_NUM_SPLITS;
 }
+inline bool variant_fp8(int v) { return v >= RG_FP8_VARIANT_BASE && v < RG_FP8_VARIANT_BASE + RG_FP8_NUM_VARIANTS; }
+inline bool variant_valid(int v) { return (v >= 0 && v < RG_NUM_VARIANTS) || variant_fp8(v); }
 inline int variant_split(int v) {
   return variant_streamk(v)      ? 1
          : v >= k2SmVariants     ? 1 << ((v - k2SmVariants) % RG_NUM_SPLITS)
@@ -62,7 +64,10 @@ inline int variant_split(int v) {
 // remainder tiles are divided among tail_ctas CTAs by K iterations (each at
 // least kSkMinIters K blocks, at most kSkMaxPieces CTAs per tile).
 constexpr int64_t kSkMinIters = 4;
-constexpr int64_t kSkMaxPieces = 4;
+// At most 2 pieces per tail tile: the last arriving piece then reads one other
+// partial, and that fixup, not the K loop, bounds the tail (phase timers: each
+// further partial adds about 0.3 us per 32-column chunk of a CTA's rows).
+constexpr int64_t kSkMaxPieces = 2;
 struct SkGeometry {
   int64_t grid;       // CTAs launched
   int64_t dp_tiles;   // tiles [0, dp_tiles) run whole, tile g + i * grid on CTA g
@@ -112,6 +117,7 @@ int timed_sweep(rg_ctx* ctx, const std::vector<int64_t>& order, const rg_sweep_o
 #endif
 
 namespace rg {
+int plan_cell(const Plan& P, int64_t M, int64_t N, int64_t K, int64_t* cell);
 struct Fp8CtxInfo {
   int32_t* err;
   long long timeout;
@@ -123,6 +129,29 @@ struct Fp8CtxInfo {
 };
 int ctx_fp8_info(rg_ctx* ctx, Fp8CtxInfo* out);
 void ctx_count_launches(rg_ctx* ctx, int64_t n);
+// An FP8 GEMM request of the serving engine (operands as rg_gemm_fp8_ex).
+struct Fp8Request {
+  int64_t M, N, K;
+  const uint8_t* qA;
+  int64_t lda;
+  const float* sA;
+  int64_t lds_a;
+  const uint8_t* qB;
+  int64_t ldb;
+  const float* sB;
+  int64_t lds_b;
+  float* C;
+  int64_t ldc;
+};
+// The argument checks of rg_gemm_fp8_ex for a request (RG_OK or the status it would return).
+int fp8_request_status(const Fp8Request& r);
+// Enqueues on `st` the leaves of phase `phase` of the request's FP8 plan cell (without a plan:
+// one leaf, RG_FP8_VARIANT(0, 0), phase 0), with the given split-K workspace and tickets;
+// *max_phase receives the cell's largest phase.
+int fp8_enqueue_phase(rg_ctx* ctx, const rg_plan* plan, const Fp8Request& r, int32_t phase, float* ws,
+                      int64_t ws_bytes, int32_t* tickets, int64_t max_tickets, void* stream, int32_t* max_phase);
+// The split-K workspace and tickets of a group (for work enqueued on the group's stream).
+void group_workspace(rg_group* g, float** ws, int64_t* ws_bytes, int32_t** tickets, int64_t* max_tickets);
 // The CUDA device of a context (for threads the library starts).
 int ctx_device(const rg_ctx* ctx);
 int sweep_surfaces(const rg_grid* grid, int32_t rows, const int64_t* t_ns, double* tflops_out, double* stats_out);

@@ -99,10 +99,11 @@ extern "C" int rg_plan_build_ex(const rg_grid* grid, const int64_t* T0_ns, int32
       (grid->m.start != grid->m.step || grid->n.start != grid->n.step || grid->k.start != grid->k.step))
     return rg::fail(RG_ERR_INVALID, "rg_plan_build: splitting needs start == step on every axis");
   for (int v = 0; v < n_variants; ++v) {
-    if (variant_ids[v] < 0 || variant_ids[v] >= RG_NUM_VARIANTS)
-      return rg::fail(RG_ERR_INVALID, "rg_plan_build: variant id out of range");
+    if (!rg::variant_valid(variant_ids[v])) return rg::fail(RG_ERR_INVALID, "rg_plan_build: variant id out of range");
     if (v > 0 && variant_ids[v] <= variant_ids[v - 1])
       return rg::fail(RG_ERR_INVALID, "rg_plan_build: variant ids must be strictly increasing");
+    if (rg::variant_fp8(variant_ids[v]) != rg::variant_fp8(variant_ids[0]))
+      return rg::fail(RG_ERR_INVALID, "rg_plan_build: BF16 and FP8 variant ids cannot share a plan");
   }
   const Dims d{grid->m.count, grid->n.count, grid->k.count};
   const int64_t cells = rg::cells_of(*grid);
@@ -262,6 +263,8 @@ extern "C" int rg_plan_lookup(const rg_plan* plan, int64_t M, int64_t N, int64_t
 // ---------------------------------------------------------------- file format
 namespace {
 const char kMagic[8] = {'R', 'G', 'P', 'L', 'A', 'N', '0', '1'};
+// 2: the variant numbering without the multicast pairs, with cta_group::2 stream-K and FP8 ids
+const uint32_t kPlanFileVersion = 2;
 
 template <class T>
 void put(std::vector<uint8_t>& b, const T* p, size_t n) {
@@ -311,7 +314,7 @@ extern "C" int rg_plan_save(const rg_plan* plan, const rg_ctx* ctx, const char* 
   const uint64_t sum = fnv1a(body.data(), body.size());
   FILE* f = std::fopen(path, "wb");
   if (!f) return rg::fail(RG_ERR_INVALID, std::string("rg_plan_save: cannot open ") + path);
-  const uint32_t version = 1;
+  const uint32_t version = kPlanFileVersion;
   bool ok = std::fwrite(kMagic, 1, 8, f) == 8 && std::fwrite(&version, 4, 1, f) == 1 &&
             std::fwrite(&sum, 8, 1, f) == 1 && std::fwrite(body.data(), 1, body.size(), f) == body.size();
   ok = (std::fclose(f) == 0) && ok;
@@ -333,7 +336,7 @@ extern "C" int rg_plan_load(const char* path, const rg_ctx* ctx, rg_plan** out) 
     while ((n = std::fread(buf, 1, sizeof(buf), f)) > 0) body.insert(body.end(), buf, buf + n);
   }
   std::fclose(f);
-  if (!ok || std::memcmp(magic, kMagic, 8) != 0 || version != 1)
+  if (!ok || std::memcmp(magic, kMagic, 8) != 0 || version != kPlanFileVersion)
     return rg::fail(RG_ERR_PLAN_MISMATCH, "rg_plan_load: not a plan file of this version");
   if (fnv1a(body.data(), body.size()) != sum)
     return rg::fail(RG_ERR_PLAN_MISMATCH, "rg_plan_load: checksum mismatch");
@@ -346,7 +349,7 @@ extern "C" int rg_plan_load(const char* path, const rg_ctx* ctx, rg_plan** out) 
   int64_t nv = 0, cells = 0, nl = 0;
   ok = get(body, off, name, 64) && get(body, off, &sms, 1) && get(body, off, &P.grid, 1) &&
        get(body, off, &nv, 1) && get(body, off, &cells, 1) && get(body, off, &nl, 1) && nv > 0 &&
-       nv <= RG_NUM_VARIANTS && cells == rg::cells_of(P.grid) && nl >= cells;
+       nv <= RG_NUM_VARIANTS + RG_FP8_NUM_VARIANTS && cells == rg::cells_of(P.grid) && nl >= cells;
   if (ok) {
     P.variant_ids.resize(nv);
     P.T0s.resize(cells); P.vstar.resize(cells); P.T1.resize(cells); P.target3.resize(3 * cells);

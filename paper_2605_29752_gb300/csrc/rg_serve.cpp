@@ -96,12 +96,23 @@ struct Arena {  // first-fit allocator over one device allocation, 256-byte gran
   }
 };
 
-int64_t request_bytes(const rg_serve_request& r) { return 2 * r.M * r.K + 2 * r.K * r.N + 4 * r.M * r.N; }
+int64_t request_bytes(const rg_serve_request& r) {
+  if (r.dtype == RG_DTYPE_FP8)
+    return r.M * r.K + r.K * r.N + 4 * r.M * r.N + 4 * (((r.M + 127) / 128) * r.lds_a + ((r.K + 127) / 128) * r.lds_b);
+  return 2 * r.M * r.K + 2 * r.K * r.N + 4 * r.M * r.N;
+}
+
+rg::Fp8Request fp8_request(const rg_serve_request& r, float* C, int64_t ldc) {
+  return rg::Fp8Request{r.M,  r.N,  r.K,   static_cast<const uint8_t*>(r.A), r.lda, r.sA, r.lds_a,
+                        static_cast<const uint8_t*>(r.B), r.ldb, r.sB, r.lds_b, C, ldc};
+}
 
 // The per-request checks of rg_gemm (sizes, leading dimensions, TMA alignment),
 // made at admission so that one malformed request is rejected alone instead of
 // failing the grouped launch it would join.
 int request_status(const rg_serve_request& r) {
+  if (r.dtype == RG_DTYPE_FP8) return rg::fp8_request_status(fp8_request(r, r.C, r.ldc));
+  if (r.dtype != RG_DTYPE_BF16) return RG_ERR_INVALID;
   if (r.M <= 0 || r.N <= 0 || r.K <= 0 || !r.A || !r.B) return RG_ERR_INVALID;
   if (r.lda < r.K || r.ldb < r.N || (r.C && r.ldc < r.N)) return RG_ERR_INVALID;
   if ((reinterpret_cast<uintptr_t>(r.A) & 15) || (reinterpret_cast<uintptr_t>(r.B) & 15) || (r.lda % 8) ||
@@ -153,6 +164,7 @@ class Engine {
     }
     if (need_arena && !arena_.init(o_.hbm_budget_bytes))
       return rg::fail(RG_ERR_OOM, "rg_serve: output arena of the budget size");
+    t0_ = std::chrono::steady_clock::now();  // the engine's clock starts once it is set up
     return RG_OK;
   }
 
@@ -336,10 +348,16 @@ class Engine {
 
   int launch_batch(Slot& s) {
     std::vector<std::pair<int32_t, rg_group_problem>> leaves;
+    std::vector<int64_t> fp8;  // FP8 members, run leaf by leaf after each phase's grouped launch
     s.members.clear();
     while (!ready_.empty() && static_cast<int32_t>(s.members.size()) < o_.max_batch) {
       const int64_t i = ready_.front();
       ready_.pop_front();
+      if (recs_[static_cast<size_t>(i)].req.dtype == RG_DTYPE_FP8) {
+        fp8.push_back(i);
+        s.members.push_back(i);
+        continue;
+      }
       const int rc = route(recs_[static_cast<size_t>(i)], leaves);
       if (rc != RG_OK) {  // a shape beyond the plan grid fails alone
         Record& rec = recs_[static_cast<size_t>(i)];
@@ -353,15 +371,41 @@ class Engine {
     const int64_t t = now_ns();
     int32_t max_phase = 0;
     for (const auto& l : leaves) max_phase = std::max(max_phase, l.first);
+    float* ws = nullptr;
+    int32_t* tickets = nullptr;
+    int64_t ws_bytes = 0, max_tickets = 0;
+    rg::group_workspace(s.group, &ws, &ws_bytes, &tickets, &max_tickets);
+    std::vector<int32_t> fp8_phases(fp8.size(), 0);
     std::vector<rg_group_problem> probs;
     for (int32_t ph = 0; ph <= max_phase; ++ph) {  // a K split's later pieces after the earlier ones
       probs.clear();
       for (const auto& l : leaves)
         if (l.first == ph) probs.push_back(l.second);
-      if (probs.empty()) continue;
-      const int rc = rg_gemm_grouped(s.group, probs.data(), static_cast<int32_t>(probs.size()), s.stream);
-      if (rc != RG_OK) return rc;
+      if (!probs.empty()) {
+        const int rc = rg_gemm_grouped(s.group, probs.data(), static_cast<int32_t>(probs.size()), s.stream);
+        if (rc != RG_OK) return rc;
+      }
+      for (size_t j = 0; j < fp8.size(); ++j) {  // the same stream, so the group's workspace is free
+        if (ph > fp8_phases[j]) continue;
+        Record& rec = recs_[static_cast<size_t>(fp8[j])];
+        if (rec.done) continue;
+        int32_t mp = 0;
+        const int rc = rg::fp8_enqueue_phase(ctx_, o_.fp8_plan, fp8_request(rec.req, rec.c_ptr, rec.req.C ? rec.req.ldc : rec.req.N),
+                                             ph, ws, ws_bytes, tickets, max_tickets, s.stream, &mp);
+        if (rc == RG_ERR_SHAPE && ph == 0) {  // beyond the FP8 plan's grid: fails alone, before any launch
+          rec.res.status = rc;
+          finish(fp8[j], now_ns());
+          s.members.erase(std::find(s.members.begin(), s.members.end(), fp8[j]));
+          continue;
+        }
+        if (rc != RG_OK) return rc;
+        if (ph == 0) {
+          fp8_phases[j] = mp;
+          max_phase = std::max(max_phase, mp);
+        }
+      }
     }
+    if (s.members.empty()) return RG_OK;
     if (cudaEventRecord(s.done, s.stream) != cudaSuccess) return rg::fail(RG_ERR_CUDA, "rg_serve: event record");
     for (int64_t i : s.members) {
       recs_[static_cast<size_t>(i)].res.launched_ns = t;
@@ -381,7 +425,7 @@ class Engine {
   std::deque<int64_t> arrived_, ready_;
   int64_t resident_ = 0, stalls_ = 0, batches_ = 0, done_count_ = 0;
   bool stalled_head_ = false;
-  const std::chrono::steady_clock::time_point t0_ = std::chrono::steady_clock::now();
+  std::chrono::steady_clock::time_point t0_ = std::chrono::steady_clock::now();
 };
 
 }  // namespace
@@ -393,6 +437,7 @@ extern "C" void rg_serve_opts_default(rg_serve_opts* o) {
   o->max_inflight = 2;
   o->tile = RG_TILE_128x128;
   o->workspace_mib = 256;
+  o->fp8_plan = nullptr;
 }
 
 extern "C" int rg_serve(rg_ctx* ctx, const rg_plan* plan, const rg_serve_opts* opts, const rg_serve_request* reqs,

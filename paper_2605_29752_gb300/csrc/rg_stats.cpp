@@ -113,6 +113,8 @@ extern "C" void rg_sweep_opts_default(rg_sweep_opts* o) {
   o->seed = 0;
   o->spin_ns = 4000;
   o->prune_splits = 1;
+  o->shard_index = 0;
+  o->shard_count = 1;
   o->reserved = 0;
 }
 
@@ -184,7 +186,7 @@ int sweep_surfaces(const rg_grid* grid, int32_t rows, const int64_t* t_ns, doubl
     double* tf = tflops_out ? tflops_out + static_cast<int64_t>(v) * cells : nullptr;
     double* st = stats_out ? stats_out + 6 * static_cast<int64_t>(v) : nullptr;
     bool full = true;
-    for (int64_t i = 0; i < cells && full; ++i) full = t[i] != RG_T_UNMEASURED;
+    for (int64_t i = 0; i < cells && full; ++i) full = t[i] != RG_T_UNMEASURED && t[i] != RG_T_OTHER_SHARD;
     if (full) {
       double rough[5], mean = 0.0;
       const int rc = rg_surface_stats(grid, t, tf, rough, &mean);
@@ -197,7 +199,7 @@ int sweep_surfaces(const rg_grid* grid, int32_t rows, const int64_t* t_ns, doubl
     }
     if (tf)
       for (int64_t i = 0; i < cells; ++i) {
-        if (t[i] == RG_T_UNMEASURED) {
+        if (t[i] == RG_T_UNMEASURED || t[i] == RG_T_OTHER_SHARD) {
           tf[i] = 0.0;
           continue;
         }

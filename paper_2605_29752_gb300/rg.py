@@ -15,7 +15,9 @@ import os
 
 import numpy as np
 
-_LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "librg.so")
+# RG_LIBRARY may name another build of the same library (for example the phase-timer build,
+# librg_timers.so, next to librg.so); by default the in-tree librg.so.
+_LIB_PATH = os.environ.get("RG_LIBRARY") or os.path.join(os.path.dirname(os.path.abspath(__file__)), "librg.so")
 
 RG_OK = 0
 RG_ERR_INVALID = -1
@@ -29,6 +31,7 @@ RG_ERR_ADMISSION = -8
 RG_ERR_NO_DEVICE = -9
 
 RG_T_UNMEASURED = 1 << 60
+RG_T_OTHER_SHARD = 0
 RG_NUM_TILES = 6
 RG_NUM_SPLITS = 4
 RG_NUM_VARIANTS = RG_NUM_TILES * RG_NUM_SPLITS + RG_NUM_TILES + 2 * RG_NUM_SPLITS + 2
@@ -102,7 +105,8 @@ class rg_leaf(C.Structure):
 class rg_sweep_opts(C.Structure):
     _fields_ = [("reps", C.c_int32), ("warmup", C.c_int32), ("global_warmup", C.c_int32),
                 ("shuffle", C.c_int32), ("seed", C.c_uint64), ("spin_ns", C.c_int64),
-                ("prune_splits", C.c_int32), ("reserved", C.c_int32)]
+                ("prune_splits", C.c_int32), ("shard_index", C.c_int32), ("shard_count", C.c_int32),
+                ("reserved", C.c_int32)]
 
 
 class rg_group_problem(C.Structure):
@@ -114,13 +118,28 @@ class rg_group_problem(C.Structure):
 
 class rg_serve_opts(C.Structure):
     _fields_ = [("hbm_budget_bytes", C.c_int64), ("max_batch", C.c_int32), ("max_inflight", C.c_int32),
-                ("tile", C.c_int32), ("workspace_mib", C.c_int32)]
+                ("tile", C.c_int32), ("workspace_mib", C.c_int32), ("fp8_plan", C.c_void_p)]
+
+
+RG_DTYPE_BF16 = 0
+RG_DTYPE_FP8 = 1
 
 
 class rg_serve_request(C.Structure):
     _fields_ = [("M", C.c_int64), ("N", C.c_int64), ("K", C.c_int64), ("A", C.c_void_p), ("lda", C.c_int64),
                 ("B", C.c_void_p), ("ldb", C.c_int64), ("C", C.c_void_p), ("ldc", C.c_int64),
-                ("arrival_ns", C.c_int64)]
+                ("arrival_ns", C.c_int64), ("dtype", C.c_int32), ("reserved", C.c_int32),
+                ("sA", C.c_void_p), ("lds_a", C.c_int64), ("sB", C.c_void_p), ("lds_b", C.c_int64)]
+
+
+def serve_request(M, N, K, A, lda, B, ldb, Cp, ldc, arrival_ns=0, fp8=None) -> rg_serve_request:
+    """One request; fp8 = (sA, lds_a, sB, lds_b) makes it an FP8 request (A, B are e4m3 codes)."""
+    if fp8 is None:
+        return rg_serve_request(M, N, K, _ptr(A), lda, _ptr(B), ldb, _ptr(Cp), ldc, int(arrival_ns), RG_DTYPE_BF16,
+                                0, None, 0, None, 0)
+    sA, lds_a, sB, lds_b = fp8
+    return rg_serve_request(M, N, K, _ptr(A), lda, _ptr(B), ldb, _ptr(Cp), ldc, int(arrival_ns), RG_DTYPE_FP8, 0,
+                            _ptr(sA), lds_a, _ptr(sB), lds_b)
 
 
 class rg_serve_result(C.Structure):
@@ -177,11 +196,17 @@ _sigs = {
     "rg_serve_stop": (C.c_int, [_P, C.POINTER(rg_serve_stats)]),
     "rg_fp8_quantize": (C.c_int, [_P, _P, _I64, _I64, _I64, _P, _I64, _P, _P]),
     "rg_gemm_fp8": (C.c_int, [_P, _I64, _I64, _I64, _P, _I64, _P, _P, _I64, _P, _P, _I64, _P]),
-    "rg_sweep_fp8": (C.c_int, [_P, C.POINTER(rg_grid), _P, _P, _P, _P, _P, C.POINTER(rg_sweep_opts), _P, _P]),
+    "rg_gemm_fp8_ex": (C.c_int, [_P, _I64, _I64, _I64, _P, _I64, _P, _I64, _P, _I64, _P, _I64, _P, _I64, _I32, _I32,
+                                 _I64, _I64, _I64, _P]),
+    "rg_gemm_fp8_plan": (C.c_int, [_P, _P, _I64, _I64, _I64, _P, _I64, _P, _I64, _P, _I64, _P, _I64, _P, _I64, _P]),
+    "rg_sweep_fp8": (C.c_int, [_P, C.POINTER(rg_grid), _I32, _P, _P, _P, _P, _P, _P, _P, C.POINTER(rg_sweep_opts), _P,
+                               _P, _P, _P]),
     "rg_landscape": (C.c_int, [C.POINTER(rg_grid), _I32, C.c_double, _I32, C.c_double, _I32, _P, _I32, _I32, _P]),
     "rg_kol": (C.c_int, [C.c_double, C.c_double, C.c_double, C.c_double, _P, _P]),
     "rg_gemm_noalloc": (C.c_int, [_I64, _I64, _I64, _P, _I64, _P, _I64, _P, _I64, _I32, _I32, _P]),
     "rg_noalloc_check": (C.c_int, [_P]),
+    "rg_phase_trace": (C.c_int, [_P, _I32]),
+    "rg_phase_trace_read": (C.c_int, [_P, _P, _I32, C.POINTER(_I32)]),
     "rg_plan_free": (None, [_P]),
     "rg_plan_grid": (C.c_int, [_P, C.POINTER(rg_grid)]),
     "rg_plan_tables": (C.c_int, [_P, _P, _P, _P, _P, _P, _P, _P]),
@@ -516,12 +541,12 @@ def rg_serve_opts_default() -> rg_serve_opts:
 
 
 def rg_serve(ctx, plan, opts: rg_serve_opts, requests):
-    """requests: iterables (M, N, K, A, lda, B, ldb, C or None, ldc, arrival_ns).
-    Returns (list of result dicts, stats dict)."""
+    """requests: iterables (M, N, K, A, lda, B, ldb, C or None, ldc, arrival_ns[, (sA, lds_a, sB, lds_b)])
+    -- the optional last item makes an FP8 request.  Returns (list of result dicts, stats dict)."""
     n = len(requests)
     arr = (rg_serve_request * max(1, n))()
-    for i, (M, N, K, A, lda, B, ldb, Cp, ldc, t) in enumerate(requests):
-        arr[i] = rg_serve_request(M, N, K, _ptr(A), lda, _ptr(B), ldb, _ptr(Cp), ldc, int(t))
+    for i, r in enumerate(requests):
+        arr[i] = serve_request(*r[:10], fp8=r[10] if len(r) > 10 else None)
     res = (rg_serve_result * max(1, n))()
     st = rg_serve_stats()
     _check(_lib.rg_serve(ctx, plan, C.byref(opts), arr, n, res, C.byref(st)), "rg_serve")
@@ -543,9 +568,9 @@ def rg_serve_start(ctx, plan, opts: rg_serve_opts) -> int:
     return h.value
 
 
-def rg_serve_submit(server, M, N, K, A, lda, B, ldb, Cp, ldc) -> int:
-    """Submit one request; returns its id."""
-    req = rg_serve_request(M, N, K, _ptr(A), lda, _ptr(B), ldb, _ptr(Cp), ldc, 0)
+def rg_serve_submit(server, M, N, K, A, lda, B, ldb, Cp, ldc, fp8=None) -> int:
+    """Submit one request (fp8 = (sA, lds_a, sB, lds_b) for an FP8 one); returns its id."""
+    req = serve_request(M, N, K, A, lda, B, ldb, Cp, ldc, 0, fp8)
     i = _I64()
     _check(_lib.rg_serve_submit(server, C.byref(req), C.byref(i)), "rg_serve_submit")
     return i.value
@@ -581,12 +606,54 @@ def rg_gemm_fp8(ctx, M, N, K, qA, lda, sA, qB, ldb, sB, Cp, ldc, stream=None) ->
                             _stream(stream)), "rg_gemm_fp8")
 
 
-def rg_sweep_fp8(ctx, grid: rg_grid, qA, sA, qB, sB, Cp, opts: rg_sweep_opts | None = None, stream=None) -> np.ndarray:
-    out = np.zeros(grid_cells(grid), np.int64)
+RG_FP8_VARIANT_BASE = 64
+RG_FP8_NUM_TILES = 2
+RG_FP8_NUM_VARIANTS = RG_FP8_NUM_TILES * RG_NUM_SPLITS
+FP8_TILES = [(128, 256), (128, 128)]
+
+
+def fp8_variant(tile: int, split: int = 1) -> int:
+    """FP8 variant id: tile 0 = 128x256, 1 = 128x128; in-kernel split-K 1/2/4/8."""
+    return RG_FP8_VARIANT_BASE + tile * RG_NUM_SPLITS + SPLITS.index(split)
+
+
+def fp8_variant_name(v: int) -> str:
+    t, s = divmod(v - RG_FP8_VARIANT_BASE, RG_NUM_SPLITS)
+    bm, bn = FP8_TILES[t]
+    return f"fp8 {bm}x{bn}/S{SPLITS[s]}"
+
+
+def rg_gemm_fp8_ex(ctx, M, N, K, qA, lda, sA, lds_a, qB, ldb, sB, lds_b, Cp, ldc, variant_id, beta=0, pm=0, pn=0,
+                   pk=0, stream=None) -> None:
+    _check(_lib.rg_gemm_fp8_ex(ctx, M, N, K, _ptr(qA), lda, _ptr(sA), lds_a, _ptr(qB), ldb, _ptr(sB), lds_b,
+                               _ptr(Cp), ldc, variant_id, beta, pm, pn, pk, _stream(stream)), "rg_gemm_fp8_ex")
+
+
+def rg_gemm_fp8_plan(ctx, plan, M, N, K, qA, lda, sA, lds_a, qB, ldb, sB, lds_b, Cp, ldc, stream=None) -> None:
+    _check(_lib.rg_gemm_fp8_plan(ctx, plan, M, N, K, _ptr(qA), lda, _ptr(sA), lds_a, _ptr(qB), ldb, _ptr(sB), lds_b,
+                                 _ptr(Cp), ldc, _stream(stream)), "rg_gemm_fp8_plan")
+
+
+def rg_sweep_fp8_surfaces(ctx, grid: rg_grid, variant_ids, qA, sA, qB, sB, Cp, opts: rg_sweep_opts | None = None,
+                          plan: int | None = None, stream=None):
+    """(t_ns[rows][cells], tflops[rows][cells], stats[rows][6]) of an FP8 sweep (variants or a plan)."""
+    vids = np.ascontiguousarray(variant_ids if plan is None else [0], dtype=np.int32)
+    out = np.zeros((len(vids), grid_cells(grid)), np.int64)
+    tf = np.zeros((len(vids), grid_cells(grid)), np.float64)
+    st = np.zeros((len(vids), 6), np.float64)
     o = opts or rg_sweep_opts_default()
-    _check(_lib.rg_sweep_fp8(ctx, C.byref(grid), _ptr(qA), _ptr(sA), _ptr(qB), _ptr(sB), _ptr(Cp), C.byref(o),
-                             out.ctypes.data, _stream(stream)), "rg_sweep_fp8")
-    return out
+    _check(_lib.rg_sweep_fp8(ctx, C.byref(grid), len(vids), vids.ctypes.data, plan, _ptr(qA), _ptr(sA), _ptr(qB),
+                             _ptr(sB), _ptr(Cp), C.byref(o), out.ctypes.data, tf.ctypes.data, st.ctypes.data,
+                             _stream(stream)), "rg_sweep_fp8")
+    return out, tf, st
+
+
+def rg_sweep_fp8(ctx, grid: rg_grid, qA, sA, qB, sB, Cp, opts: rg_sweep_opts | None = None, stream=None,
+                 variant_ids=None, plan: int | None = None) -> np.ndarray:
+    """t_ns[cells] of the default FP8 variant (or t_ns[rows][cells] when variant_ids or a plan is given)."""
+    vids = [fp8_variant(0, 1)] if variant_ids is None else variant_ids
+    t = rg_sweep_fp8_surfaces(ctx, grid, vids, qA, sA, qB, sB, Cp, opts, plan, stream)[0]
+    return t[0] if variant_ids is None and plan is None else t
 
 
 RG_LANDSCAPE_IDEAL = 0
@@ -625,3 +692,21 @@ def rg_noalloc_check(stream=None) -> int:
     """Status of the rg_gemm_noalloc work enqueued so far on the current device (synchronises the
     stream): RG_OK, or RG_ERR_TIMEOUT if a bounded wait expired (the scratch is then cleared)."""
     return _lib.rg_noalloc_check(_stream(stream))
+
+
+RG_TRACE_FIELDS = 12
+TRACE_FIELDS = ("gt_entry_ns", "gt_exit_ns", "exit", "dep_wait", "first_stage", "last_mma_commit",
+                "first_acc_ready", "epilogue_done", "fixup_start", "fixup_end", "units", "reserved")
+
+
+def rg_phase_trace(ctx, enable: bool) -> None:
+    """Enable the per-CTA phase stamps of a phase-timer build (RG_PHASE_TIMERS=1)."""
+    _check(_lib.rg_phase_trace(ctx, 1 if enable else 0), "rg_phase_trace")
+
+
+def rg_phase_trace_read(ctx, max_ctas: int = 1024) -> np.ndarray:
+    """uint64[n_ctas][RG_TRACE_FIELDS] stamps of the last traced launch (see include/rg.h)."""
+    out = np.zeros((max_ctas, RG_TRACE_FIELDS), np.uint64)
+    n = _I32()
+    _check(_lib.rg_phase_trace_read(ctx, out.ctypes.data, max_ctas, C.byref(n)), "rg_phase_trace_read")
+    return out[:n.value]

@@ -75,3 +75,18 @@ def test_noise_floor_of_identical_repeats_is_zero_and_scales():
     b = a + np.where(np.arange(a.size) % 2 == 0, 1.0, -1.0)     # alternating +-1 difference
     nf = bench.noise_floor(a, b, 4)
     assert nf["R_3D"] >= 0.0 and nf["R_N_slice"] >= 0.0
+
+
+def test_phase_summary_skips_stamps_a_cta_never_reached():
+    """Phase medians of the phase-timer records: a phase counts only the CTAs that reached both of its
+    stamps (the odd CTA of a cta_group::2 pair issues no MMAs; only last arrivers run a fixup)."""
+    rec = np.zeros((4, 12), np.uint64)
+    rec[:, 0], rec[:, 1], rec[:, 2] = 1000, 3000, 4000          # 2000 ns over 4000 cycles: 0.5 ns / cycle
+    rec[:, 3], rec[:, 7], rec[:, 10] = 100, 3000, 1
+    rec[:2, 4], rec[:2, 5] = 200, 1200                           # only the even CTAs issue MMAs
+    rec[1, 8], rec[1, 9] = 2000, 2600                            # one fixup
+    out = bench.phase_summary(rec)
+    assert out["first_stage_to_last_mma_commit_ns"] == 500.0 and out["first_stage_to_last_mma_commit_ctas"] == 2
+    assert out["fixup_ns"] == 300.0 and out["fixup_ctas"] == 1
+    assert out["cta_total_ns"] == 2000.0 and out["launch_span_ns"] == 2000.0
+    assert out["first_release_to_last_exit_ns"] == 1950.0 and out["release_skew_ns"] == 0.0

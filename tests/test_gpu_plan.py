@@ -200,3 +200,29 @@ def test_plan_host_buffers(rg, ctx, shape):
         assert np.array_equal(C.cpu().numpy()[:, :N], c_h)
     finally:
         rg.rg_plan_free(h)
+
+
+def test_sharded_sweep_partitions_the_items(rg, ctx):
+    """Two shards of one sweep (the same seed) time disjoint sets of (variant, cell) items that together
+    cover every item the pruning keeps; pruned items are marked on both."""
+    g = rg.make_grid((128, 128, 3))
+    Mx = 384
+    A = dev_bf16(synthetic.bf16_uniform_stream(0, synthetic.TAG_A, Mx * Mx))
+    B = dev_bf16(synthetic.bf16_uniform_stream(0, synthetic.TAG_B, Mx * Mx))
+    C = torch.zeros(Mx * Mx, device="cuda")
+    vids = [rg.variant(1, 1), rg.variant(2, 2), rg.variant(0, 4)]
+    full = rg.rg_sweep(ctx, g, vids, A, B, C)
+    parts = []
+    for i in range(2):
+        o = rg.rg_sweep_opts_default()
+        o.shard_index, o.shard_count = i, 2
+        parts.append(rg.rg_sweep(ctx, g, vids, A, B, C, o))
+    pruned = full == rg.RG_T_UNMEASURED
+    assert np.all((parts[0] == rg.RG_T_UNMEASURED) == pruned) and np.all((parts[1] == rg.RG_T_UNMEASURED) == pruned)
+    mine = [(p != rg.RG_T_OTHER_SHARD) & ~pruned for p in parts]
+    assert not np.any(mine[0] & mine[1]) and np.all(mine[0] | mine[1] | pruned)
+    assert abs(int(mine[0].sum()) - int(mine[1].sum())) <= 1            # balanced
+    o = rg.rg_sweep_opts_default()
+    o.shard_index, o.shard_count = 2, 2
+    with pytest.raises(rg.RGError):
+        rg.rg_sweep(ctx, g, vids, A, B, C, o)

@@ -296,3 +296,82 @@ def test_online_server_submit_poll_wait_stop(rg, ctx, streams):
             rg.rg_serve_poll(None, 0)                           # a null server is refused
     finally:
         rg.rg_plan_free(plan)
+
+
+def test_serving_mixed_bf16_and_fp8_requests(rg, ctx, streams):
+    """FP8 requests (top-left blocks of one block-quantised 1024 x 1024 pair, whole scale arrays)
+    interleaved with BF16 ones: each FP8 result is bitwise rg_gemm_fp8_plan's with the same FP8 plan
+    and within the FP8 bound of the dequantised float64 product; the BF16 ones are unchanged by
+    the mix; every request gives the same bits alone."""
+    from oracle import fp8 as of
+    a_bits, b_bits, A, B = streams
+    plan = _full_plan(rg, 0, _full_vids(rg))
+    g = rg.make_grid((128, 128, 8))
+    fvids = [rg.fp8_variant(t, s) for t in range(2) for s in rg.SPLITS]
+    rs = np.random.default_rng(5)
+    s8 = (np.arange(8) + 1) * 128.0
+    base = 50.0 + 2.0 * s8[:, None, None] * s8[None, :, None] * s8[None, None, :] / 8e5
+    T0 = np.stack([np.round(base * rs.uniform(0.6, 1.6, size=(8, 8, 8))) for _ in fvids]).astype(np.int64)
+    fplan = rg.rg_plan_build(g, T0.reshape(len(fvids), -1), fvids)
+    try:
+        xa = torch.from_numpy(synthetic.normal_stream_f32(0, 1, MX * MX)).cuda()
+        xb = torch.from_numpy(synthetic.normal_stream_f32(0, 2, MX * MX)).cuda()
+        qa = torch.empty(MX * MX, dtype=torch.uint8, device="cuda")
+        qb = torch.empty(MX * MX, dtype=torch.uint8, device="cuda")
+        nb = MX // 128
+        sa = torch.empty(nb * nb, device="cuda")
+        sb = torch.empty(nb * nb, device="cuda")
+        rg.rg_fp8_quantize(ctx, xa, MX, MX, MX, qa, MX, sa)
+        rg.rg_fp8_quantize(ctx, xb, MX, MX, MX, qb, MX, sb)
+        rg.rg_check(ctx)
+        Ad = of.dequantize(qa.cpu().numpy().reshape(MX, MX), sa.cpu().numpy().reshape(nb, nb))
+        Bd = of.dequantize(qb.cpu().numpy().reshape(MX, MX), sb.cpu().numpy().reshape(nb, nb))
+        trace = _trace(70, 40000.0, seed=21)
+        reqs, outs, is8 = [], [], []
+        for i, (M, N, K, t) in enumerate(trace):
+            C = torch.full((M, N), float("nan"), device="cuda")
+            outs.append(C)
+            if i % 2:
+                reqs.append((M, N, K, qa, MX, qb, MX, C, N, t, (sa, nb, sb, nb)))
+            else:
+                reqs.append((M, N, K, A, K, B, N, C, N, t))
+            is8.append(bool(i % 2))
+        opts = rg.rg_serve_opts_default()
+        opts.max_batch = 10
+        opts.fp8_plan = fplan
+        res, st = rg.rg_serve(ctx, plan, opts, reqs)
+        rg.rg_check(ctx)
+        assert all(r["status"] == 0 for r in res) and st["requests"] == len(trace)
+        for i, (M, N, K, _) in enumerate(trace):
+            got = outs[i].cpu().numpy()
+            if is8[i]:
+                ref = torch.full((M, N), float("nan"), device="cuda")
+                rg.rg_gemm_fp8_plan(ctx, fplan, M, N, K, qa, MX, sa, nb, qb, MX, sb, nb, ref, N)
+                rg.rg_check(ctx)
+                assert np.array_equal(ref.cpu().numpy(), got), i
+                a, b = Ad[:M, :K], Bd[:K, :N]
+                ratio, ez = og.error_ratio(got, a @ b, np.abs(a) @ np.abs(b))
+                assert ez and ratio <= 4.0 * K * 2.0 ** -24, (i, ratio)
+            else:
+                ref = torch.full((M, N), float("nan"), device="cuda")
+                rg.rg_gemm_plan(ctx, plan, M, N, K, A, K, B, N, ref, N)
+                rg.rg_check(ctx)
+                leaves, _ = rg.rg_plan_lookup(plan, M, N, K)
+                if not any(rg.variant_name(l[0]).endswith("SK") for l in leaves):
+                    assert np.array_equal(ref.cpu().numpy(), got), i
+        for i in range(0, len(trace), 9):                     # alone
+            alone = torch.full_like(outs[i], float("nan"))
+            r = list(reqs[i])
+            r[7], r[9] = alone, 0
+            r1, _ = rg.rg_serve(ctx, plan, opts, [tuple(r)])
+            assert r1[0]["status"] == 0 and torch.equal(alone, outs[i]), i
+        # an FP8 request beyond the FP8 plan's grid fails alone
+        big = torch.zeros((1152, 128), device="cuda")
+        qbig = torch.zeros(1152 * 128, dtype=torch.uint8, device="cuda")    # in bounds even if it ran
+        sbig = torch.ones(9, device="cuda")
+        r2, _ = rg.rg_serve(ctx, plan, opts, [(1152, 128, 128, qbig, 128, qbig, 128, big, 128, 0, (sbig, 1, sbig, 1)),
+                                              reqs[0][:7] + (outs[0], reqs[0][8], 0)])
+        assert r2[0]["status"] == rg.RG_ERR_SHAPE and r2[1]["status"] == 0
+    finally:
+        rg.rg_plan_free(fplan)
+        rg.rg_plan_free(plan)

@@ -54,7 +54,7 @@ CASES = [
     ((768, 1024, 2048), 34, 0),      # 256x256 cta_group::2 pair, split 1
     ((520, 512, 2048), 35, 0),       # 256x256 cta_group::2 pair, split 2, ragged M
     ((2048, 1024, 1024), 5, 0),      # 128x128 split 2 on 128 tiles: partials exactly the scratch size
-    ((1024, 1024, 2048), 25, 0),     # 128x128 stream-K on 64 tiles, 4 pieces: exactly the scratch size
+    ((1024, 1024, 2048), 25, 0),     # 128x128 stream-K on 64 tiles, 2 pieces each: half the scratch
 ]
 
 
