@@ -700,14 +700,15 @@ def main():
                                       np.mean([p["R_N_slice"] for p in plain])),
         "mean_gain_pct": 100.0 * (value / np.mean([p["mean_tflops"] for p in plain]) - 1),
         "roofline": {"bound": "tensor", "achieved": dom_ach, "peak": p_burst, "unit": "TFLOP/s",
-                     "frac": dom_ach / p_burst, "traffic": None,
+                     "frac": dom_ach / p_burst, **dominant_traffic(rg.variant_name(dom)),
                      "mean_frac": float(np.mean([q["roofline_mean_frac"] for q in smooth])),
                      "kernel": f"gemm_bf16 {rg.variant_name(dom)}",
                      "note": f"dominant kernel of the smoothed pass ({100 * dom_share:.1f}% of its device time, "
                              f"{int(dsel.sum())} single-launch cells): useful 2MNK flops / CUDA-event time of "
-                             f"those cells' timed launches; peak = {peak_src} bf16 burst; per-cell launches "
-                             f"differ in size, so DRAM traffic is given per launch for one captured shape "
-                             f"under roofline_capture"},
+                             f"those cells' timed launches; peak = {peak_src} bf16 burst; the cells differ in "
+                             f"size, so traffic is per launch of one captured mid-size cell (traffic_cell, "
+                             f"profiles/{TRAFFIC_PROFILE}.md), and mean_frac is the mean over all cells of "
+                             f"t_roof / t_measured for the smoothed pass"},
         "roofline_all_gemms": {"achieved": agg_smooth, "frac": agg_smooth / p_burst, "unit": "TFLOP/s"},
         "roofline_mean_frac": {"plain": float(np.mean([p["roofline_mean_frac"] for p in plain])),
                                "smoothed": float(np.mean([q["roofline_mean_frac"] for q in smooth])),
@@ -753,6 +754,21 @@ def kernel_source_hash():
 
 CAPTURE_PROFILE = "gemm_bf16_256x256_2sm_8192x8192x4096"   # profiles/<name>.md and .json
 CAPTURE_VARIANT = "256x256/2SM"
+TRAFFIC_PROFILE = "gemm_bf16_256x256_2sm_2048x2048x4096"   # a mid-size landscape cell of the dominant kernel
+
+
+def dominant_traffic(variant_name):
+    """DRAM traffic per launch of the dominant kernel on one captured mid-size landscape cell, from the ncu
+    capture in profiles/ (null when the kernel differs from the captured one or the source changed since)."""
+    path = os.path.join(ROOT, "profiles", TRAFFIC_PROFILE + ".json")
+    if variant_name != CAPTURE_VARIANT or not os.path.exists(path):
+        return {"traffic": None, "traffic_note": "no capture of this kernel on a landscape cell"}
+    prof = json.load(open(path))
+    if prof["kernel_source_sha256"] != kernel_source_hash():
+        return {"traffic": None, "traffic_note": "the kernel source changed since the capture"}
+    t = prof["dram_bytes_read"] + prof["dram_bytes_write"]
+    return {"traffic": t, "traffic_cell": prof["shape"], "traffic_over_algorithmic": t / prof["algorithmic_bytes"],
+            "traffic_note": prof["l2_resident"]}
 
 
 def roofline_capture(rg, ctx, p_burst, dev, reps=10):

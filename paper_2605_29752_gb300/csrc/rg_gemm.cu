@@ -521,7 +521,11 @@ __device__ __forceinline__ void gemm_body(Sched& sched, float* ws, int32_t* tick
 #if RG_PHASE_TIMERS
   const long long t_entry = clock64();
   unsigned long long* trace_row = trace ? trace + static_cast<size_t>(blockIdx.x) * kTraceFields : nullptr;
-  if (trace_row && threadIdx.x == 0) trace_row[0] = global_ns();
+  if (trace_row && threadIdx.x == 0) {
+    trace_row[0] = global_ns();
+    for (int f = 3; f < kTraceFields; ++f) trace_row[f] = 0;  // stamps this launch may not reach
+  }
+  __syncthreads();
 #else
   (void)trace;
 #endif
