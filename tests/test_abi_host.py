@@ -306,3 +306,36 @@ def test_surface_stats_bit_exact_over_a_wide_dynamic_range(rg):
     assert np.array_equal(tf.reshape(shape), S)
     assert mean == roughness.mean(S)
     assert r == roughness.roughness_all(S)
+
+
+def test_fp8_plan_tables_match_oracle(rg):
+    """An FP8 plan (FP8 variant ids) is the same DP over the same table: bit-exact with the oracle."""
+    rng = np.random.default_rng(31)
+    vids = [rg.fp8_variant(t, s) for t in range(2) for s in (1, 2, 4, 8)]
+    T0v = rng.integers(1, 300, size=(len(vids), 4, 3, 5)).astype(np.int64)
+    _compare_plan(rg, T0v, vids, (4, 3, 5))
+
+
+def test_plan_build_refuses_mixed_precisions(rg):
+    g = _grid(rg, 2, 2, 2)
+    with pytest.raises(rg.RGError) as e:
+        rg.rg_plan_build(g, np.ones((2, 8), np.int64), [1, rg.fp8_variant(0, 1)])
+    assert e.value.code == rg.RG_ERR_INVALID
+    with pytest.raises(rg.RGError):
+        rg.rg_plan_build(g, np.ones((1, 8), np.int64), [rg.RG_NUM_VARIANTS])            # neither range
+
+
+def test_plan_file_of_another_version_is_refused(rg, tmp_path):
+    """A plan file whose version field differs (variant numbering of another library version) is refused."""
+    T0 = np.arange(1, 9, dtype=np.int64).reshape(1, -1)
+    h = rg.rg_plan_build(_grid(rg, 2, 2, 2), T0, [5])
+    p = str(tmp_path / "plan.bin")
+    try:
+        rg.rg_plan_save(h, p)
+    finally:
+        rg.rg_plan_free(h)
+    data = bytearray(open(p, "rb").read())
+    assert data[:8] == b"RGPLAN01"
+    data[8:12] = (1).to_bytes(4, "little")                  # the version field
+    open(p, "wb").write(bytes(data))
+    assert rg.rg_plan_load_status(p) == rg.RG_ERR_PLAN_MISMATCH

@@ -7,12 +7,13 @@ tables and values equal to the oracle's bit for bit; this module re-collects the
 with the gpu marker, so that they also run against the build whose numbers a
 benchmark on that host reports: full-grid T0*/T1/T2/action/q, leaves, the
 tie-heavy seeded cases, surface statistics (including the wide dynamic range),
-landscapes, rg_decompose, rg_kol and the pad-only fine-grid plan."""
+landscapes, rg_decompose, rg_kol, the pad-only fine-grid plan and FP8 plans."""
 import pytest
 
 from test_abi_host import (  # noqa: F401  (re-collected tests and their fixture)
     rg,
     test_decompose_matches_oracle_bit_exact,
+    test_fp8_plan_tables_match_oracle,
     test_kol_matches_oracle,
     test_landscapes_match_oracle_bit_exact,
     test_library_exports_every_header_function,
