@@ -132,8 +132,9 @@ def single_shape_fp8(args, rg, torch):
 
 
 def single_shape(args):
-    """Time one GEMM configuration: `reps` back-to-back launches between CUDA events (and, with
-    --phase-timers, one traced launch of the phase-timer build)."""
+    """Time one GEMM configuration: `reps` back-to-back launches under the landscape's protocol (and a
+    Python loop of rg_gemm calls, which also times the host), and, with --phase-timers, the last of
+    five back-to-back launches of the phase-timer build."""
     if args.phase_timers:
         os.environ["RG_LIBRARY"] = os.path.join(ROOT, "paper_2605_29752_gb300", "librg_timers.so")
     import torch
@@ -160,20 +161,26 @@ def single_shape(args):
     torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     rg.rg_check(ctx)
+    us_host = e0.elapsed_time(e1) / args.reps * 1e3
+    # The landscape's protocol: a device spin lets the host enqueue all `reps` launches first, so the
+    # events time back-to-back device work (the Python loop above also times the host's launch rate).
+    grid = rg.make_grid((M, 128, 1), (N, 128, 1), (K, 128, 1))
+    opts = rg.rg_sweep_opts_default()
+    opts.reps, opts.warmup, opts.shuffle, opts.prune_splits = args.reps, 1, 0, 0
+    us = float(rg.rg_sweep(ctx, grid, [v], A, B, C, opts)[0, 0]) * 1e-3
     phases = None
     if args.phase_timers:
         rg.rg_phase_trace(ctx, True)
-        for _ in range(5):          # back to back, as the sweep times them: the buffer keeps the last launch's
-            rg.rg_gemm(ctx, M, N, K, A, K, B, N, C, N, v)
+        opts.reps = 5               # the buffer keeps the last of the back-to-back launches
+        rg.rg_sweep(ctx, grid, [v], A, B, C, opts)
         torch.cuda.synchronize()
         phases = phase_summary(rg.rg_phase_trace_read(ctx))
         rg.rg_phase_trace(ctx, False)
     rg.rg_destroy(ctx)
-    us = e0.elapsed_time(e1) / args.reps * 1e3
     tf = 2.0 * M * N * K / (us * 1e-6) / 1e12
     byts = 2 * M * K + 2 * K * N + 4 * M * N
     line = {"shape": [M, N, K], "variant": args.variant, "us_per_launch": us, "tflops": tf,
-            "algorithmic_bytes": byts, "algorithmic_flops": 2 * M * N * K}
+            "us_per_call_python_loop": us_host, "algorithmic_bytes": byts, "algorithmic_flops": 2 * M * N * K}
     if phases is not None:
         line["phase_times"] = phases
         line["library"] = "librg_timers.so (phase stamps compiled in; the timed launches carry them too)"
@@ -1105,8 +1112,9 @@ def serving(rg, ctx, plan, A, B, count, n_req=20000, n_warm=1000, tile=1):
 
 def fp8_landscape(rg, ctx, dev, count, p_bf16):
     """FP8 e4m3 block-scaled GEMM on the {512..4096 step 512}^3 subgrid: the autotune table over the
-    eight FP8 variants (128x256 and 128x128 tiles x split-K 1/2/4/8), the DP plan built from it, and
-    the plan re-measured.  Returns the report block and the state the error check needs."""
+    twelve FP8 variants (128x256, 128x128 and the 256x256 cta_group::2 pair x split-K 1/2/4/8), the DP
+    plan built from it, and the plan re-measured.  Returns the report block and the state the error
+    check needs."""
     import torch
     Mx = STEP * count
     if Mx < 512:
@@ -1146,13 +1154,14 @@ def fp8_landscape(rg, ctx, dev, count, p_bf16):
     out = {"grid": f"{{512..{Mx} step 512}}^3", "cells": int(t.shape[1]),
            "variants": [rg.fp8_variant_name(v) for v in vids],
            "fixed_128x256": block(t[fixed], tf[fixed], st[fixed]),
-           "best_of_8_table": {"mean_tflops": float(bst), "R_N_slice": float(btf["R_N_slice"]),
+           "best_of_variants_table": {"mean_tflops": float(bst), "R_N_slice": float(btf["R_N_slice"]),
                                "R_3D": float(btf["R_3D"])},
            "plan_measured": block(tp[0], tfp[0], stp[0]),
            "winners": {rg.fp8_variant_name(v): float(np.mean(tb["vstar"].ravel() == v))
                        for v in sorted(set(tb["vstar"].ravel().tolist()))},
            "dp_actions": {a: float(np.mean(tb["action"] == i)) for i, a in enumerate(("keep", "M", "N", "K"))},
-           "tflops_4096cube": {"fixed_128x256": float(tf[fixed][i4096]), "plan": float(tfp[0][i4096])},
+           "tflops_4096cube": {"fixed_128x256": float(tf[fixed][i4096]), "plan": float(tfp[0][i4096]),
+                               "pair_256x256": float(tf[vids.index(rg.fp8_variant(rg.FP8_PAIR_TILE, 1))][i4096])},
            "peak_note": "FP8 roofline = 2 x the measured BF16 burst peak (the nominal ratio; no FP8 peak measured)",
            "scales": "per-128x128-block FP32 scales; the sweep reads compact scale arrays for each cell's "
                      "contiguous operand prefixes (timing only)"}

@@ -66,11 +66,15 @@ enum {
 };
 #define RG_NUM_SPLITS 4
 #define RG_VARIANT(tile, log2_split) ((tile) * RG_NUM_SPLITS + (log2_split))
-/* Stream-K variant of a tile (ids 24..29, after the split-K ids): whole waves of
- * tiles run data-parallel; the remainder tiles' K iterations are divided evenly
- * among at most one CTA per SM (each CTA at least 4 K blocks, at most 2 CTAs per
- * tile); a tile whose iterations span two CTAs is summed by its last arriving
- * piece in the fixed order of their K ranges. */
+/* Stream-K variant of a tile (ids 24..29, after the split-K ids): with T = wP + r
+ * tiles on P SMs (0 < r < P), either all whole waves but the last run
+ * data-parallel and the K iterations of the last whole wave and the remainder
+ * are divided evenly among the P CTAs (w >= 1 and r <= P/4 or r >= P/2; each CTA
+ * gets at least one tile's worth, so at most 2 CTAs share a tile), or all whole
+ * waves run data-parallel and the r remainder tiles' iterations are divided
+ * evenly among up to min(2r, P) CTAs (each at least 4 K blocks).  A tile whose
+ * iterations span several CTAs is summed by its last arriving piece in the
+ * fixed order of their K ranges. */
 #define RG_VARIANT_SK(tile) (RG_NUM_TILES * RG_NUM_SPLITS + (tile))
 /* 2-SM variant of a 256-row tile (ids 30..33 for 256x128, 34..37 for 256x256,
  * split-K 1/2/4/8): a 2-CTA cluster computes one 256 x BN tile as a single
@@ -83,12 +87,11 @@ enum {
 #define RG_VARIANT_2SM(tile, log2_split) \
   (RG_NUM_TILES * RG_NUM_SPLITS + RG_NUM_TILES + ((tile) - RG_TILE_256x128) * RG_NUM_SPLITS + (log2_split))
 /* cta_group::2 stream-K variant of a 256-row tile (id 38 for 256x128, 39 for
- * 256x256): whole waves of 256 x BN pair tiles run data-parallel on the 2-CTA
- * clusters; the remainder tiles' K iterations are divided evenly among at most
- * one cluster per SM pair (each at least 4 K blocks, at most 2 clusters per
- * tile), and each CTA of a cluster sums its own 128 rows of a shared tile in
- * the fixed order of the pieces' K ranges.  It removes the partial last wave
- * that quantises the large cells (Sec. 9.4 names split-K as the remedy). */
+ * 256x256): the stream-K schedule above over 256 x BN pair tiles and the 2-CTA
+ * clusters (one per SM pair); each CTA of a cluster sums its own 128 rows of a
+ * shared tile in the fixed order of the pieces' K ranges.  It removes the
+ * partial last wave that quantises the large cells (Sec. 9.4 names split-K as
+ * the remedy). */
 #define RG_VARIANT_2SM_SK(tile) (RG_NUM_TILES * RG_NUM_SPLITS + RG_NUM_TILES + 2 * RG_NUM_SPLITS + \
                                  (tile) - RG_TILE_256x128)
 #define RG_NUM_VARIANTS (RG_NUM_TILES * RG_NUM_SPLITS + RG_NUM_TILES + 2 * RG_NUM_SPLITS + 2)
@@ -130,8 +133,8 @@ typedef struct {
                                  split-K (S > 1, also cta_group::2) where the unsplit
                                  CTA count already fills the SMs or a split would get
                                  fewer than 2 K blocks; stream-K (also cta_group::2)
-                                 where there is no whole wave or the remainder is not
-                                 spread over more CTAs than it has tiles;
+                                 where the tiles fill no whole wave or no tile is
+                                 split;
                                  cta_group::2 pairs with M <= 128                     */
   int32_t shard_index;        /* with shard_count > 1: this call times only the items at
                                  positions shard_index, shard_index + shard_count, ... of
@@ -421,10 +424,13 @@ int rg_serve_stop(rg_server* server, rg_serve_stats* stats);
  * produced by rg_fp8_quantize.  qA, qB, C 16-byte aligned; lda, ldb multiples of
  * 16; ldc a multiple of 4.  Device pointers, stream-ordered.
  * FP8 kernel variants (ids in their own range, RG_FP8_VARIANT_BASE + ...): the
- * 128 x 256 and 128 x 128 output tiles (FP8 tile 0 and 1), each with in-kernel
- * split-K S = 1/2/4/8, id = RG_FP8_VARIANT(tile, log2(S)).  Split-K partials go
- * through the context's workspace and are summed by the last arriving split in
- * the fixed order 0..S-1, so results are deterministic.
+ * 128 x 256 and 128 x 128 output tiles (FP8 tile 0 and 1) and the 256 x 256 tile
+ * as a tcgen05 cta_group::2 pair on a 2-CTA cluster (FP8 tile 2: each CTA loads
+ * its 128 rows of A and 128 columns of B, and promotes and stores its own 128
+ * output rows), each with in-kernel split-K S = 1/2/4/8, id =
+ * RG_FP8_VARIANT(tile, log2(S)).  Split-K partials go through the context's
+ * workspace and are summed by the last arriving split in the fixed order
+ * 0..S-1, so results are deterministic.
  * rg_gemm_fp8_ex: one launch of `variant`, beta = 0 writes C, beta = 1 adds into
  * it; (pm, pn, pk) >= (M, N, K) run it as the zero-padded problem of that size (0
  * = same), never materialised (zero-filled reads, clipped stores, scales of
@@ -438,7 +444,7 @@ int rg_serve_stop(rg_server* server, rg_serve_stats* stats);
  * must be multiples of 128 (grid steps that are), else RG_ERR_SHAPE.  A BF16
  * plan is refused (RG_ERR_INVALID), as rg_gemm_plan refuses an FP8 plan. */
 #define RG_FP8_VARIANT_BASE 64
-#define RG_FP8_NUM_TILES 2
+#define RG_FP8_NUM_TILES 3
 #define RG_FP8_VARIANT(tile, log2_split) (RG_FP8_VARIANT_BASE + (tile) * RG_NUM_SPLITS + (log2_split))
 #define RG_FP8_NUM_VARIANTS (RG_FP8_NUM_TILES * RG_NUM_SPLITS)
 int rg_fp8_quantize(rg_ctx* ctx, const float* X, int64_t rows, int64_t cols, int64_t ldx, uint8_t* Q,
@@ -452,7 +458,8 @@ int rg_gemm_fp8_plan(rg_ctx* ctx, const rg_plan* plan, int64_t M, int64_t N, int
                      int64_t lda, const float* sA, int64_t lds_a, const uint8_t* qB, int64_t ldb, const float* sB,
                      int64_t lds_b, float* C, int64_t ldc, void* stream);
 /* Times FP8 GEMMs on every cell of `grid` with the sweep protocol and outputs of
- * rg_sweep (same options; split pruning as rg_sweep's for split-K): n_variants
+ * rg_sweep (same options; split pruning as rg_sweep's for split-K, and the pair
+ * tile pruned where M <= 128): n_variants
  * FP8 variant ids, or a plan (n_variants = 1, ids ignored).  Cell (M, N, K) uses
  * the contiguous prefixes qA[0 : M*K] (lda = K) and qB[0 : K*N] (ldb = N) with
  * compact scale arrays read from sA and sB (they must hold the largest cell's

@@ -19,6 +19,9 @@
 //              store (beta = 0) or reduce-add (beta = 1).  With S > 1 the unit's partial
 //              goes to the split-K workspace instead, and the last arriving split of a
 //              (tile, warp) sums the S partials in the fixed order 0..S-1.
+// The 256 x 256 tile also runs as a tcgen05 cta_group::2 pair (gemm_fp8_2sm_kernel):
+// each CTA of a 2-CTA cluster loads its 128 rows of A and 128 columns of B, the even
+// CTA issues the M = 256 MMAs, and each CTA promotes and stores its own 128 rows.
 // Padding is never materialised: tensor maps carry the logical extents, reads
 // past them are zero-filled, stores clipped, and scales outside the logical
 // blocks read as 0.  Every mbarrier wait is bounded; on expiry the kernel
@@ -51,21 +54,37 @@ constexpr int STAGING_PER_WARP = 2 * 4096;
 constexpr long long kDrainCycles = 1LL << 30;
 constexpr uint32_t FULL = 0xffffffffu;
 
-template <int BN>
+// PAIR: a cta_group::2 pair computes a 256 x BN tile; each CTA loads its 128 rows of A
+// and BN / 2 columns of B and holds its 128 output rows x BN columns in its own TMEM.
+template <int BN, bool PAIR = false>
 struct Cfg {
-  static constexpr int STAGES = BN == 256 ? 3 : 4;
+  static constexpr int CTAS = PAIR ? 2 : 1;
+  static constexpr int STAGES = PAIR ? 5 : BN == 256 ? 3 : 4;
   static constexpr int A_BYTES = BM * BK;
-  static constexpr int B_BYTES = BK * BN;     // BN / 128 N-major column boxes of BK rows
+  static constexpr int B_BYTES = BK * BN / CTAS;  // (BN / CTAS) / 128 N-major column boxes of BK rows
   static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
   static constexpr int TMEM_COLS = NACC * BN;
   static constexpr int STAGING_OFF = STAGES * STAGE_BYTES;
   static constexpr int BAR_OFF = STAGING_OFF + kEpiWarps * STAGING_PER_WARP;
   static constexpr int SMEM_BYTES = 1024 + BAR_OFF + 256;
   static constexpr int HALF = BN / 2;         // columns per promotion warp
-  static constexpr uint32_t IDESC = instr_desc(0, 0, 0, 1, 128, BN);  // E4M3 x E4M3, A K-major, B MN-major
+  // E4M3 x E4M3, A K-major, B MN-major; M = 256 across a pair
+  static constexpr uint32_t IDESC = instr_desc(0, 0, 0, 1, 128 * CTAS, BN);
   static_assert(SMEM_BYTES <= 232448, "shared memory budget");
   static_assert(BN == 128 || BN == 256, "tile width");
+  static_assert(!PAIR || BN == 256, "pair tile");
 };
+
+// D (+)= A * B across a CTA pair (cta_group::2, M = 256 per instruction), e4m3 inputs, F32 accumulator.
+__device__ __forceinline__ void mma_f8_pair(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                            uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::2.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
 
 struct Args {
   int32_t M, N;            // logical output extents
@@ -109,14 +128,16 @@ __device__ __forceinline__ void put_block(const CUtensorMap* map, const float* v
   sbuf ^= 1;
 }
 
-// SPLIT = false: the instance for S = 1 (no workspace path, so its promotion loop,
-// which holds BN / 2 accumulators per thread, carries no split-K state).
-template <int BN, bool SPLIT>
-__global__ void __launch_bounds__(kThreads, 1)
-    gemm_fp8_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                    const __grid_constant__ CUtensorMap tmC, const __grid_constant__ CUtensorMap tmW,
-                    const Args args) {
-  using C = Cfg<BN>;
+// The kernel body.  SPLIT = false: the instance for S = 1 (no workspace path, so its
+// promotion loop, which holds BN / 2 accumulators per thread, carries no split-K
+// state).  PAIR: one CTA of a cta_group::2 pair (launched as 2-CTA clusters): units
+// are (256-row pair tile, split); both CTAs load their operand halves, the even
+// CTA's lane issues the pair MMAs, and each CTA promotes and stores its own 128
+// rows; tiles, tickets and workspace rows count 128-row tiles (tiles_m is even).
+template <int BN, bool SPLIT, bool PAIR>
+__device__ __forceinline__ void fp8_body(const CUtensorMap& tmA, const CUtensorMap& tmB, const CUtensorMap& tmC,
+                                         const CUtensorMap& tmW, const Args& args) {
+  using C = Cfg<BN, PAIR>;
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw_s = smem_u32(smem_raw);
   uint8_t* smem = smem_raw + ((1024u - (raw_s & 1023u)) & 1023u);
@@ -135,11 +156,26 @@ __global__ void __launch_bounds__(kThreads, 1)
 
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
-  const int ntiles = args.tiles_m * args.tiles_n;
+  const int ntiles = args.tiles_m * args.tiles_n;  // 128-row tiles
   const int S = SPLIT ? args.splits : 1;
-  const int total = ntiles * S;
-  // unit u = (tile u / S, split u % S) runs K blocks [s * kblocks / S, (s + 1) * kblocks / S)
+  const int rank = PAIR ? static_cast<int>(cluster_ctarank()) : 0;
+  const int cid = PAIR ? static_cast<int>(blockIdx.x) / 2 : static_cast<int>(blockIdx.x);
+  const int ncl = PAIR ? static_cast<int>(gridDim.x) / 2 : static_cast<int>(gridDim.x);
+  const int total = (PAIR ? ntiles / 2 : ntiles) * S;
+  // unit u = ((pair) tile u / S, split u % S) runs K blocks [s * kblocks / S, (s + 1) * kblocks / S)
   auto kb_lo = [&](int s) { return S == 1 ? 0 : s * args.kblocks / S; };
+  // this CTA's 128-row tile of unit u: tile index (tickets, workspace) and coordinates
+  auto tile_of = [&](int u, int& tm, int& tn) {
+    const int t = u / S;
+    if constexpr (PAIR) {
+      tm = 2 * (t / args.tiles_n) + rank;
+      tn = t % args.tiles_n;
+    } else {
+      tm = t / args.tiles_n;
+      tn = t % args.tiles_n;
+    }
+    return tm * args.tiles_n + tn;
+  };
 
   if (threadIdx.x == 0) {
     prefetch_tmap(&tmA);
@@ -151,18 +187,24 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     for (int b = 0; b < NACC; ++b) {
       mbar_init(tfull_bar(b), 1);
-      mbar_init(tempty_bar(b), kEpiWarps);
+      mbar_init(tempty_bar(b), PAIR ? 2 * kEpiWarps : kEpiWarps);  // pair: both CTAs' warps, on the even CTA
     }
     mbar_init(drain_bar, 1);
     *abort_flag = 0;
     fence_mbar_init();
   }
   if (warp == 1) {
-    tmem_alloc(smem_u32(tmem_slot), C::TMEM_COLS);
-    tmem_relinquish();
+    if constexpr (PAIR) {  // collective with the partner's warp 1: the same columns in both CTAs
+      tmem_alloc_pair(smem_u32(tmem_slot), C::TMEM_COLS);
+      tmem_relinquish_pair();
+    } else {
+      tmem_alloc(smem_u32(tmem_slot), C::TMEM_COLS);
+      tmem_relinquish();
+    }
   }
   tc_fence_before();
   __syncthreads();
+  if constexpr (PAIR) cluster_sync();  // the partner's barriers are initialised
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
   grid_dependency_wait();
@@ -173,9 +215,10 @@ __global__ void __launch_bounds__(kThreads, 1)
       int stage = 0, fills = 0;
       uint32_t ph = 0, issued_mask = 0, issued_ph = 0;
       bool ok = true;
-      for (int u = blockIdx.x; ok && u < total; u += gridDim.x) {
-        const int tile = u / S, s = u % S;
-        const int tm = tile / args.tiles_n, tn = tile % args.tiles_n;
+      for (int u = cid; ok && u < total; u += ncl) {
+        const int s = u % S;
+        int tm, tn;
+        tile_of(u, tm, tn);
         const int kb1 = s + 1 == S ? args.kblocks : kb_lo(s + 1);
         for (int kb = kb_lo(s); kb < kb1; ++kb) {
           if (fills >= C::STAGES && !mbar_wait(empty_bar(stage), ph ^ 1u, args.timeout, abort_flag)) {
@@ -184,11 +227,19 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
           ++fills;
           const uint32_t sa = sbase + stage * C::STAGE_BYTES;
-          mbar_arrive_expect_tx(full_bar(stage), C::STAGE_BYTES);
-          tma_load_2d(sa, &tmA, full_bar(stage), kb * BK, tm * BM);
+          if constexpr (PAIR) {
+            // both CTAs' loads complete on the even CTA's full barrier, which expects both halves
+            if (rank == 0) mbar_arrive_expect_tx(full_bar(stage), 2 * C::STAGE_BYTES);
+            const uint32_t fb = mapa_shared(full_bar(stage), 0);
+            tma_load_2d_pair(sa, &tmA, fb, kb * BK, tm * BM);
+            tma_load_2d_pair(sa + C::A_BYTES, &tmB, fb, tn * BN + rank * (BN / 2), kb * BK);
+          } else {
+            mbar_arrive_expect_tx(full_bar(stage), C::STAGE_BYTES);
+            tma_load_2d(sa, &tmA, full_bar(stage), kb * BK, tm * BM);
 #pragma unroll
-          for (int j = 0; j < BN / 128; ++j)
-            tma_load_2d(sa + C::A_BYTES + j * (BK * 128), &tmB, full_bar(stage), tn * BN + j * 128, kb * BK);
+            for (int j = 0; j < BN / 128; ++j)
+              tma_load_2d(sa + C::A_BYTES + j * (BK * 128), &tmB, full_bar(stage), tn * BN + j * 128, kb * BK);
+          }
           issued_mask |= 1u << stage;
           issued_ph = (issued_ph & ~(1u << stage)) | (ph << stage);
           if (++stage == C::STAGES) {
@@ -201,16 +252,26 @@ __global__ void __launch_bounds__(kThreads, 1)
         atomicExch(args.err, 1);
         *abort_flag = 1;
       }
-      for (int i = 0; i < C::STAGES; ++i)
-        if (issued_mask & (1u << i)) mbar_wait(full_bar(i), (issued_ph >> i) & 1u, kDrainCycles, no_abort);
+      // no TMA write may still be landing when the CTA exits
+      if (!PAIR || rank == 0) {
+        for (int i = 0; i < C::STAGES; ++i)
+          if (issued_mask & (1u << i)) mbar_wait(full_bar(i), (issued_ph >> i) & 1u, kDrainCycles, no_abort);
+      } else if (!ok) {
+        // the odd CTA's loads complete on its partner's barriers; after an abort it gives
+        // them a bounded time to land (normally every one of them was consumed)
+        const long long t0 = clock64();
+        while (clock64() - t0 < (kDrainCycles >> 6)) {
+        }
+      }
     }
   } else if (warp == 1) {
-    // Lane 0 alone issues the MMAs and commits (no per-K-block warp vote).
-    if (lane == 0) {
+    // Lane 0 alone issues the MMAs and commits (no per-K-block warp vote); a pair's
+    // odd CTA issues nothing: the even CTA's MMAs read and write both.
+    if (lane == 0 && (!PAIR || rank == 0)) {
       int stage = 0, acc = 0;
       uint32_t ph = 0, aph = 0;
       bool ok = true;
-      for (int u = blockIdx.x; ok && u < total; u += gridDim.x) {
+      for (int u = cid; ok && u < total; u += ncl) {
         const int s = u % S;
         const int kb1 = s + 1 == S ? args.kblocks : kb_lo(s + 1);
         for (int kb = kb_lo(s); kb < kb1; ++kb) {
@@ -226,11 +287,21 @@ __global__ void __launch_bounds__(kThreads, 1)
           const uint64_t adesc0 = smem_desc_sw128(sa, 16, 1024);
           const uint64_t bdesc0 = smem_desc_sw128(sb, BK * 128, 1024);  // column boxes BK*128 apart
 #pragma unroll
-          for (int k = 0; k < BK / 32; ++k)
-            mma_f8(d, adesc0 + static_cast<uint64_t>((k * 32) >> 4), bdesc0 + static_cast<uint64_t>((k * (32 * 128)) >> 4),
-                   C::IDESC, k > 0 ? 1u : 0u);
-          mma_commit(empty_bar(stage));
-          mma_commit(tfull_bar(acc));
+          for (int k = 0; k < BK / 32; ++k) {
+            const uint64_t ad = adesc0 + static_cast<uint64_t>((k * 32) >> 4);
+            const uint64_t bd = bdesc0 + static_cast<uint64_t>((k * (32 * 128)) >> 4);
+            if constexpr (PAIR)
+              mma_f8_pair(d, ad, bd, C::IDESC, k > 0 ? 1u : 0u);
+            else
+              mma_f8(d, ad, bd, C::IDESC, k > 0 ? 1u : 0u);
+          }
+          if constexpr (PAIR) {
+            mma_commit_pair_multicast(empty_bar(stage), 3);  // the stage is free in both CTAs
+            mma_commit_pair_multicast(tfull_bar(acc), 3);    // both CTAs' rows of the product are ready
+          } else {
+            mma_commit(empty_bar(stage));
+            mma_commit(tfull_bar(acc));
+          }
           if (++stage == C::STAGES) {
             stage = 0;
             ph ^= 1u;
@@ -244,7 +315,10 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (!ok) {
         atomicExch(args.err, 2);
         *abort_flag = 1;
-        mma_commit(drain_bar);
+        if constexpr (PAIR)
+          mma_commit_pair(drain_bar);
+        else
+          mma_commit(drain_bar);  // completes once every issued MMA has finished
         mbar_wait(drain_bar, 0, kDrainCycles, no_abort);
       }
     }
@@ -258,9 +332,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     int acc = 0, sbuf = 0;
     uint32_t aph = 0;
     bool ok = true;
-    for (int u = blockIdx.x; ok && u < total; u += gridDim.x) {
-      const int tile = u / S, s = u % S;
-      const int tm = tile / args.tiles_n, tn = tile % args.tiles_n;
+    for (int u = cid; ok && u < total; u += ncl) {
+      const int s = u % S;
+      int tm, tn;
+      const int tile = tile_of(u, tm, tn);
       const int kb1 = s + 1 == S ? args.kblocks : kb_lo(s + 1);
       const int nb = (tn * BN + hc * C::HALF) / SB;  // this half's scale block column
       // scale rows and the last K block with real scales (0 outside the logical blocks: padding)
@@ -288,7 +363,12 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         tc_fence_before();
         __syncwarp();
-        if (lane == 0) mbar_arrive(tempty_bar(acc));
+        if (lane == 0) {
+          if constexpr (PAIR)
+            mbar_arrive_cluster(mapa_shared(tempty_bar(acc), 0));  // the even CTA's MMA reuses it
+          else
+            mbar_arrive(tempty_bar(acc));
+        }
         if (++acc == NACC) {
           acc = 0;
           aph ^= 1u;
@@ -373,10 +453,33 @@ __global__ void __launch_bounds__(kThreads, 1)
     __syncwarp();
   }
   __syncthreads();
+  // no CTA of a pair exits while its partner may still arrive on its barriers or run
+  // MMAs on its shared memory and TMEM
+  if constexpr (PAIR) cluster_sync();
   if (warp == 1) {
     tc_fence_after();
-    tmem_dealloc(tmem_base, C::TMEM_COLS);
+    if constexpr (PAIR)
+      tmem_dealloc_pair(tmem_base, C::TMEM_COLS);
+    else
+      tmem_dealloc(tmem_base, C::TMEM_COLS);
   }
+}
+
+template <int BN, bool SPLIT>
+__global__ void __launch_bounds__(kThreads, 1)
+    gemm_fp8_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                    const __grid_constant__ CUtensorMap tmC, const __grid_constant__ CUtensorMap tmW,
+                    const Args args) {
+  fp8_body<BN, SPLIT, false>(tmA, tmB, tmC, tmW, args);
+}
+
+// The 256 x 256 tile as a cta_group::2 pair (grid: 2 CTAs per cluster).
+template <bool SPLIT>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
+    gemm_fp8_2sm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                        const __grid_constant__ CUtensorMap tmC, const __grid_constant__ CUtensorMap tmW,
+                        const Args args) {
+  fp8_body<256, SPLIT, true>(tmA, tmB, tmC, tmW, args);
 }
 
 // One CTA per 128 x 128 block: amax, scale = amax / 448 (1 for an all-zero
@@ -421,10 +524,18 @@ struct TileInfo {
   KernFn fn;        // S = 1
   KernFn fn_split;  // S > 1
   int bn, smem;
+  bool pair;        // cta_group::2: 256 x bn tiles on 2-CTA clusters
 };
+// FP8 tiles: 0 = 128 x 256, 1 = 128 x 128, 2 = 256 x 256 as a cta_group::2 pair.
 static TileInfo tile_info(int tile) {
-  return tile == 0 ? TileInfo{gemm_fp8_kernel<256, false>, gemm_fp8_kernel<256, true>, 256, Cfg<256>::SMEM_BYTES}
-                   : TileInfo{gemm_fp8_kernel<128, false>, gemm_fp8_kernel<128, true>, 128, Cfg<128>::SMEM_BYTES};
+  switch (tile) {
+    case 0:
+      return TileInfo{gemm_fp8_kernel<256, false>, gemm_fp8_kernel<256, true>, 256, Cfg<256>::SMEM_BYTES, false};
+    case 1:
+      return TileInfo{gemm_fp8_kernel<128, false>, gemm_fp8_kernel<128, true>, 128, Cfg<128>::SMEM_BYTES, false};
+    default:
+      return TileInfo{gemm_fp8_2sm_kernel<false>, gemm_fp8_2sm_kernel<true>, 256, Cfg<256, true>::SMEM_BYTES, true};
+  }
 }
 
 // The kernels' shared-memory limit, once per device.
@@ -497,7 +608,9 @@ static int prepare(const Fp8CtxInfo& info, int64_t M, int64_t N, int64_t K, cons
   const int tile = (variant - RG_FP8_VARIANT_BASE) / RG_NUM_SPLITS;
   const int splits = 1 << ((variant - RG_FP8_VARIANT_BASE) % RG_NUM_SPLITS);
   const TileInfo ti = tile_info(tile);
-  const int64_t tiles_m = (pm + BM - 1) / BM, tiles_n = (pn + ti.bn - 1) / ti.bn, kblocks = (pk + BK - 1) / BK;
+  int64_t tiles_m = (pm + BM - 1) / BM;
+  if (ti.pair) tiles_m += tiles_m & 1;  // whole 256-row pair tiles (an odd CTA past M loads zeros, stores nothing)
+  const int64_t tiles_n = (pn + ti.bn - 1) / ti.bn, kblocks = (pk + BK - 1) / BK;
   const int64_t ntiles = tiles_m * tiles_n;
   if (splits > 1 && (splits * ntiles * BM * ti.bn * 4 > info.ws_bytes || ntiles * kEpiWarps > info.max_tickets))
     return fail(RG_ERR_SHAPE, "FP8 GEMM: split-K workspace too small for this shape");
@@ -534,7 +647,8 @@ static int prepare(const Fp8CtxInfo& info, int64_t M, int64_t N, int64_t K, cons
   g.timeout = info.timeout;
   L->fn = splits > 1 ? ti.fn_split : ti.fn;
   L->smem = ti.smem;
-  L->grid = dim3(static_cast<unsigned>(std::min<int64_t>(ntiles * splits, info.sms)));
+  L->grid = ti.pair ? dim3(static_cast<unsigned>(2 * std::min<int64_t>(ntiles / 2 * splits, info.sms / 2)))
+                    : dim3(static_cast<unsigned>(std::min<int64_t>(ntiles * splits, info.sms)));
   return RG_OK;
 }
 
@@ -684,19 +798,22 @@ extern "C" int rg_sweep_fp8(rg_ctx* ctx, const rg_grid* grid, int32_t n_variants
     *N = rg::axis_value(grid->n, (cell / nk) % nn);
     *K = rg::axis_value(grid->k, cell % nk);
   };
-  if (o.prune_splits && !plan) {  // a split is worth timing only where the unsplit tiles leave SMs idle
+  // a split is worth timing only where the unsplit tiles leave SMs idle (counting both CTAs of
+  // a pair tile), a pair tile only beyond 128 rows
+  if (o.prune_splits && !plan) {
     std::vector<int64_t> keep;
     keep.reserve(order.size());
     for (int64_t it : order) {
       const int32_t v = variant_ids[it / cells];
       const int S = 1 << ((v - RG_FP8_VARIANT_BASE) % RG_NUM_SPLITS);
-      bool pruned = false;
-      if (S > 1) {
-        int64_t M, N, K;
-        dims(it, &M, &N, &K);
-        const int bn = tile_info((v - RG_FP8_VARIANT_BASE) / RG_NUM_SPLITS).bn;
-        const int64_t tiles = ((M + BM - 1) / BM) * ((N + bn - 1) / bn);
-        pruned = tiles >= info.sms || (K + BK - 1) / BK < 2 * S;
+      const TileInfo ti = tile_info((v - RG_FP8_VARIANT_BASE) / RG_NUM_SPLITS);
+      int64_t M, N, K;
+      dims(it, &M, &N, &K);
+      bool pruned = ti.pair && M <= 128;
+      if (S > 1 && !pruned) {
+        const int64_t rows = ti.pair ? 2 * ((M + 2 * BM - 1) / (2 * BM)) : (M + BM - 1) / BM;
+        const int64_t ctas = rows * ((N + ti.bn - 1) / ti.bn);
+        pruned = ctas >= info.sms || (K + BK - 1) / BK < 2 * S;
       }
       if (pruned)
         t_ns_out[it] = RG_T_UNMEASURED;

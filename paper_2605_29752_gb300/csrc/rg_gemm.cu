@@ -261,8 +261,9 @@ struct MemTwinSched : SingleSched<false> {
 };
 
 // Stream-K (hybrid): whole waves of tiles run data-parallel, one tile per CTA
-// per wave (tile g + i * G on CTA g, for tiles below dp_tiles = G * floor(T / G));
-// the remaining tiles' K iterations are divided evenly among the first tail CTAs:
+// per wave (tile g + i * G on CTA g, for tiles below dp_tiles: all whole waves,
+// or all but the last in sk_geometry's balanced form); the remaining tiles' K
+// iterations are divided evenly among the first tail CTAs:
 // CTA h owns tail iterations [h I / tail, (h+1) I / tail), processed as one
 // segment per tile it touches.  A tail tile covered by one segment is stored
 // directly; one split over several CTAs is summed by its last arriving segment
@@ -1821,8 +1822,8 @@ static int sweep_impl(rg_ctx* ctx, const rg_grid* grid, int32_t n_variants, cons
       const int64_t pairs = ((M + ts.bm - 1) / ts.bm) * ((N + ts.bn - 1) / ts.bn);
       if (sk) {  // as the 1-CTA stream-K rule, over clusters
         const int64_t clusters = ctx->sm_count / 2;
-        const rg::SkGeometry gsk = rg::sk_geometry(pairs, (K + rg::kBK - 1) / rg::kBK, clusters);
-        return pairs < clusters || gsk.tail_ctas <= pairs - gsk.dp_tiles;
+        return pairs < clusters ||
+               rg::sk_geometry(pairs, (K + rg::kBK - 1) / rg::kBK, clusters).max_pieces == 1;
       }
       if (S == 1) return false;
       return 2 * pairs >= ctx->sm_count || (K + rg::kBK - 1) / rg::kBK < 2 * S;
@@ -1833,9 +1834,8 @@ static int sweep_impl(rg_ctx* ctx, const rg_grid* grid, int32_t n_variants, cons
     const rg::TileShape ts = rg::tile_shape(rg::variant_tile(v));
     const int64_t tiles = ((M + ts.bm - 1) / ts.bm) * ((N + ts.bn - 1) / ts.bn);
     const int64_t kblocks = (K + rg::kBK - 1) / rg::kBK;
-    if (sk) {  // stream-K changes something only where whole waves leave a remainder spread over several CTAs
-      const rg::SkGeometry gsk = rg::sk_geometry(tiles, kblocks, ctx->sm_count);
-      return tiles < ctx->sm_count || gsk.tail_ctas <= tiles - gsk.dp_tiles;
+    if (sk) {  // stream-K is timed where the tiles fill a wave (split-K covers fewer) and it splits some tile
+      return tiles < ctx->sm_count || rg::sk_geometry(tiles, kblocks, ctx->sm_count).max_pieces == 1;
     }
     return tiles >= ctx->sm_count || kblocks < 2 * S;
   };

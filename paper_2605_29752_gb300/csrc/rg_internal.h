@@ -59,12 +59,27 @@ inline int variant_split(int v) {
          : v >= k2SmVariants     ? 1 << ((v - k2SmVariants) % RG_NUM_SPLITS)
                                  : 1 << (v % RG_NUM_SPLITS);
 }
-// Stream-K geometry shared by the launcher, the sweep's pruning and the kernel:
-// whole waves of tiles run data-parallel (one tile per CTA per wave); only the
-// remainder tiles are divided among tail_ctas CTAs by K iterations (each at
-// least kSkMinIters K blocks, at most kSkMaxPieces CTAs per tile).
+// Stream-K geometry shared by the launcher, the sweep's pruning and the kernel,
+// for T tiles on P CTAs with T = w P + r, 0 < r < P (whole waves with no
+// remainder run data-parallel).
+//  - Balanced form (w >= 1 and r <= P/4 or r >= P/2): all whole waves but the
+//    last run data-parallel (one tile per CTA per wave), and the K iterations of
+//    the last whole wave plus the remainder are divided evenly among all P CTAs.
+//    Each gets at least one tile's worth, so no tile spans more than 2 CTAs, and
+//    the partial wave costs 1 + r/P tiles of time per CTA instead of 2, at the
+//    price of one published partial per CTA.
+//  - Remainder form (w = 0, or P/4 < r < P/2): all whole waves run data-parallel
+//    and only the r remainder tiles' iterations are divided, among up to
+//    min(kSkMaxPieces r, P) CTAs (each at least kSkMinIters K blocks); the tail
+//    costs about half a tile and 2r partials.  With w = 0 a tile can span one
+//    more CTA than kSkMaxPieces; max_pieces counts it.
+// Measured on GB300 (sweep protocol, 9 shapes): the balanced form wins where r is
+// small (4096 x 1280 x 4096 on 256 x 256 pairs, r/P = 4/76: 36.9 against 41.0 us)
+// and where r >= P/2 (2176 x 1920 x 1152 on 128 x 128, r/P = 103/152: 18.7 against
+// 21.8 us); the remainder form where P/4 < r < P/2 (2560 x 2560 x 2048 on pairs,
+// 24/76: 28.2 against 31.5 us), since its 2r partials cost less than P of them.
 constexpr int64_t kSkMinIters = 4;
-// At most 2 pieces per tail tile: the last arriving piece then reads one other
+// About 2 pieces per tail tile: the last arriving piece then reads one other
 // partial, and that fixup, not the K loop, bounds the tail (phase timers: each
 // further partial adds about 0.3 us per 32-column chunk of a CTA's rows).
 constexpr int64_t kSkMaxPieces = 2;
@@ -76,17 +91,25 @@ struct SkGeometry {
 };
 inline SkGeometry sk_geometry(int64_t tiles, int64_t kblocks, int64_t sms) {
   SkGeometry g{};
-  g.dp_tiles = (tiles / sms) * sms;
-  const int64_t tail = tiles - g.dp_tiles;
-  g.grid = g.dp_tiles > 0 ? sms : 1;
+  const int64_t waves = tiles / sms, rem = tiles % sms;
+  g.grid = waves > 0 ? sms : 1;
   g.max_pieces = 1;
   g.tail_ctas = 0;
-  if (tail == 0) return g;
+  if (rem == 0) {
+    g.dp_tiles = tiles;
+    return g;
+  }
+  const bool balanced = waves > 0 && (4 * rem <= sms || 2 * rem >= sms);
+  g.dp_tiles = balanced ? (waves - 1) * sms : waves * sms;
+  const int64_t tail = tiles - g.dp_tiles;
   const int64_t iters = tail * kblocks;
-  int64_t c = iters / kSkMinIters;
-  if (c > tail * kSkMaxPieces) c = tail * kSkMaxPieces;
-  if (c > sms) c = sms;
-  if (c < 1) c = 1;
+  int64_t c = sms;
+  if (!balanced) {
+    c = iters / kSkMinIters;
+    if (c > tail * kSkMaxPieces) c = tail * kSkMaxPieces;
+    if (c > sms) c = sms;
+    if (c < 1) c = 1;
+  }
   g.tail_ctas = c;
   if (g.grid < c) g.grid = c;
   auto begin = [&](int64_t h) { return h * iters / c; };

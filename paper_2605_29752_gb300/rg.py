@@ -607,20 +607,22 @@ def rg_gemm_fp8(ctx, M, N, K, qA, lda, sA, qB, ldb, sB, Cp, ldc, stream=None) ->
 
 
 RG_FP8_VARIANT_BASE = 64
-RG_FP8_NUM_TILES = 2
+RG_FP8_NUM_TILES = 3
 RG_FP8_NUM_VARIANTS = RG_FP8_NUM_TILES * RG_NUM_SPLITS
-FP8_TILES = [(128, 256), (128, 128)]
+FP8_TILES = [(128, 256), (128, 128), (256, 256)]
+FP8_PAIR_TILE = 2                    # the 256x256 tile runs as a cta_group::2 pair
 
 
 def fp8_variant(tile: int, split: int = 1) -> int:
-    """FP8 variant id: tile 0 = 128x256, 1 = 128x128; in-kernel split-K 1/2/4/8."""
+    """FP8 variant id: tile 0 = 128x256, 1 = 128x128, 2 = 256x256 cta_group::2 pair; split-K 1/2/4/8."""
     return RG_FP8_VARIANT_BASE + tile * RG_NUM_SPLITS + SPLITS.index(split)
 
 
 def fp8_variant_name(v: int) -> str:
     t, s = divmod(v - RG_FP8_VARIANT_BASE, RG_NUM_SPLITS)
     bm, bn = FP8_TILES[t]
-    return f"fp8 {bm}x{bn}/S{SPLITS[s]}"
+    pair = "/2SM" if t == FP8_PAIR_TILE else ""
+    return f"fp8 {bm}x{bn}{pair}/S{SPLITS[s]}"
 
 
 def rg_gemm_fp8_ex(ctx, M, N, K, qA, lda, sA, lds_a, qB, ldb, sB, lds_b, Cp, ldc, variant_id, beta=0, pm=0, pn=0,

@@ -174,7 +174,7 @@ def _run_ex(rg, ctx, M, N, K, ops, v, beta=0, c0=None, pads=(0, 0, 0)):
     return C.cpu().numpy()
 
 
-FP8_VARIANTS = list(range(64, 72))
+FP8_VARIANTS = list(range(64, 76))          # 128x256, 128x128, 256x256 cta_group::2 pair; split-K 1/2/4/8
 
 
 @pytest.mark.parametrize("v", FP8_VARIANTS)
@@ -192,7 +192,7 @@ def test_fp8_every_variant_ragged_and_deterministic(rg, ctx, v):
         assert np.array_equal(C.cpu().numpy(), c)
 
 
-@pytest.mark.parametrize("v", [64, 65, 67, 68, 70])
+@pytest.mark.parametrize("v", [64, 65, 67, 68, 70, 72, 73, 75])
 def test_fp8_split_k_beta_and_padding(rg, ctx, v):
     M, N, K = 512, 384, 2048
     ops = _operands(rg, ctx, M, N, K, seed=6)
@@ -206,6 +206,21 @@ def test_fp8_split_k_beta_and_padding(rg, ctx, v):
     if rg.SPLITS[(v - 64) % 4] == 1:      # zero K padding adds exact zero products: the same bits
         assert np.array_equal(cp, c)
     assert np.array_equal(c, _run_ex(rg, ctx, M, N, K, ops, v, pads=(M + 128, N + 256, K)))
+
+
+@pytest.mark.parametrize("shape", [(1024, 768, 1024), (1000, 528, 640), (3968, 4096, 512)])
+def test_fp8_pair_matches_one_cta_tile(rg, ctx, shape):
+    """The 256x256 cta_group::2 pair computes each CTA's 128 rows x 256 columns with the same MMA
+    shape per row (N = 256, K = 32 steps) and the same promotion order as the 1-CTA 128x256 tile,
+    so their results agree bit for bit (ragged edges, and an odd CTA wholly past M)."""
+    M, N, K = shape
+    ops = _operands(rg, ctx, M, N, K, seed=9)
+    c1 = _run_ex(rg, ctx, M, N, K, ops, rg.fp8_variant(0, 1))
+    c2 = _run_ex(rg, ctx, M, N, K, ops, rg.fp8_variant(2, 1))
+    assert not np.any(np.isnan(c2))
+    assert np.array_equal(c1, c2)
+    if M * N * K <= 1024 ** 3:
+        _check_fp8(c2, *(x.cpu().numpy() for x in ops), K)
 
 
 def test_fp8_scale_sub_views(rg, ctx):

@@ -183,7 +183,8 @@ def test_alignment_and_argument_errors(rg, ctx):
 
 
 @pytest.mark.parametrize("tile", range(6))
-@pytest.mark.parametrize("shape", [(1664, 1664, 2048), (2176, 1920, 1152), (128, 128, 4096), (256, 512, 640)])
+@pytest.mark.parametrize("shape", [(1664, 1664, 2048), (2176, 1920, 1152), (2560, 2048, 1024), (128, 128, 4096),
+                                   (256, 512, 640)])
 def test_stream_k_uneven_waves(rg, ctx, tile, shape):
     """Stream-K on shapes whose tile count is just above a wave, or far below the SM count: every tile
     spans one or several CTAs' iteration ranges; the result is within the bound and deterministic."""
