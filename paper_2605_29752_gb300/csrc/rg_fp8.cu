@@ -75,6 +75,13 @@ struct Cfg {
   static_assert(!PAIR || BN == 256, "pair tile");
 };
 
+// Arrive on an mbarrier given by its shared::cluster address with relaxed semantics: the pair's
+// "accumulator buffer read" signal publishes no memory (the TMEM reads it covers have completed,
+// tcgen05.wait::ld), so it needs none of the membar a release at cluster scope costs on every K block.
+__device__ __forceinline__ void mbar_arrive_cluster_relaxed(uint32_t cluster_addr) {
+  asm volatile("mbarrier.arrive.relaxed.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr) : "memory");
+}
+
 // D (+)= A * B across a CTA pair (cta_group::2, M = 256 per instruction), e4m3 inputs, F32 accumulator.
 __device__ __forceinline__ void mma_f8_pair(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
                                             uint32_t accumulate) {
@@ -365,7 +372,7 @@ __device__ __forceinline__ void fp8_body(const CUtensorMap& tmA, const CUtensorM
         __syncwarp();
         if (lane == 0) {
           if constexpr (PAIR)
-            mbar_arrive_cluster(mapa_shared(tempty_bar(acc), 0));  // the even CTA's MMA reuses it
+            mbar_arrive_cluster_relaxed(mapa_shared(tempty_bar(acc), 0));  // the even CTA's MMA reuses it
           else
             mbar_arrive(tempty_bar(acc));
         }

@@ -34,6 +34,7 @@
 #include <mutex>
 #include <string>
 #include <type_traits>
+#include <type_traits>
 #include <vector>
 
 #include "ptx.cuh"
@@ -114,6 +115,7 @@ struct KCfg {
   static constexpr int STAGING_OFF = STAGES * STAGE_BYTES;
   static constexpr int BAR_OFF = STAGING_OFF + 4 * kStagingPerWarp;
   static constexpr int SMEM_BYTES = 1024 + BAR_OFF + 256;
+  static_assert((2 * STAGES + 9) * 8 <= 256, "barrier block");
   static constexpr uint32_t IDESC = instr_desc(1, 1, 0, 1, 128 * CTAS, BN);
   static_assert(A_BYTES % 1024 == 0 && B_BYTES % 1024 == 0, "stages must keep 1024-byte alignment");
   static_assert(SMEM_BYTES <= 232448, "shared memory budget");
@@ -124,6 +126,36 @@ struct KCfg {
 __device__ __forceinline__ void st_shared_v4(uint32_t addr, float a, float b, float c, float d) {
   asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "f"(a), "f"(b), "f"(c), "f"(d)
                : "memory");
+}
+
+// Distributed shared memory (split-K clusters): a 16-byte store into another CTA's
+// shared memory (shared::cluster address), a fence ordering this thread's earlier
+// accesses at cluster scope, and a bounded wait that acquires at cluster scope what
+// other CTAs released by arriving on a barrier of this CTA.
+__device__ __forceinline__ void st_cluster_v4(uint32_t addr, float a, float b, float c, float d) {
+  asm volatile("st.shared::cluster.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "f"(a), "f"(b), "f"(c), "f"(d)
+               : "memory");
+}
+__device__ __forceinline__ void fence_acq_rel_cluster() { asm volatile("fence.acq_rel.cluster;" ::: "memory"); }
+__device__ __forceinline__ bool mbar_try_wait_cluster(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.b32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ bool mbar_wait_cluster(uint32_t bar, uint32_t parity, long long budget,
+                                                  volatile int* abort) {
+  const long long t0 = clock64();
+  while (!mbar_try_wait_cluster(bar, parity)) {
+    if (*abort) return false;
+    if (clock64() - t0 > budget) return false;
+  }
+  return true;
 }
 
 __device__ __forceinline__ void load_acc(uint32_t taddr, bool have, float (&v)[32]) {
@@ -259,6 +291,25 @@ struct SingleSched {
 struct MemTwinSched : SingleSched<false> {
   static constexpr bool kMemOnly = true;
 };
+
+// Split-K inside a cluster: a cluster of S CTAs (S = splits, consecutive blockIdx.x)
+// computes one output tile, CTA rank s the K blocks [s kblocks / S, (s+1) kblocks / S),
+// one unit per CTA (no persistence).  The S partials never leave the chip: the
+// epilogue's cluster branch sums them through distributed shared memory in the
+// fixed order 0..S-1, the same sums as the workspace path's last arriver.
+struct ClusterSplitSched : SingleSched<false> {
+  static constexpr bool kClusterSplit = true;
+  __device__ __forceinline__ int count() const {
+    return static_cast<int>(blockIdx.x) < tiles_m * tiles_n * splits ? 1 : 0;
+  }
+  __device__ __forceinline__ Unit unit(int) const {
+    return split_unit(a, b, c, w, static_cast<int>(blockIdx.x), tiles_m, tiles_n, splits, kblocks, M, N, beta, panel);
+  }
+};
+template <class S, class = void>
+struct IsClusterSplit : std::false_type {};
+template <class S>
+struct IsClusterSplit<S, std::void_t<decltype(S::kClusterSplit)>> : std::bool_constant<S::kClusterSplit> {};
 
 // Stream-K (hybrid): whole waves of tiles run data-parallel, one tile per CTA
 // per wave (tile g + i * G on CTA g, for tiles below dp_tiles: all whole waves,
@@ -531,6 +582,7 @@ __device__ __forceinline__ void gemm_body(Sched& sched, float* ws, int32_t* tick
   (void)trace;
 #endif
   constexpr bool P2 = Sched::k2Sm;  // one CTA of a cta_group::2 pair
+  constexpr bool CS = IsClusterSplit<Sched>::value;  // one K slice of a cluster split-K tile
   using C = KCfg<BM, BN, STAGES, P2 ? 2 : 1>;
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw_s = smem_u32(smem_raw);
@@ -545,6 +597,10 @@ __device__ __forceinline__ void gemm_body(Sched& sched, float* ws, int32_t* tick
   const uint32_t drain_bar = bar0 + 8u * (2 * STAGES + 4);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 5);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  // cluster split-K: the other CTAs' operand rings are free / their blocks for this CTA have landed
+  const uint32_t go_bar = bar0 + 8u * (2 * STAGES + 6);
+  const uint32_t recv_bar = bar0 + 8u * (2 * STAGES + 7);
+  const uint32_t ready_bar = bar0 + 8u * (2 * STAGES + 8);  // this CTA's four epilogue warps saw the sum final
   int never = 0;
   volatile int* no_abort = &never;
 
@@ -563,6 +619,11 @@ __device__ __forceinline__ void gemm_body(Sched& sched, float* ws, int32_t* tick
       mbar_init(tempty_bar(b), P2 ? 8 : 4);
     }
     mbar_init(drain_bar, 1);
+    if constexpr (CS) {
+      mbar_init(go_bar, sched.splits - 1);             // one arrival per other CTA
+      mbar_init(recv_bar, 4 * (sched.splits - 1));     // one per epilogue warp of every other CTA
+      mbar_init(ready_bar, 4);
+    }
     *abort_flag = 0;
     fence_mbar_init();
   }
@@ -577,7 +638,7 @@ __device__ __forceinline__ void gemm_body(Sched& sched, float* ws, int32_t* tick
   }
   tc_fence_before();
   __syncthreads();
-  if constexpr (P2) cluster_sync();  // the partner's barriers are initialised
+  if constexpr (P2 || CS) cluster_sync();  // the other CTAs' barriers are initialised
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
   // Everything above overlaps the previous grid in the stream; nothing below
@@ -770,7 +831,76 @@ __device__ __forceinline__ void gemm_body(Sched& sched, float* ws, int32_t* tick
       tc_fence_after();
       const bool have = kb1 > kb0;
       const uint32_t tacc = tmem_base + (static_cast<uint32_t>(q * 32) << 16) + static_cast<uint32_t>(acc * C::ACC_COLS);
-      if (!Sched::kSplit || w.splits == 1) {
+      if constexpr (CS) {
+        // Split-K inside the cluster, through distributed shared memory.  Block b = q kPerWarp + j
+        // (32 x 32, j = h kCols + c) of the tile is reduced by CTA b % S; the other CTAs write their
+        // partial of it into that CTA's operand ring, free once its MMAs have all completed.
+        const int S = w.splits, r = w.s;
+        constexpr int kCols = BN / 32, kPerWarp = C::HALVES * kCols;
+        const int nown = 4 * kPerWarp / S;  // blocks each CTA reduces (S divides 4 kPerWarp)
+        // 1. this CTA's ring is free once all four epilogue warps have seen the sum final
+        if (lane == 0) mbar_arrive(ready_bar);
+        if (warp == 2 && lane == 0 && mbar_wait(ready_bar, 0, timeout, abort_flag))
+          for (int o = 0; o < S; ++o)
+            if (o != r) mbar_arrive_cluster(mapa_shared(go_bar, static_cast<uint32_t>(o)));
+        // 2. every CTA's ring is free: send the blocks other CTAs reduce (slot = the source's rank
+        //    among that CTA's sources), then release them with one arrival per warp and CTA
+        ok = __all_sync(FULL, mbar_wait_cluster(go_bar, 0, timeout, abort_flag));
+        if (!ok) break;
+#pragma unroll 1
+        for (int j = 0; j < kPerWarp; ++j) {
+          const int b = q * kPerWarp + j, o = b % S;
+          if (o == r) continue;
+          float v[32];
+          load_acc(tacc + (j / kCols) * BN + (j % kCols) * 32, have, v);
+          const int slot = r < o ? r : r - 1;
+          const uint32_t dst =
+              mapa_shared(sbase + static_cast<uint32_t>(slot * nown + b / S) * 4096u, static_cast<uint32_t>(o));
+#pragma unroll
+          for (int jj = 0; jj < 8; ++jj)
+            st_cluster_v4(dst + lane * 128 + ((jj ^ (lane & 7)) << 4), v[4 * jj], v[4 * jj + 1], v[4 * jj + 2],
+                          v[4 * jj + 3]);
+        }
+        fence_acq_rel_cluster();
+        __syncwarp();
+        if (lane == 0)
+          for (int o = 0; o < S; ++o)
+            if (o != r) mbar_arrive_cluster(mapa_shared(recv_bar, static_cast<uint32_t>(o)));
+        // 3. every other CTA's partials of this CTA's blocks have landed: sum each in the fixed
+        //    order 0..S-1 (this CTA's own partial, from TMEM, at position r) and store it
+        ok = __all_sync(FULL, mbar_wait_cluster(recv_bar, 0, timeout, abort_flag));
+        if (!ok) break;
+#pragma unroll 1
+        for (int j = 0; j < kPerWarp; ++j) {
+          const int b = q * kPerWarp + j;
+          if (b % S != r) continue;
+          float own[32], sum[32];
+          load_acc(tacc + (j / kCols) * BN + (j % kCols) * 32, have, own);
+#pragma unroll 1
+          for (int src = 0; src < S; ++src) {
+            float p[32];
+            if (src == r) {
+#pragma unroll
+              for (int e = 0; e < 32; ++e) p[e] = own[e];
+            } else {
+              const uint32_t from =
+                  sbase + static_cast<uint32_t>((src < r ? src : src - 1) * nown + b / S) * 4096u + lane * 128;
+#pragma unroll
+              for (int jj = 0; jj < 8; ++jj) {
+                const float4 x = ld_shared_v4(from + ((jj ^ (lane & 7)) << 4));
+                p[4 * jj] = x.x;
+                p[4 * jj + 1] = x.y;
+                p[4 * jj + 2] = x.z;
+                p[4 * jj + 3] = x.w;
+              }
+            }
+#pragma unroll
+            for (int e = 0; e < 32; ++e) sum[e] = src == 0 ? p[e] : sum[e] + p[e];
+          }
+          store_block(w.c, sum, tm * BM + (j / kCols) * 128 + q * 32, tn * BN + (j % kCols) * 32, w.M, w.N, w.beta,
+                      stg0, sbuf, lane);
+        }
+      } else if (!Sched::kSplit || w.splits == 1) {
 #pragma unroll 1
         for (int h = 0; h < C::HALVES; ++h)
 #pragma unroll 1
@@ -996,8 +1126,9 @@ __device__ __forceinline__ void gemm_body(Sched& sched, float* ws, int32_t* tick
   }
 #endif
   // no CTA of a pair exits while its partner may still arrive on its barriers or
-  // run MMAs on its shared memory and TMEM
-  if constexpr (P2) cluster_sync();
+  // run MMAs on its shared memory and TMEM (nor one of a split-K cluster while the
+  // others may still write its shared memory)
+  if constexpr (P2 || CS) cluster_sync();
   if (warp == 1) {
     tc_fence_after();
     if constexpr (P2)
@@ -1015,6 +1146,19 @@ __global__ void __launch_bounds__(kThreads, 1)
                      const GemmArgs args) {
   SingleSched<SPLIT> sched{&tmA,        &tmB,          &tmC,   &tmW,  args.tiles_m, args.tiles_n,
                            args.splits, args.kblocks, args.M, args.N, args.beta};
+  sched.panel = args.panel;
+  gemm_body<BM, BN, STAGES>(sched, args.ws, args.tickets, args.err, args.timeout, args.stall, args.early, args.trace);
+}
+
+// Split-K through distributed shared memory: launched as clusters of S CTAs (a
+// launch attribute), one output tile per cluster.
+template <int BM, int BN, int STAGES>
+__global__ void __launch_bounds__(kThreads, 1)
+    gemm_bf16_csplit_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                            const __grid_constant__ CUtensorMap tmC, const __grid_constant__ CUtensorMap tmW,
+                            const GemmArgs args) {
+  ClusterSplitSched sched{{&tmA,        &tmB,          &tmC,   &tmW,  args.tiles_m, args.tiles_n,
+                           args.splits, args.kblocks, args.M, args.N, args.beta}};
   sched.panel = args.panel;
   gemm_body<BM, BN, STAGES>(sched, args.ws, args.tickets, args.err, args.timeout, args.stall, args.early, args.trace);
 }
@@ -1111,6 +1255,8 @@ struct TileKernel {
   KernFn two_sm_split;  // cta_group::2 split-K instance, else null
   int smem2;
   KernFn two_sm_sk;     // cta_group::2 stream-K instance, else null
+  KernFn csplit;        // split-K through distributed shared memory (clusters of S CTAs)
+  int ring;             // bytes of the operand ring (the cluster split-K receive space)
 };
 
 // Stages of the cta_group::2 instances: 16 KB of A + BN/2 x 64 of B per stage and CTA.
@@ -1121,7 +1267,8 @@ template <int BM, int BN, int ST>
 TileKernel make_tile_kernel() {
   TileKernel t{gemm_bf16_kernel<BM, BN, ST, false>, gemm_bf16_kernel<BM, BN, ST, true>,
                gemm_bf16_streamk_kernel<BM, BN, ST>, BM, BN, KCfg<BM, BN, ST>::SMEM_BYTES,
-               gemm_bf16_memtwin_kernel<BM, BN, ST>, nullptr, nullptr, 0, nullptr};
+               gemm_bf16_memtwin_kernel<BM, BN, ST>, nullptr, nullptr, 0, nullptr,
+               gemm_bf16_csplit_kernel<BM, BN, ST>, KCfg<BM, BN, ST>::STAGING_OFF};
   if constexpr (BM == 256 && BN >= 128) {
     t.two_sm = gemm_bf16_2sm_kernel<BN, kStages2Sm<BN>, false>;
     t.two_sm_split = gemm_bf16_2sm_kernel<BN, kStages2Sm<BN>, true>;
@@ -1289,8 +1436,18 @@ static int prepare(rg_ctx* ctx, int64_t M, int64_t N, int64_t K, const void* A, 
   const int64_t tiles_m = (pm + tk.bm - 1) / tk.bm;
   const int64_t tiles_n = (pn + tk.bn - 1) / tk.bn;
   const int64_t kblocks = (pk + kBK - 1) / kBK;
+  // Split-K of a 1-CTA tile of at least 128 x 256 outputs runs as clusters of S CTAs reducing
+  // through distributed shared memory, when the other S - 1 partials of a CTA's 1/S of the tile
+  // fit its operand ring (not 256 x 256 with S = 8); otherwise through the workspace.  Measured
+  // under the sweep protocol, the cluster form is 2-9 % faster than the workspace for these
+  // tiles (768^2 x 2048 on 128 x 256, S = 2: 15.6 against 15.9 us; 256 x 512 x 4096 on 256 x 128,
+  // S = 4: 19.6 against 21.4 us) but 3-21 % slower for the smaller ones (128^2 x 4096 on 128 x 64,
+  // S = 8: 13.4 against 10.6 us), where its cluster launch and handshakes cost more than the
+  // workspace round trip of their small partials.
+  const bool csplit = splits > 1 && !two && !sk && tk.bm * tk.bn >= 128 * 256 &&
+                      static_cast<int64_t>(splits - 1) * tk.bm * tk.bn * 4 / splits <= tk.ring;
   // workspace slots per tile: the split count, or stream-K's most segments on one tile
-  int64_t slots = splits;
+  int64_t slots = csplit ? 1 : splits;
   SkGeometry skg{};
   if (sk) {  // cta_group::2: the schedule runs over pair tiles and clusters
     skg = two ? sk_geometry(tiles_m * tiles_n, kblocks, ctx->sm_count / 2)
@@ -1317,9 +1474,10 @@ static int prepare(rg_ctx* ctx, int64_t M, int64_t N, int64_t K, const void* A, 
   if (rc != RG_OK) return rc;
   L->fn = (sk && two) ? tk.two_sm_sk
           : sk        ? tk.sk
+          : csplit    ? tk.csplit
           : two       ? (splits > 1 ? tk.two_sm_split : tk.two_sm)
                       : (splits > 1 ? tk.fn_split : tk.fn);
-  L->cluster = two ? 2 : 1;
+  L->cluster = two ? 2 : csplit ? splits : 1;
   L->smem = two ? tk.smem2 : tk.smem;
   L->ws_slots = slots;
   GemmArgs& g = L->args;
@@ -1348,6 +1506,8 @@ static int prepare(rg_ctx* ctx, int64_t M, int64_t N, int64_t K, const void* A, 
     L->grid = dim3(static_cast<unsigned>(2 * skg.grid));
   } else if (two) {  // one 2-CTA cluster per (256-row tile, split), at most one CTA per SM
     L->grid = dim3(static_cast<unsigned>(2 * std::min<int64_t>(tiles_m * tiles_n * splits, ctx->sm_count / 2)));
+  } else if (csplit) {  // one cluster of S CTAs per tile, not persistent
+    L->grid = dim3(static_cast<unsigned>(units));
   } else {
     L->grid = dim3(static_cast<unsigned>(sk ? skg.grid : std::min<int64_t>(units, ctx->sm_count)));
   }
@@ -1555,6 +1715,8 @@ extern "C" int rg_init(int device, int64_t workspace_bytes, rg_ctx** out) {
                                 cudaSuccess) ||
         (e = cudaFuncSetAttribute(reinterpret_cast<const void*>(tk.sk), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   tk.smem)) != cudaSuccess ||
+        (e = cudaFuncSetAttribute(reinterpret_cast<const void*>(tk.csplit),
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, tk.smem)) != cudaSuccess ||
         (e = cudaFuncSetAttribute(reinterpret_cast<const void*>(tk.mem), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   tk.smem)) != cudaSuccess ||
         (tk.two_sm && (e = cudaFuncSetAttribute(reinterpret_cast<const void*>(tk.two_sm),
@@ -2248,7 +2410,7 @@ static int noalloc_setup(int dev, NoallocDevice** out) {
     if (rc != RG_OK) return rc;
     for (int t = 0; t < RG_NUM_TILES; ++t) {
       const TileKernel& tk = tile_kernel(t);
-      for (KernFn fn : {tk.fn, tk.fn_split, tk.sk}) {
+      for (KernFn fn : {tk.fn, tk.fn_split, tk.sk, tk.csplit}) {
         e = cudaFuncSetAttribute(reinterpret_cast<const void*>(fn), cudaFuncAttributeMaxDynamicSharedMemorySize, tk.smem);
         if (e != cudaSuccess) return cuda_fail(e, "rg_gemm_noalloc: shared-memory attribute");
       }

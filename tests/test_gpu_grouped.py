@@ -210,3 +210,34 @@ def test_grouped_split_k_and_two_sm_items(rg, ctx, case):
             assert np.array_equal(got, Cr.cpu().numpy()), rg.variant_name(v)
     finally:
         rg.rg_group_destroy(g)
+
+
+@pytest.mark.parametrize("tile", range(6))
+def test_cluster_split_equals_workspace_split(rg, ctx, tile):
+    """rg_gemm runs split-K of the 128x256, 256x128 and 256x256 tiles as a cluster of S CTAs that
+    reduce through distributed shared memory (the workspace kernel for the smaller tiles and where the
+    partials do not fit: 256x256 with S = 8); a grouped launch runs the same split through the
+    workspace and its last arriver.  Both sum the S partials in the order 0..S-1, so they agree bit
+    for bit; both lie within the oracle's bound."""
+    M, N, K = 520, 264, 1000
+    g = rg.rg_group_create(ctx, tile, 8, 64 << 20)
+    try:
+        a, b, A, B = _problem(M, N, K, seed=60 + tile)
+        a64, b64 = og.bf16_bits_to_f64(a), og.bf16_bits_to_f64(b)
+        for s in (2, 4, 8):
+            v = rg.variant(tile, s)
+            for beta in (0, 1):
+                c0 = synthetic.normal_stream_f32(61 + tile, s, M * N).reshape(M, N)
+                Cc = torch.from_numpy(c0).cuda() if beta else torch.full((M, N), float("nan"), device="cuda")
+                Cw = torch.from_numpy(c0).cuda() if beta else torch.full((M, N), float("nan"), device="cuda")
+                rg.rg_gemm(ctx, M, N, K, A, K, B, N, Cc, N, v, beta)
+                rg.rg_gemm_grouped(g, [(M, N, K, A, K, B, N, Cw, N, beta, 0, 0, 0, v)])
+                rg.rg_check(ctx)
+                got = Cc.cpu().numpy()
+                c64 = a64 @ b64 + (c0.astype(np.float64) if beta else 0.0)
+                s64 = np.abs(a64) @ np.abs(b64) + (np.abs(c0.astype(np.float64)) if beta else 0.0)
+                ratio, ez = og.error_ratio(got, c64, s64)
+                assert ez and ratio <= og.bound(K + beta), (rg.variant_name(v), beta, ratio)
+                assert np.array_equal(got, Cw.cpu().numpy()), (rg.variant_name(v), beta)
+    finally:
+        rg.rg_group_destroy(g)
