@@ -350,11 +350,20 @@ __device__ __forceinline__ void fp8_body(const CUtensorMap& tmA, const CUtensorM
       float r[C::HALF];
 #pragma unroll
       for (int i = 0; i < C::HALF; ++i) r[i] = 0.f;
+      // The K blocks' scale products, 32 at a time, one per lane: lane l holds that of K block
+      // kb0 + 32 j + l.  A load per K block would put its global-memory latency on the promotion's
+      // critical path whenever the block's product is already waiting in TMEM.
+      float sc_lane = 0.f;
       for (int kb = kb_lo(s); kb < kb1; ++kb) {
-        // (scale pointers are recomputed from the kernel parameters: registers are scarce here)
-        const float sc = kb < kbv ? args.sA[static_cast<size_t>(tm) * args.sa_ld + kb] *
-                                        args.sB[static_cast<size_t>(kb) * args.sb_ld + nb]
-                                  : 0.f;
+        const int rel = kb - kb_lo(s);
+        if ((rel & 31) == 0) {
+          // (scale pointers are recomputed from the kernel parameters: registers are scarce here)
+          const int k = kb + lane;
+          sc_lane = (k < kb1 && k < kbv) ? args.sA[static_cast<size_t>(tm) * args.sa_ld + k] *
+                                               args.sB[static_cast<size_t>(k) * args.sb_ld + nb]
+                                         : 0.f;
+        }
+        const float sc = __shfl_sync(FULL, sc_lane, rel & 31);
         ok = __all_sync(FULL, mbar_wait(tfull_bar(acc), aph, args.timeout, abort_flag));
         if (!ok) break;
         tc_fence_after();
