@@ -606,7 +606,7 @@ def main():
         T0v = merge_t0_shards(local_t, hdr, dist, dev, rg.RG_T_UNMEASURED, rg.RG_T_OTHER_SHARD)
     else:
         T0v = rg.rg_sweep(ctx, grid, all_v, A, B, C)
-    s1_rows = [rg.variant(t, 1) for t in range(rg.RG_NUM_TILES)]
+    s1_rows = [rg.variant(t, 1) for t in range(rg.RG_NUM_PAPER_TILES)]   # the paper's best-of-6
     plan_smooth = rg.rg_plan_build(grid, T0v, all_v)
     setup_s = time.perf_counter() - t_setup
     fixed_v = rg.variant(FIXED_TILE, 1)
@@ -690,8 +690,9 @@ def main():
         "data": "synthetic",
         "config": {"workload": f"BF16 NN GEMM landscape, (M,N,K) in {{128..{Mx} step 128}}^3 = {ncell} cells, "
                                f"U[-1,1) BF16 operands (seed 0), FP32 accumulate/output",
-                   "smoothed": f"best-of-{rg.RG_NUM_VARIANTS} autotune (6 tiles x {{split-K 1/2/4/8, stream-K}} + "
-                               "2 cta_group::2 tiles x split-K 1/2/4/8) + DP pad/split plan, O(1) lookup",
+                   "smoothed": f"best-of-{rg.RG_NUM_VARIANTS} autotune (the paper's 6 tiles and 128x192, each x "
+                               "{split-K 1/2/4/8, stream-K}; 2 cta_group::2 tiles x {split-K 1/2/4/8, stream-K}) + "
+                               "DP pad/split plan, O(1) lookup",
                    "plain": "fixed 128x128 tile, split 1",
                    "timing": "per cell: 1 warm-up launch, device spin, mean of 5 back-to-back launches between "
                              "CUDA events (paper protocol, warm per cell: operands of small cells stay L2-resident "
@@ -714,8 +715,8 @@ def main():
                              f"{int(dsel.sum())} single-launch cells): useful 2MNK flops / CUDA-event time of "
                              f"those cells' timed launches; peak = {peak_src} bf16 burst; the cells differ in "
                              f"size, so traffic is per launch of one captured mid-size cell (traffic_cell, "
-                             f"profiles/{TRAFFIC_PROFILE}.md), and mean_frac is the mean over all cells of "
-                             f"t_roof / t_measured for the smoothed pass"},
+                             f"traffic_profile), and mean_frac is the mean over all cells of t_roof / t_measured "
+                             f"for the smoothed pass"},
         "roofline_all_gemms": {"achieved": agg_smooth, "frac": agg_smooth / p_burst, "unit": "TFLOP/s"},
         "roofline_mean_frac": {"plain": float(np.mean([p["roofline_mean_frac"] for p in plain])),
                                "smoothed": float(np.mean([q["roofline_mean_frac"] for q in smooth])),
@@ -761,21 +762,24 @@ def kernel_source_hash():
 
 CAPTURE_PROFILE = "gemm_bf16_256x256_2sm_8192x8192x4096"   # profiles/<name>.md and .json
 CAPTURE_VARIANT = "256x256/2SM"
-TRAFFIC_PROFILE = "gemm_bf16_256x256_2sm_2048x2048x4096"   # a mid-size landscape cell of the dominant kernel
+# ncu captures of kernels that can dominate the smoothed pass, each on a mid-size landscape cell it wins
+TRAFFIC_PROFILES = {"256x256/2SM": "gemm_bf16_256x256_2sm_2048x2048x4096",
+                    "128x192/S1": "gemm_bf16_128x192_2048x1536x4096"}
 
 
 def dominant_traffic(variant_name):
     """DRAM traffic per launch of the dominant kernel on one captured mid-size landscape cell, from the ncu
     capture in profiles/ (null when the kernel differs from the captured one or the source changed since)."""
-    path = os.path.join(ROOT, "profiles", TRAFFIC_PROFILE + ".json")
-    if variant_name != CAPTURE_VARIANT or not os.path.exists(path):
+    name = TRAFFIC_PROFILES.get(variant_name)
+    path = os.path.join(ROOT, "profiles", f"{name}.json")
+    if name is None or not os.path.exists(path):
         return {"traffic": None, "traffic_note": "no capture of this kernel on a landscape cell"}
     prof = json.load(open(path))
     if prof["kernel_source_sha256"] != kernel_source_hash():
         return {"traffic": None, "traffic_note": "the kernel source changed since the capture"}
     t = prof["dram_bytes_read"] + prof["dram_bytes_write"]
     return {"traffic": t, "traffic_cell": prof["shape"], "traffic_over_algorithmic": t / prof["algorithmic_bytes"],
-            "traffic_note": prof["l2_resident"]}
+            "traffic_profile": f"profiles/{name}.md", "traffic_note": prof["l2_resident"]}
 
 
 def roofline_capture(rg, ctx, p_burst, dev, reps=10):
@@ -851,7 +855,7 @@ def extras(args, rg, ctx, grid, T0v, plan_smooth, A, B, C, flops, Mv, Nv, Kv, de
     ia = ik = 2048 // STEP - 1
     if ia < count:
         ct = {}
-        for tile in range(rg.RG_NUM_TILES):
+        for tile in range(rg.RG_NUM_PAPER_TILES):
             v = rg.variant(tile, 1)
             t_line = T0v[v].reshape(count, count, count)[ia, :, ik]
             tfl = 2.0 * 2048 * 2048 * (np.arange(1, count + 1) * STEP) / (t_line * 1e3)
@@ -864,7 +868,7 @@ def extras(args, rg, ctx, grid, T0v, plan_smooth, A, B, C, flops, Mv, Nv, Kv, de
     bw = (json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("hbm_gbs", 6800.0)
           if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 6800.0)
     ideal = rg.rg_landscape(grid, rg.RG_LANDSCAPE_IDEAL, p_burst, sms, 0.0, [(128, 128)])
-    opt = rg.rg_landscape(grid, rg.RG_LANDSCAPE_OPTIMAL, p_burst, sms, bw, rg.TILES)
+    opt = rg.rg_landscape(grid, rg.RG_LANDSCAPE_OPTIMAL, p_burst, sms, bw, rg.TILES[:rg.RG_NUM_PAPER_TILES])
     fp = {}
     for name, surf in (("ideal_128x128", ideal), ("optimal_six_tiles", opt)):
         t_eq = np.maximum(1, np.round(flops / (surf * 1e3))).astype(np.int64)   # as integer ns, for the stats call
@@ -945,7 +949,7 @@ def decomposition(rg, ctx, grid, T0v, s1_rows, fixed_v, A, B, C, p_burst, count)
     out["fixed_128x128_full_grid"], _ = summary(grid, T0v[fixed_v], tm_fixed)
     kmax = STEP * count
     gk = rg.make_grid((STEP, STEP, count), (STEP, STEP, count), (kmax, STEP, 1))
-    tm6 = rg.rg_sweep_memtwin(ctx, gk, list(range(rg.RG_NUM_TILES)), A, B, C)
+    tm6 = rg.rg_sweep_memtwin(ctx, gk, list(range(rg.RG_NUM_PAPER_TILES)), A, B, C)
     tg6 = np.stack([T0v[v].reshape(count, count, count)[:, :, -1].ravel() for v in s1_rows])
     win = tg6.argmin(axis=0)
     cols = np.arange(tg6.shape[1])
@@ -972,7 +976,7 @@ def fine_n_sweep(rg, ctx, A, B, C, n0=3000, step=32, count=35, mk=4096):
     """N = 3000..4088 step 32 at M = K = 4096 for every tile (split 1), then DP padding (T0 -> T1) on
     that fine grid per tile and on the best-of-6 envelope (Sec. 8.3-8.4, Tables 13-14)."""
     g = rg.make_grid((mk, STEP, 1), (n0, step, count), (mk, STEP, 1))
-    rows = [rg.variant(t, 1) for t in range(rg.RG_NUM_TILES)]
+    rows = [rg.variant(t, 1) for t in range(rg.RG_NUM_PAPER_TILES)]
     T0 = rg.rg_sweep(ctx, g, rows, A, B, C)
     Ns = n0 + step * np.arange(count)
     out = {"grid": f"M = K = {mk}, N = {n0}..{Ns[-1]} step {step}"}

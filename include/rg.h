@@ -54,19 +54,24 @@ enum {
 };
 
 /* ---- kernel variants ----
- * Six output tiles (BM x BN), each with an in-kernel split-K factor S in
- * {1, 2, 4, 8} (id = tile * RG_NUM_SPLITS + log2(S)) and a stream-K schedule
- * (id = RG_VARIANT_SK(tile)); the two 256-row tiles with BN >= 128 also run as
- * tcgen05 cta_group::2 pairs (RG_VARIANT_2SM).  Ties in best-of selection go
- * to the lowest id.                                           (Sec. 6.1, 6.4) */
+ * Seven output tiles (BM x BN): the paper's six (tiles 0..5, RG_NUM_PAPER_TILES,
+ * the best-of-6 of Sec. 6.4) and a 128 x 192 tile, whose 1.5x-wider column
+ * tiles fill the 152 SMs where 128 x 128 and 128 x 256 leave a partial wave.
+ * Each tile has an in-kernel split-K factor S in {1, 2, 4, 8} (id = tile *
+ * RG_NUM_SPLITS + log2(S)) and a stream-K schedule (id = RG_VARIANT_SK(tile));
+ * the two 256-row tiles with BN >= 128 also run as tcgen05 cta_group::2 pairs
+ * (RG_VARIANT_2SM).  Ties in best-of selection go to the lowest id.
+ *                                                             (Sec. 6.1, 6.4) */
 enum {
   RG_TILE_128x64 = 0, RG_TILE_128x128 = 1, RG_TILE_128x256 = 2,
   RG_TILE_256x64 = 3, RG_TILE_256x128 = 4, RG_TILE_256x256 = 5,
-  RG_NUM_TILES = 6
+  RG_TILE_128x192 = 6,
+  RG_NUM_TILES = 7,
+  RG_NUM_PAPER_TILES = 6
 };
 #define RG_NUM_SPLITS 4
 #define RG_VARIANT(tile, log2_split) ((tile) * RG_NUM_SPLITS + (log2_split))
-/* Stream-K variant of a tile (ids 24..29, after the split-K ids): with T = wP + r
+/* Stream-K variant of a tile (ids 28..34, after the split-K ids): with T = wP + r
  * tiles on P SMs (0 < r < P), either all whole waves but the last run
  * data-parallel and the K iterations of the last whole wave and the remainder
  * are divided evenly among the P CTAs (w >= 1 and r <= P/4 or r >= P/2; each CTA
@@ -76,7 +81,7 @@ enum {
  * iterations span several CTAs is summed by its last arriving piece in the
  * fixed order of their K ranges. */
 #define RG_VARIANT_SK(tile) (RG_NUM_TILES * RG_NUM_SPLITS + (tile))
-/* 2-SM variant of a 256-row tile (ids 30..33 for 256x128, 34..37 for 256x256,
+/* 2-SM variant of a 256-row tile (ids 35..38 for 256x128, 39..42 for 256x256,
  * split-K 1/2/4/8): a 2-CTA cluster computes one 256 x BN tile as a single
  * tcgen05 cta_group::2 MMA unit; each CTA loads 128 rows of A and BN/2 columns
  * of B and holds its 128 output rows in its own TMEM, so each SM moves
@@ -86,7 +91,7 @@ enum {
  * this library uses TMA multicast. */
 #define RG_VARIANT_2SM(tile, log2_split) \
   (RG_NUM_TILES * RG_NUM_SPLITS + RG_NUM_TILES + ((tile) - RG_TILE_256x128) * RG_NUM_SPLITS + (log2_split))
-/* cta_group::2 stream-K variant of a 256-row tile (id 38 for 256x128, 39 for
+/* cta_group::2 stream-K variant of a 256-row tile (id 43 for 256x128, 44 for
  * 256x256): the stream-K schedule above over 256 x BN pair tiles and the 2-CTA
  * clusters (one per SM pair); each CTA of a cluster sums its own 128 rows of a
  * shared tile in the fixed order of the pieces' K ranges.  It removes the
@@ -287,7 +292,7 @@ int rg_surface_stats(const rg_grid* grid, const int64_t* t_ns, double* tflops_ou
  * variant the autotuner chose for it: a 1-CTA tile with in-kernel split-K
  * (S = 1/2/4/8) or a cta_group::2 pair tile with split-K; a stream-K variant
  * runs as its tile with split 1; variant = -1 means the group's tile, split 1.
- * The problems are sorted into eight kernel families (the six 1-CTA tiles, the
+ * The problems are sorted into nine kernel families (the seven 1-CTA tiles, the
  * two cta_group::2 tiles); each family present becomes one persistent launch
  * over all SMs whose work units are the concatenation of its problems'
  * (tile, K split) units.  Each problem has its own sizes, operands, leading

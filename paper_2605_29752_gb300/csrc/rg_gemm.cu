@@ -1,6 +1,6 @@
 // BF16 NN GEMM for sm_103a (C = A * B, A M x K row-major, B K x N row-major,
-// C M x N FP32; Sec. 2.2 of "From Roofline to Ruggedness") in six tile
-// variants (Sec. 6.1) with the padding and split-K of Sec. 7.1 fused in, plus
+// C M x N FP32; Sec. 2.2 of "From Roofline to Ruggedness") in the paper's six
+// tiles (Sec. 6.1) and a 128 x 192 one, with the padding and split-K of Sec. 7.1 fused in, plus
 // the sweep (Sec. 3, Sec. 5.4) and plan execution (Sec. 7.1) that drive it.
 //
 // Kernel structure (one CTA per SM, persistent over output tiles x K splits):
@@ -19,7 +19,9 @@
 // warp writes its FP32 partial rows to the workspace, fences and takes a
 // ticket; the last arriver of a (tile, warp) row block sums the S partials in
 // the fixed order 0..S-1 (so results are deterministic), stores C and resets
-// the ticket.  No CTA ever waits for another CTA.
+// the ticket.  No CTA waits for another CTA outside its own cluster (a
+// cta_group::2 pair, or the S CTAs of a cluster split-K tile, which the
+// hardware schedules together).
 // Every mbarrier wait is bounded; on expiry the kernel records an error code
 // in a device word, releases its TMEM and returns.
 #include <cuda.h>
@@ -1282,11 +1284,12 @@ static const TileKernel& tile_kernel(int tile) {
   static const TileKernel table[RG_NUM_TILES] = {
       make_tile_kernel<128, 64, 8>(),  make_tile_kernel<128, 128, 6>(), make_tile_kernel<128, 256, 4>(),
       make_tile_kernel<256, 64, 4>(),  make_tile_kernel<256, 128, 4>(), make_tile_kernel<256, 256, 3>(),
+      make_tile_kernel<128, 192, 4>(),
   };
   return table[tile];
 }
 
-// Grouped launches come in eight kernel families: the six 1-CTA tiles, then the
+// Grouped launches come in nine kernel families: the seven 1-CTA tiles, then the
 // cta_group::2 forms of the 256x128 and 256x256 tiles.
 constexpr int kGroupFamilies = RG_NUM_TILES + 2;
 using GroupedFn = void (*)(const GroupHeader*, const GroupItem*, const CUtensorMap, float*, int32_t*, int32_t*,
@@ -1296,6 +1299,7 @@ static const void* grouped_kernel(int family) {
       gemm_bf16_grouped_kernel<128, 64, 8>,  gemm_bf16_grouped_kernel<128, 128, 6>,
       gemm_bf16_grouped_kernel<128, 256, 4>, gemm_bf16_grouped_kernel<256, 64, 4>,
       gemm_bf16_grouped_kernel<256, 128, 4>, gemm_bf16_grouped_kernel<256, 256, 3>,
+      gemm_bf16_grouped_kernel<128, 192, 4>,
       gemm_bf16_grouped_2sm_kernel<128, kStages2Sm<128>>, gemm_bf16_grouped_2sm_kernel<256, kStages2Sm<256>>,
   };
   return reinterpret_cast<const void*>(table[family]);

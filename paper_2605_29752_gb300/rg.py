@@ -32,10 +32,11 @@ RG_ERR_NO_DEVICE = -9
 
 RG_T_UNMEASURED = 1 << 60
 RG_T_OTHER_SHARD = 0
-RG_NUM_TILES = 6
+RG_NUM_TILES = 7
+RG_NUM_PAPER_TILES = 6                # tiles 0..5: the paper's six (best-of-6)
 RG_NUM_SPLITS = 4
 RG_NUM_VARIANTS = RG_NUM_TILES * RG_NUM_SPLITS + RG_NUM_TILES + 2 * RG_NUM_SPLITS + 2
-TILES = [(128, 64), (128, 128), (128, 256), (256, 64), (256, 128), (256, 256)]
+TILES = [(128, 64), (128, 128), (128, 256), (256, 64), (256, 128), (256, 256), (128, 192)]
 SPLITS = [1, 2, 4, 8]
 SK = "SK"
 TWO_SM = "2SM"
@@ -63,7 +64,7 @@ def variant(tile: int, split=1) -> int:
 
 
 def variant_tile(v: int) -> int:
-    """Tile index (0..5) of a variant id."""
+    """Tile index (0..6) of a variant id."""
     n = RG_NUM_TILES * RG_NUM_SPLITS
     if v >= _BASE_2SM_SK:
         return 4 + v - _BASE_2SM_SK

@@ -336,6 +336,6 @@ def test_plan_file_of_another_version_is_refused(rg, tmp_path):
         rg.rg_plan_free(h)
     data = bytearray(open(p, "rb").read())
     assert data[:8] == b"RGPLAN01"
-    data[8:12] = (1).to_bytes(4, "little")                  # the version field
+    data[8:12] = (2).to_bytes(4, "little")                  # the version field: the six-tile numbering
     open(p, "wb").write(bytes(data))
     assert rg.rg_plan_load_status(p) == rg.RG_ERR_PLAN_MISMATCH

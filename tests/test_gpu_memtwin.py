@@ -32,7 +32,7 @@ def dev_bf16(bits):
     return torch.from_numpy(np.ascontiguousarray(bits).view(np.int16)).cuda().view(torch.bfloat16)
 
 
-@pytest.mark.parametrize("tile", range(6))
+@pytest.mark.parametrize("tile", range(7))
 @pytest.mark.parametrize("shape", [(300, 264, 200), (128, 64, 64), (520, 776, 1000)])
 def test_memtwin_stays_inside_c(rg, ctx, tile, shape):
     M, N, K = shape
@@ -56,7 +56,7 @@ def test_memtwin_stays_inside_c(rg, ctx, tile, shape):
 def test_memtwin_rejects_bad_tile(rg, ctx):
     t = torch.zeros(64 * 64, device="cuda")
     with pytest.raises(rg.RGError) as e:
-        rg.rg_gemm_memtwin(ctx, 64, 64, 64, t, 64, t, 64, t, 64, 6)
+        rg.rg_gemm_memtwin(ctx, 64, 64, 64, t, 64, t, 64, t, 64, rg.RG_NUM_TILES)
     assert e.value.code == rg.RG_ERR_INVALID
 
 
