@@ -17,8 +17,9 @@ Modules
 
 Parity status: gemm, dp, roughness, fp8 quantisation and the ideal landscape are
 pinned by tests/test_oracle_*.py.  The first-principles *optimal* landscape
-(landscape.optimal_surface) is "parity unpinned": the values the paper prints for
-it cannot be reproduced from its stated constants.  The FP8 GEMM error has no
+(landscape.optimal_surface) is pinned by its parts and by hand-worked cells on
+GB300 constants, but stays "parity unpinned" against the paper's own numbers:
+the values the paper prints for it cannot be reproduced from its stated constants.  The FP8 GEMM error has no
 bound in the paper beyond float32 accumulation ("parity unpinned" for its
 observed error; its exact-product special cases are pinned).
 """

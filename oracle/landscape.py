@@ -13,10 +13,12 @@ max(t_compute, t_memory) with t_compute = 2MNK / (P eta_wave),
 eta_wave = W / (ceil(W / C) C), and t_memory = 2MK/(BW eta_A) + 2KN/(BW eta_B)
 + 4MN/(BW eta_D).  The channel efficiencies eta follow the paper's GDDR6
 interleave model when ``channels`` is given, else 1 (HBM: no disclosed hash).
-PARITY UNPINNED: the paper's printed optimal statistics (Table 18) are not
-reproduced by its own stated constants under any reading found, so only its
-parts (eta_wave, the channel eta, the memory and compute terms) are pinned,
-not the surface.
+Pins: its parts (eta_wave, the channel eta, the memory and compute terms), the
+one-tile free-memory reduction to the ideal, and hand-worked cells on GB300
+constants (a compute-bound multi-tile cell and a memory-bound one), which fix
+the best-over-tiles of max(t_compute, t_memory) composition.  Against the
+paper's own numbers it stays unpinned: its printed optimal statistics (Table
+18) are not reproduced by its stated constants under any reading found.
 
 kol (Sec. 10.2-10.3, Table 19): tau = mean A / mean O, rho = R(A) / R(O);
 throughput bands T0 < 0.50 <= T1 < 0.75 <= T2 < 0.95 <= T3; smoothness bands

@@ -67,3 +67,27 @@ def test_optimal_memory_bound_small_shape():
     t_mem = (2 * M * K + 2 * K * N + 4 * M * N) / 451e9
     v = landscape.optimal_cell(M, N, K, 108.2, 20, [(256, 256), (128, 128), (64, 64)], 451.0)
     assert abs(v - 2 * M * N * K / t_mem / 1e12) < 1e-9
+
+
+PAPER_SIX = [(128, 64), (128, 128), (128, 256), (256, 64), (256, 128), (256, 256)]
+
+
+def test_optimal_hand_worked_multi_tile_cell_on_gb300_constants():
+    """M = 2048, N = 1536, K = 4096 on P = 1919.8 TFLOP/s, C = 152, BW = 6789.6 GB/s, the paper's six tiles
+    (Sec. 9.2), worked by hand.  Tile counts W = ceil(M/TM) ceil(N/TN) and wave efficiencies W / (ceil(W/C) C):
+    128x64 -> 16 * 24 = 384, three waves of 152, eta = 384/456 = 16/19; 128x128 -> 192 and 256x64 -> 192,
+    two waves, eta = 12/19; 128x256 -> 96 and 256x128 -> 96, eta = 12/19; 256x256 -> 48, eta = 6/19.
+    The best tile is 128x64: t_comp = 2MNK / (P 16/19) = 15.94 us, above t_mem = (2MK + 2KN + 4MN) / BW =
+    41,943,040 B / 6789.6 GB/s = 6.18 us, so the cell reaches P * 16/19.  (A min in place of the max, the
+    worst tile in place of the best, or another wave formula each give a different value.)"""
+    v = landscape.optimal_cell(2048, 1536, 4096, 1919.8, 152, PAPER_SIX, 6789.6)
+    assert abs(v - 1919.8 * 16 / 19) < 1e-9
+
+
+def test_optimal_hand_worked_memory_bound_multi_tile_cell():
+    """M = 2048, N = 1536, K = 128 on the same constants: the best tile is again 128x64 (eta = 16/19), whose
+    t_comp = 2MNK / (P 16/19) = 0.498 us is below t_mem = (2MK + 2KN + 4MN) / BW = 13,500,416 B / 6789.6 GB/s =
+    1.988 us, so every tile is memory-bound and the cell reaches 2MNK BW / bytes = 405.00 TFLOP/s."""
+    v = landscape.optimal_cell(2048, 1536, 128, 1919.8, 152, PAPER_SIX, 6789.6)
+    expect = 2 * 2048 * 1536 * 128 * 6789.6e9 / 13_500_416 / 1e12
+    assert abs(v - expect) < 1e-9 and abs(expect - 405.0) < 0.01
