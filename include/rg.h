@@ -221,7 +221,11 @@ int rg_launch_count(const rg_ctx* ctx, int64_t* out);
  * size (pass 0 for "same as M, N, K"); the padding is never materialised:
  * out-of-range operand reads are zero-filled and out-of-range outputs dropped.
  * M, N or K == 0: nothing to compute (C untouched if M or N is 0; C = 0 for
- * K == 0 with beta = 0). */
+ * K == 0 with beta = 0).  Split-K (S > 1) of the 128x256, 256x128 and 256x256
+ * 1-CTA tiles (not 256x256 with S = 8) runs as clusters of S CTAs that sum the
+ * S partials through distributed shared memory; the other split variants sum
+ * them through the context's workspace.  Both sum in the order 0..S-1, so the
+ * two forms give the same bits. */
 int rg_gemm(rg_ctx* ctx, int64_t M, int64_t N, int64_t K,
             const void* A, int64_t lda, const void* B, int64_t ldb,
             float* C, int64_t ldc, int32_t variant, int32_t beta,
