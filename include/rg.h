@@ -54,24 +54,26 @@ enum {
 };
 
 /* ---- kernel variants ----
- * Seven output tiles (BM x BN): the paper's six (tiles 0..5, RG_NUM_PAPER_TILES,
- * the best-of-6 of Sec. 6.4) and a 128 x 192 tile, whose 1.5x-wider column
- * tiles fill the 152 SMs where 128 x 128 and 128 x 256 leave a partial wave.
- * Each tile has an in-kernel split-K factor S in {1, 2, 4, 8} (id = tile *
- * RG_NUM_SPLITS + log2(S)) and a stream-K schedule (id = RG_VARIANT_SK(tile));
- * the two 256-row tiles with BN >= 128 also run as tcgen05 cta_group::2 pairs
- * (RG_VARIANT_2SM).  Ties in best-of selection go to the lowest id.
- *                                                             (Sec. 6.1, 6.4) */
+ * Eight output tiles (BM x BN): the paper's six (tiles 0..5, RG_NUM_PAPER_TILES,
+ * the best-of-6 of Sec. 6.4) and two 192-wide ones, 128 x 192 and 256 x 192,
+ * whose 1.5x-wider column tiles fill the 152 SMs where the 128- and 256-wide
+ * tiles leave a partial wave.  Each tile has an in-kernel split-K factor S in
+ * {1, 2, 4, 8} (id = tile * RG_NUM_SPLITS + log2(S)) and a stream-K schedule
+ * (id = RG_VARIANT_SK(tile)); the three 256-row tiles with BN >= 128 (the pair
+ * tiles 256x128, 256x256, 256x192, in that order) also run as tcgen05
+ * cta_group::2 pairs (RG_VARIANT_2SM).  Ties in best-of selection go to the
+ * lowest id.                                                  (Sec. 6.1, 6.4) */
 enum {
   RG_TILE_128x64 = 0, RG_TILE_128x128 = 1, RG_TILE_128x256 = 2,
   RG_TILE_256x64 = 3, RG_TILE_256x128 = 4, RG_TILE_256x256 = 5,
-  RG_TILE_128x192 = 6,
-  RG_NUM_TILES = 7,
-  RG_NUM_PAPER_TILES = 6
+  RG_TILE_128x192 = 6, RG_TILE_256x192 = 7,
+  RG_NUM_TILES = 8,
+  RG_NUM_PAPER_TILES = 6,
+  RG_NUM_PAIR_TILES = 3
 };
 #define RG_NUM_SPLITS 4
 #define RG_VARIANT(tile, log2_split) ((tile) * RG_NUM_SPLITS + (log2_split))
-/* Stream-K variant of a tile (ids 28..34, after the split-K ids): with T = wP + r
+/* Stream-K variant of a tile (ids 32..39, after the split-K ids): with T = wP + r
  * tiles on P SMs (0 < r < P), either all whole waves but the last run
  * data-parallel and the K iterations of the last whole wave and the remainder
  * are divided evenly among the P CTAs (w >= 1 and r <= P/4 or r >= P/2; each CTA
@@ -81,25 +83,29 @@ enum {
  * iterations span several CTAs is summed by its last arriving piece in the
  * fixed order of their K ranges. */
 #define RG_VARIANT_SK(tile) (RG_NUM_TILES * RG_NUM_SPLITS + (tile))
-/* 2-SM variant of a 256-row tile (ids 35..38 for 256x128, 39..42 for 256x256,
- * split-K 1/2/4/8): a 2-CTA cluster computes one 256 x BN tile as a single
- * tcgen05 cta_group::2 MMA unit; each CTA loads 128 rows of A and BN/2 columns
- * of B and holds its 128 output rows in its own TMEM, so each SM moves
+/* Index of a pair tile among the pair tiles (256x128 -> 0, 256x256 -> 1, 256x192 -> 2). */
+#define RG_PAIR_INDEX(tile) ((tile) == RG_TILE_256x192 ? 2 : (tile) - RG_TILE_256x128)
+/* 2-SM variant of a 256-row tile (ids 40..43 for 256x128, 44..47 for 256x256,
+ * 48..51 for 256x192, split-K 1/2/4/8): a 2-CTA cluster computes one 256 x BN
+ * tile as a single tcgen05 cta_group::2 MMA unit; each CTA loads 128 rows of A
+ * and BN/2 columns of B (256x192: two 64-column boxes, of which its MMAs read
+ * 96) and holds its 128 output rows in its own TMEM, so each SM moves about
  * 128 x BK + BN/2 x BK operand elements per K block instead of 256 x BK + BN x BK.
  * With split-K each CTA publishes and reduces its own 128 rows as in the 1-CTA
  * kernels (same workspace, tickets and fixed summation order).  No kernel of
  * this library uses TMA multicast. */
 #define RG_VARIANT_2SM(tile, log2_split) \
-  (RG_NUM_TILES * RG_NUM_SPLITS + RG_NUM_TILES + ((tile) - RG_TILE_256x128) * RG_NUM_SPLITS + (log2_split))
-/* cta_group::2 stream-K variant of a 256-row tile (id 43 for 256x128, 44 for
- * 256x256): the stream-K schedule above over 256 x BN pair tiles and the 2-CTA
- * clusters (one per SM pair); each CTA of a cluster sums its own 128 rows of a
- * shared tile in the fixed order of the pieces' K ranges.  It removes the
- * partial last wave that quantises the large cells (Sec. 9.4 names split-K as
- * the remedy). */
-#define RG_VARIANT_2SM_SK(tile) (RG_NUM_TILES * RG_NUM_SPLITS + RG_NUM_TILES + 2 * RG_NUM_SPLITS + \
-                                 (tile) - RG_TILE_256x128)
-#define RG_NUM_VARIANTS (RG_NUM_TILES * RG_NUM_SPLITS + RG_NUM_TILES + 2 * RG_NUM_SPLITS + 2)
+  (RG_NUM_TILES * RG_NUM_SPLITS + RG_NUM_TILES + RG_PAIR_INDEX(tile) * RG_NUM_SPLITS + (log2_split))
+/* cta_group::2 stream-K variant of a 256-row tile (ids 52, 53, 54 for 256x128,
+ * 256x256, 256x192): the stream-K schedule above over 256 x BN pair tiles and
+ * the 2-CTA clusters (one per SM pair); each CTA of a cluster sums its own 128
+ * rows of a shared tile in the fixed order of the pieces' K ranges.  It removes
+ * the partial last wave that quantises the large cells (Sec. 9.4 names split-K
+ * as the remedy). */
+#define RG_VARIANT_2SM_SK(tile) (RG_NUM_TILES * RG_NUM_SPLITS + RG_NUM_TILES + \
+                                 RG_NUM_PAIR_TILES * RG_NUM_SPLITS + RG_PAIR_INDEX(tile))
+#define RG_NUM_VARIANTS (RG_NUM_TILES * RG_NUM_SPLITS + RG_NUM_TILES + RG_NUM_PAIR_TILES * RG_NUM_SPLITS + \
+                         RG_NUM_PAIR_TILES)
 
 typedef struct rg_ctx rg_ctx;
 typedef struct rg_plan rg_plan;
@@ -221,8 +227,8 @@ int rg_launch_count(const rg_ctx* ctx, int64_t* out);
  * size (pass 0 for "same as M, N, K"); the padding is never materialised:
  * out-of-range operand reads are zero-filled and out-of-range outputs dropped.
  * M, N or K == 0: nothing to compute (C untouched if M or N is 0; C = 0 for
- * K == 0 with beta = 0).  Split-K (S > 1) of the 128x256, 256x128 and 256x256
- * 1-CTA tiles (not 256x256 with S = 8) runs as clusters of S CTAs that sum the
+ * K == 0 with beta = 0).  Split-K (S > 1) of the 128x256, 256x128, 256x256 and
+ * 256x192 1-CTA tiles (not 256x256 with S = 8) runs as clusters of S CTAs that sum the
  * S partials through distributed shared memory; the other split variants sum
  * them through the context's workspace.  Both sum in the order 0..S-1, so the
  * two forms give the same bits. */
@@ -296,8 +302,8 @@ int rg_surface_stats(const rg_grid* grid, const int64_t* t_ns, double* tflops_ou
  * variant the autotuner chose for it: a 1-CTA tile with in-kernel split-K
  * (S = 1/2/4/8) or a cta_group::2 pair tile with split-K; a stream-K variant
  * runs as its tile with split 1; variant = -1 means the group's tile, split 1.
- * The problems are sorted into nine kernel families (the seven 1-CTA tiles, the
- * two cta_group::2 tiles); each family present becomes one persistent launch
+ * The problems are sorted into eleven kernel families (the eight 1-CTA tiles, the
+ * three cta_group::2 tiles); each family present becomes one persistent launch
  * over all SMs whose work units are the concatenation of its problems'
  * (tile, K split) units.  Each problem has its own sizes, operands, leading
  * dimensions, beta and padded launch extents (pm, pn, pk as in rg_gemm;

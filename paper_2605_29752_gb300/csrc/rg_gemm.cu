@@ -106,7 +106,10 @@ struct GemmArgs {
 template <int BM, int BN, int STAGES, int CTAS = 1>
 struct KCfg {
   static constexpr int A_BYTES = BM * kBK * 2;
-  static constexpr int B_BYTES = kBK * (BN / CTAS) * 2;
+  // B columns a CTA loads: its BN / CTAS rounded up to whole 64-column (128-byte) boxes
+  // (a 256x192 pair's CTA loads 128 columns, of which its MMAs read 96)
+  static constexpr int BN_LOAD = (BN / CTAS + 63) / 64 * 64;
+  static constexpr int B_BYTES = kBK * BN_LOAD * 2;
   static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
   static constexpr int HALVES = BM / 128;
   static constexpr int ACC_COLS = HALVES * BN;
@@ -122,7 +125,7 @@ struct KCfg {
   static_assert(A_BYTES % 1024 == 0 && B_BYTES % 1024 == 0, "stages must keep 1024-byte alignment");
   static_assert(SMEM_BYTES <= 232448, "shared memory budget");
   static_assert(BN % 64 == 0 && BN <= 256 && (BM == 128 || BM == 256), "tile shape");
-  static_assert(CTAS == 1 || (CTAS == 2 && BM == 128 && BN % 128 == 0), "pair tile shape");
+  static_assert(CTAS == 1 || (CTAS == 2 && BM == 128 && BN % 64 == 0), "pair tile shape");
 };
 
 __device__ __forceinline__ void st_shared_v4(uint32_t addr, float a, float b, float c, float d) {
@@ -695,7 +698,7 @@ __device__ __forceinline__ void gemm_body(Sched& sched, float* ws, int32_t* tick
             const uint32_t fb = mapa_shared(full_bar(stage), 0);
             tma_load_2d_pair(sa, w.a, fb, kb * kBK, w.tm * BM);
 #pragma unroll
-            for (int j = 0; j < BN / 128; ++j)
+            for (int j = 0; j < C::BN_LOAD / 64; ++j)
               tma_load_2d_pair(sb + j * (kBK * 128), w.b, fb, w.tn * BN + sched.rank * (BN / 2) + j * 64, kb * kBK);
           } else {
             mbar_arrive_expect_tx(full_bar(stage), C::STAGE_BYTES);
@@ -1263,7 +1266,7 @@ struct TileKernel {
 
 // Stages of the cta_group::2 instances: 16 KB of A + BN/2 x 64 of B per stage and CTA.
 template <int BN>
-constexpr int kStages2Sm = BN == 256 ? 6 : 8;
+constexpr int kStages2Sm = BN == 128 ? 8 : 6;
 
 template <int BM, int BN, int ST>
 TileKernel make_tile_kernel() {
@@ -1284,14 +1287,14 @@ static const TileKernel& tile_kernel(int tile) {
   static const TileKernel table[RG_NUM_TILES] = {
       make_tile_kernel<128, 64, 8>(),  make_tile_kernel<128, 128, 6>(), make_tile_kernel<128, 256, 4>(),
       make_tile_kernel<256, 64, 4>(),  make_tile_kernel<256, 128, 4>(), make_tile_kernel<256, 256, 3>(),
-      make_tile_kernel<128, 192, 4>(),
+      make_tile_kernel<128, 192, 4>(), make_tile_kernel<256, 192, 3>(),
   };
   return table[tile];
 }
 
-// Grouped launches come in nine kernel families: the seven 1-CTA tiles, then the
-// cta_group::2 forms of the 256x128 and 256x256 tiles.
-constexpr int kGroupFamilies = RG_NUM_TILES + 2;
+// Grouped launches come in eleven kernel families: the eight 1-CTA tiles, then the
+// cta_group::2 forms of the pair tiles (256x128, 256x256, 256x192).
+constexpr int kGroupFamilies = RG_NUM_TILES + RG_NUM_PAIR_TILES;
 using GroupedFn = void (*)(const GroupHeader*, const GroupItem*, const CUtensorMap, float*, int32_t*, int32_t*,
                            long long);
 static const void* grouped_kernel(int family) {
@@ -1299,16 +1302,17 @@ static const void* grouped_kernel(int family) {
       gemm_bf16_grouped_kernel<128, 64, 8>,  gemm_bf16_grouped_kernel<128, 128, 6>,
       gemm_bf16_grouped_kernel<128, 256, 4>, gemm_bf16_grouped_kernel<256, 64, 4>,
       gemm_bf16_grouped_kernel<256, 128, 4>, gemm_bf16_grouped_kernel<256, 256, 3>,
-      gemm_bf16_grouped_kernel<128, 192, 4>,
+      gemm_bf16_grouped_kernel<128, 192, 4>, gemm_bf16_grouped_kernel<256, 192, 3>,
       gemm_bf16_grouped_2sm_kernel<128, kStages2Sm<128>>, gemm_bf16_grouped_2sm_kernel<256, kStages2Sm<256>>,
+      gemm_bf16_grouped_2sm_kernel<192, kStages2Sm<192>>,
   };
   return reinterpret_cast<const void*>(table[family]);
 }
 static int family_smem(int family) {
-  return family < RG_NUM_TILES ? tile_kernel(family).smem : tile_kernel(RG_TILE_256x128 + family - RG_NUM_TILES).smem2;
+  return family < RG_NUM_TILES ? tile_kernel(family).smem : tile_kernel(pair_tile(family - RG_NUM_TILES)).smem2;
 }
 static int family_bn(int family) {
-  return family < RG_NUM_TILES ? tile_kernel(family).bn : tile_kernel(RG_TILE_256x128 + family - RG_NUM_TILES).bn;
+  return family < RG_NUM_TILES ? tile_kernel(family).bn : tile_kernel(pair_tile(family - RG_NUM_TILES)).bn;
 }
 // The family and the variant a grouped problem runs: stream-K variants run as
 // their tile with split 1 (the grouped scheduler has no stream-K form).
@@ -1317,7 +1321,7 @@ static int grouped_variant(int v) {
   return variant_2sm(v) ? RG_VARIANT_2SM(variant_tile(v), 0) : RG_VARIANT(variant_tile(v), 0);
 }
 static int family_of(int v) {
-  return variant_2sm(v) ? RG_NUM_TILES + variant_tile(v) - RG_TILE_256x128 : variant_tile(v);
+  return variant_2sm(v) ? RG_NUM_TILES + RG_PAIR_INDEX(variant_tile(v)) : variant_tile(v);
 }
 
 }  // namespace rg

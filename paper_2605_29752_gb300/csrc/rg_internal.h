@@ -40,15 +40,21 @@ struct TileShape {
 TileShape tile_shape(int tile);
 // Variant ids: tile * RG_NUM_SPLITS + log2(split) for the split-K variants, then
 // RG_VARIANT_SK(tile) (stream-K), RG_VARIANT_2SM(tile, log2(split)) (cta_group::2,
-// 256-row tiles with BN >= 128) and RG_VARIANT_2SM_SK(tile) (cta_group::2 stream-K).
+// the pair tiles 256x128, 256x256, 256x192) and RG_VARIANT_2SM_SK(tile)
+// (cta_group::2 stream-K).
 constexpr int kClassicVariants = RG_NUM_TILES * RG_NUM_SPLITS;
 constexpr int k2SmVariants = kClassicVariants + RG_NUM_TILES;
-constexpr int k2SmSkVariants = k2SmVariants + 2 * RG_NUM_SPLITS;
+constexpr int k2SmSkVariants = k2SmVariants + RG_NUM_PAIR_TILES * RG_NUM_SPLITS;
+// The tile of the i-th pair tile (RG_PAIR_INDEX inverted).
+constexpr int pair_tile(int i) { return i == 2 ? RG_TILE_256x192 : RG_TILE_256x128 + i; }
+constexpr bool is_pair_tile(int t) {
+  return t == RG_TILE_256x128 || t == RG_TILE_256x256 || t == RG_TILE_256x192;
+}
 inline bool variant_2sm(int v) { return v >= k2SmVariants; }
 inline bool variant_streamk(int v) { return (v >= kClassicVariants && v < k2SmVariants) || v >= k2SmSkVariants; }
 inline int variant_tile(int v) {
-  return v >= k2SmSkVariants     ? RG_TILE_256x128 + (v - k2SmSkVariants)
-         : v >= k2SmVariants     ? RG_TILE_256x128 + (v - k2SmVariants) / RG_NUM_SPLITS
+  return v >= k2SmSkVariants     ? pair_tile(v - k2SmSkVariants)
+         : v >= k2SmVariants     ? pair_tile((v - k2SmVariants) / RG_NUM_SPLITS)
          : v >= kClassicVariants ? v - kClassicVariants
                                  : v / RG_NUM_SPLITS;
 }

@@ -264,8 +264,9 @@ extern "C" int rg_plan_lookup(const rg_plan* plan, int64_t M, int64_t N, int64_t
 namespace {
 const char kMagic[8] = {'R', 'G', 'P', 'L', 'A', 'N', '0', '1'};
 // 2: the variant numbering without the multicast pairs, with cta_group::2 stream-K and FP8 ids;
-// 3: seven tiles (128 x 192 added), which renumbers every id from 24 on
-const uint32_t kPlanFileVersion = 3;
+// 3: seven tiles (128 x 192 added), which renumbers every id from 24 on;
+// 4: eight tiles and three pair tiles (256 x 192 added), which renumbers every id from 28 on
+const uint32_t kPlanFileVersion = 4;
 
 template <class T>
 void put(std::vector<uint8_t>& b, const T* p, size_t n) {

@@ -22,7 +22,7 @@ void clear_error() { g_last_error.clear(); }
 
 TileShape tile_shape(int tile) {
   static const TileShape shapes[RG_NUM_TILES] = {{128, 64}, {128, 128}, {128, 256}, {256, 64},
-                                                 {256, 128}, {256, 256}, {128, 192}};
+                                                 {256, 128}, {256, 256}, {128, 192}, {256, 192}};
   return shapes[tile];
 }
 

@@ -32,53 +32,53 @@ RG_ERR_NO_DEVICE = -9
 
 RG_T_UNMEASURED = 1 << 60
 RG_T_OTHER_SHARD = 0
-RG_NUM_TILES = 7
+RG_NUM_TILES = 8
 RG_NUM_PAPER_TILES = 6                # tiles 0..5: the paper's six (best-of-6)
 RG_NUM_SPLITS = 4
-RG_NUM_VARIANTS = RG_NUM_TILES * RG_NUM_SPLITS + RG_NUM_TILES + 2 * RG_NUM_SPLITS + 2
-TILES = [(128, 64), (128, 128), (128, 256), (256, 64), (256, 128), (256, 256), (128, 192)]
+PAIR_TILES = [4, 5, 7]                # 256x128, 256x256, 256x192: also run as cta_group::2 pairs
+RG_NUM_VARIANTS = RG_NUM_TILES * RG_NUM_SPLITS + RG_NUM_TILES + len(PAIR_TILES) * (RG_NUM_SPLITS + 1)
+TILES = [(128, 64), (128, 128), (128, 256), (256, 64), (256, 128), (256, 256), (128, 192), (256, 192)]
 SPLITS = [1, 2, 4, 8]
 SK = "SK"
 TWO_SM = "2SM"
 TWO_SM_SK = "2SM-SK"
 _BASE_2SM = RG_NUM_TILES * RG_NUM_SPLITS + RG_NUM_TILES
-_BASE_2SM_SK = _BASE_2SM + 2 * RG_NUM_SPLITS
+_BASE_2SM_SK = _BASE_2SM + len(PAIR_TILES) * RG_NUM_SPLITS
 
 
 def variant(tile: int, split=1) -> int:
     """Variant id of a tile with split factor 1/2/4/8, split="SK" for stream-K, "2SM" / ("2SM", S)
     for the cta_group::2 pair with split factor S, or "2SM-SK" for the cta_group::2 stream-K form
-    (the last three for tiles 256x128 and 256x256 only)."""
-    if split == TWO_SM_SK:
-        if tile not in (4, 5):
-            raise ValueError("the 2-SM variants exist for the 256x128 and 256x256 tiles only")
-        return _BASE_2SM_SK + tile - 4
-    if split == TWO_SM or (isinstance(split, tuple) and split[0] == TWO_SM):
-        if tile not in (4, 5):
-            raise ValueError("the 2-SM variant exists for the 256x128 and 256x256 tiles only")
+    (the last three for the pair tiles 256x128, 256x256 and 256x192 only)."""
+    if split == TWO_SM_SK or split == TWO_SM or (isinstance(split, tuple) and split[0] == TWO_SM):
+        if tile not in PAIR_TILES:
+            raise ValueError("the 2-SM variants exist for the 256x128, 256x256 and 256x192 tiles only")
+        i = PAIR_TILES.index(tile)
+        if split == TWO_SM_SK:
+            return _BASE_2SM_SK + i
         s = 1 if split == TWO_SM else split[1]
-        return _BASE_2SM + (tile - 4) * RG_NUM_SPLITS + SPLITS.index(s)
+        return _BASE_2SM + i * RG_NUM_SPLITS + SPLITS.index(s)
     if split == SK:
         return RG_NUM_TILES * RG_NUM_SPLITS + tile
     return tile * RG_NUM_SPLITS + SPLITS.index(split)
 
 
 def variant_tile(v: int) -> int:
-    """Tile index (0..6) of a variant id."""
+    """Tile index (0..7) of a variant id."""
     n = RG_NUM_TILES * RG_NUM_SPLITS
     if v >= _BASE_2SM_SK:
-        return 4 + v - _BASE_2SM_SK
+        return PAIR_TILES[v - _BASE_2SM_SK]
     if v >= _BASE_2SM:
-        return 4 + (v - _BASE_2SM) // RG_NUM_SPLITS
+        return PAIR_TILES[(v - _BASE_2SM) // RG_NUM_SPLITS]
     return v - n if v >= n else v // RG_NUM_SPLITS
 
 
 def variant_name(v: int) -> str:
     if v >= _BASE_2SM_SK:
-        bm, bn = TILES[4 + v - _BASE_2SM_SK]
+        bm, bn = TILES[variant_tile(v)]
         return f"{bm}x{bn}/2SM-SK"
     if v >= _BASE_2SM:
-        bm, bn = TILES[4 + (v - _BASE_2SM) // RG_NUM_SPLITS]
+        bm, bn = TILES[variant_tile(v)]
         s = SPLITS[(v - _BASE_2SM) % RG_NUM_SPLITS]
         return f"{bm}x{bn}/2SM" + ("" if s == 1 else f"-S{s}")
     if v >= RG_NUM_TILES * RG_NUM_SPLITS:

@@ -11,7 +11,7 @@ from oracle import gemm as og
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-ALL_VARIANTS = list(range(45))          # 28 split-K (7 tiles), 7 stream-K, 8 cta_group::2 (2 tiles x 4 splits), 2 cta_group::2 stream-K
+ALL_VARIANTS = list(range(55))          # 32 split-K (8 tiles), 8 stream-K, 12 cta_group::2 (3 tiles x 4 splits), 3 cta_group::2 stream-K
 
 
 @pytest.fixture(scope="module")
@@ -126,7 +126,7 @@ def test_beta_one_accumulates(rg, ctx, v):
     check(run(rg, ctx, a, b, v, beta=1, c0=c0), a, b, c0=c0)
 
 
-@pytest.mark.parametrize("v", [1, 2, 3, 7, 11, 15, 19, 23, 25, 26, 27, 28, 29, 30, 31, 32, 33, 34])
+@pytest.mark.parametrize("v", [1, 2, 3, 7, 11, 15, 19, 23, 25, 26, 27, 29, 30, 31, 32, 33, 34, 35, 36, 37, 38, 39])
 def test_split_k_deterministic(rg, ctx, v):
     M, N, K = 512, 384, 2048
     a, b = synthetic.operands_bf16(M, N, K, seed=7)
@@ -143,7 +143,7 @@ def test_more_splits_than_k_blocks(rg, ctx):
 
 
 @pytest.mark.parametrize("shape", [(4096, 4096, 4096), (3968, 4096, 3840), (4096, 1152, 4096)])
-@pytest.mark.parametrize("tile", range(7))
+@pytest.mark.parametrize("tile", range(8))
 def test_full_size_sampled(rg, ctx, shape, tile):
     M, N, K = shape
     a_bits, b_bits = synthetic.operands_bf16(M, N, K, seed=0)
@@ -182,7 +182,7 @@ def test_alignment_and_argument_errors(rg, ctx):
     rg.rg_check(ctx)
 
 
-@pytest.mark.parametrize("tile", range(7))
+@pytest.mark.parametrize("tile", range(8))
 @pytest.mark.parametrize("shape", [(1664, 1664, 2048), (2176, 1920, 1152), (2560, 2048, 1024), (128, 128, 4096),
                                    (256, 512, 640)])
 def test_stream_k_uneven_waves(rg, ctx, tile, shape):
@@ -196,7 +196,7 @@ def test_stream_k_uneven_waves(rg, ctx, tile, shape):
     assert np.array_equal(c1, run(rg, ctx, a, b, v))
 
 
-@pytest.mark.parametrize("v", [28, 31, 33, 34])
+@pytest.mark.parametrize("v", [32, 35, 37, 38, 39])
 def test_stream_k_beta_one(rg, ctx, v):
     M, N, K = 640, 384, 1536
     a, b = synthetic.operands_bf16(M, N, K, seed=13)
@@ -204,7 +204,7 @@ def test_stream_k_beta_one(rg, ctx, v):
     check(run(rg, ctx, a, b, v, beta=1, c0=c0), a, b, c0=c0)
 
 
-@pytest.mark.parametrize("tile", [4, 5])
+@pytest.mark.parametrize("tile", [4, 5, 7])
 @pytest.mark.parametrize("shape", [(384, 640, 1024), (1664, 1664, 2048), (128, 64, 256), (200, 264, 96),
                                    (4096, 1152, 4096)])
 def test_two_sm(rg, ctx, tile, shape):
@@ -228,7 +228,7 @@ def test_two_sm(rg, ctx, tile, shape):
     assert np.array_equal(c, run(rg, ctx, a, b, rg.variant(tile, 1)))
 
 
-@pytest.mark.parametrize("tile", [4, 5])
+@pytest.mark.parametrize("tile", [4, 5, 7])
 def test_two_sm_exact_cases_beta_and_padding(rg, ctx, tile):
     v = rg.variant(tile, rg.TWO_SM)
     one = np.float32(1.0).view(np.uint32) >> 16
@@ -251,7 +251,7 @@ def test_two_sm_exact_cases_beta_and_padding(rg, ctx, tile):
     assert np.array_equal(c_plain, run(rg, ctx, a, b, v, pads=(M + 256, N + 128, K + 384)))
 
 
-@pytest.mark.parametrize("tile", [4, 5])
+@pytest.mark.parametrize("tile", [4, 5, 7])
 @pytest.mark.parametrize("split", [2, 4, 8])
 def test_two_sm_split_k(rg, ctx, tile, split):
     """cta_group::2 with split-K: each CTA reduces its own 128 rows in the fixed split
@@ -271,7 +271,7 @@ def test_two_sm_split_k(rg, ctx, tile, split):
     check(run(rg, ctx, a, b, v, beta=1, c0=c0), a, b, c0=c0)
 
 
-@pytest.mark.parametrize("tile", [4, 5])
+@pytest.mark.parametrize("tile", [4, 5, 7])
 @pytest.mark.parametrize("shape", [(4096, 1280, 4096), (4096, 2432, 1024), (2560, 2560, 2048), (3968, 3712, 512),
                                    (1000, 1000, 1000), (512, 512, 1024), (200, 264, 96)])
 def test_two_sm_stream_k(rg, ctx, tile, shape):
@@ -297,7 +297,7 @@ def test_two_sm_stream_k(rg, ctx, tile, shape):
     assert np.array_equal(c, run(rg, ctx, a, b, v))
 
 
-@pytest.mark.parametrize("tile", [4, 5])
+@pytest.mark.parametrize("tile", [4, 5, 7])
 def test_two_sm_stream_k_beta_and_padding(rg, ctx, tile):
     v = rg.variant(tile, rg.TWO_SM_SK)
     M, N, K = 2304, 1536, 1536
@@ -320,7 +320,7 @@ def test_two_sm_stream_k_beta_and_padding(rg, ctx, tile):
     check(run(rg, ctx, a, b, v, pads=(M + 256, N + 256, K + 128)), a, b)
 
 
-@pytest.mark.parametrize("tile", range(7))
+@pytest.mark.parametrize("tile", range(8))
 def test_column_panel_tile_order(rg, ctx, tile):
     """N = 8192 with K = 4096 puts more tile columns than one 32 MiB panel of B holds, so
     tiles run in column panels: every variant family still covers every tile once
@@ -337,7 +337,7 @@ def test_column_panel_tile_order(rg, ctx, tile):
         ratio, exact_zero = og.error_ratio(got, ref, s)
         assert exact_zero and ratio <= og.bound(K), ratio
     others = [rg.variant(tile, rg.SK)]
-    if tile in (4, 5):                          # the 256-row tiles also run as cta_group::2 pairs
+    if tile in rg.PAIR_TILES:                   # the pair tiles also run as cta_group::2 pairs
         others.append(rg.variant(tile, rg.TWO_SM))
     for v in others:
         got = run(rg, ctx, a, b, v)

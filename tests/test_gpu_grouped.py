@@ -36,7 +36,7 @@ SHAPES = [(128, 128, 128), (300, 200, 328), (1024, 512, 768), (256, 1024, 64), (
           (2048, 384, 256), (128, 256, 4096), (640, 640, 640)]
 
 
-@pytest.mark.parametrize("tile", range(7))
+@pytest.mark.parametrize("tile", range(8))
 def test_grouped_mixed_shapes_match_oracle_and_rg_gemm(rg, ctx, tile):
     g = rg.rg_group_create(ctx, tile, 64)
     try:
@@ -212,7 +212,7 @@ def test_grouped_split_k_and_two_sm_items(rg, ctx, case):
         rg.rg_group_destroy(g)
 
 
-@pytest.mark.parametrize("tile", range(7))
+@pytest.mark.parametrize("tile", range(8))
 def test_cluster_split_equals_workspace_split(rg, ctx, tile):
     """rg_gemm runs split-K of the 128x256, 256x128 and 256x256 tiles as a cluster of S CTAs that
     reduce through distributed shared memory (the workspace kernel for the smaller tiles and where the

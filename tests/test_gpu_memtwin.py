@@ -32,7 +32,7 @@ def dev_bf16(bits):
     return torch.from_numpy(np.ascontiguousarray(bits).view(np.int16)).cuda().view(torch.bfloat16)
 
 
-@pytest.mark.parametrize("tile", range(7))
+@pytest.mark.parametrize("tile", range(8))
 @pytest.mark.parametrize("shape", [(300, 264, 200), (128, 64, 64), (520, 776, 1000)])
 def test_memtwin_stays_inside_c(rg, ctx, tile, shape):
     M, N, K = shape

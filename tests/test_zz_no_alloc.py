@@ -50,11 +50,11 @@ CASES = [
     ((300, 200, 328), 21, 0),        # 256x256, split 2, ragged
     ((384, 512, 1024), 14, 1),       # 256x64, split 4, beta = 1
     ((2048, 1536, 1024), 8, 0),      # 128x256, split 1
-    ((640, 512, 2048), 29, 0),       # 128x128, stream-K
-    ((768, 1024, 2048), 39, 0),      # 256x256 cta_group::2 pair, split 1
-    ((520, 512, 2048), 40, 0),       # 256x256 cta_group::2 pair, split 2, ragged M
+    ((640, 512, 2048), 33, 0),       # 128x128, stream-K
+    ((768, 1024, 2048), 44, 0),      # 256x256 cta_group::2 pair, split 1
+    ((520, 512, 2048), 45, 0),       # 256x256 cta_group::2 pair, split 2, ragged M
     ((2048, 1024, 1024), 5, 0),      # 128x128 split 2 on 128 tiles: partials exactly the scratch size
-    ((1024, 1024, 2048), 29, 0),     # 128x128 stream-K on 64 tiles, 2 pieces each: half the scratch
+    ((1024, 1024, 2048), 33, 0),     # 128x128 stream-K on 64 tiles, 2 pieces each: half the scratch
     ((768, 1000, 1024), 25, 0),      # 128x192, split 2, ragged N
 ]
 
@@ -83,7 +83,7 @@ def test_matches_rg_gemm_twice(rg, shape, v, beta):
 def test_allocates_nothing_after_set_up(rg):
     """Free device memory (cudaMemGetInfo) is the same before and after a second round of calls
     over split-K, stream-K and cta_group::2 variants: nothing on this path allocates."""
-    cases = [((512, 768, 2048), 7), ((640, 512, 2048), 29), ((520, 512, 2048), 40), ((1024, 1024, 1024), 4)]
+    cases = [((512, 768, 2048), 7), ((640, 512, 2048), 33), ((520, 512, 2048), 45), ((1024, 1024, 1024), 4)]
     bufs = []
     for (M, N, K), v in cases:
         a, b = synthetic.operands_bf16(M, N, K, seed=3)
@@ -112,12 +112,12 @@ def test_rejects_split_beyond_scratch(rg):
     # one tile over the limit: 128x128 split 2 on 2048 x 1152 (144 tiles, 18 MiB of partials)
     assert rg.rg_gemm_noalloc(2048, 1152, K, A, K, B, N, C, N, 5, 0) == rg.RG_ERR_SHAPE
     # cta_group::2 256x256 split 2 on 1280 x 2048: 40 tiles x 2 x 256 KiB = 20 MiB
-    assert rg.rg_gemm_noalloc(1280, 2048, K, A, K, B, N, C, N, 40, 0) == rg.RG_ERR_SHAPE
+    assert rg.rg_gemm_noalloc(1280, 2048, K, A, K, B, N, C, N, 45, 0) == rg.RG_ERR_SHAPE
     # stream-K 128x128 on 1792 x 1280 x 2048: 140 tiles, fewer than the SMs, so every tile is
     # shared by at least 2 CTAs: at least 2 x 140 x 64 KiB = 17.5 MiB
     A2 = torch.zeros((1792, 2048), device="cuda", dtype=torch.bfloat16)
     B2 = torch.zeros((2048, 1280), device="cuda", dtype=torch.bfloat16)
-    assert rg.rg_gemm_noalloc(1792, 1280, 2048, A2, 2048, B2, 1280, C, N, 29, 0) == rg.RG_ERR_SHAPE
+    assert rg.rg_gemm_noalloc(1792, 1280, 2048, A2, 2048, B2, 1280, C, N, 33, 0) == rg.RG_ERR_SHAPE
     torch.cuda.synchronize()
     assert torch.all(C == 3.0)                       # nothing was enqueued
     assert rg.rg_gemm_noalloc(M, N, K, A, K, B, N, C, N, 4, 0) == rg.RG_OK   # split 1: no limit
