@@ -289,6 +289,19 @@ int rg_gemm_plan_host(rg_ctx* ctx, const rg_plan* plan, int64_t M, int64_t N, in
 int rg_plan_save(const rg_plan* plan, const rg_ctx* ctx, const char* path);
 int rg_plan_load(const char* path, const rg_ctx* ctx, rg_plan** out);
 
+/* ---- variant and schedule queries (host; no device needed) ----
+ * rg_variant_desc: out = {tile, split factor (1 for stream-K), stream-K (0/1),
+ * cta_group::2 (0/1), BM, BN} of BF16 variant `v` in [0, RG_NUM_VARIANTS); the
+ * pair forms report their 256-row tile.  RG_ERR_INVALID for another id.
+ * rg_streamk_geometry: the stream-K schedule of `tiles` output tiles (pair tiles
+ * for a cta_group::2 variant) of `kblocks` 64-deep K blocks on `units` CTAs
+ * (clusters): out = {CTAs (clusters) launched, tiles run whole data-parallel,
+ * CTAs (clusters) sharing the remaining tiles' K iterations, most CTAs sharing
+ * one tile}, as the stream-K variants' launcher and kernel use it.  tiles,
+ * kblocks, units > 0, else RG_ERR_INVALID. */
+int rg_variant_desc(int32_t v, int32_t out[6]);
+int rg_streamk_geometry(int64_t tiles, int64_t kblocks, int64_t units, int64_t out[4]);
+
 /* ---- surface statistics (Sec. 2 definitions; Sec. 8.6 conventions; host) ----
  * tflops_out[c] = (2.0*M*N*K) / (t_ns[c] * 1e3) per cell (may be NULL);
  * rough_out = {R_M, R_N, R_K, R_3D = (R_M+R_N+R_K)/3, R_N on the largest-K slice};

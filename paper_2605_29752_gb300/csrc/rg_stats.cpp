@@ -118,6 +118,32 @@ extern "C" void rg_sweep_opts_default(rg_sweep_opts* o) {
   o->reserved = 0;
 }
 
+extern "C" int rg_variant_desc(int32_t v, int32_t out[6]) {
+  rg::clear_error();
+  if (!out || v < 0 || v >= RG_NUM_VARIANTS) return rg::fail(RG_ERR_INVALID, "rg_variant_desc: variant id out of range");
+  const int tile = rg::variant_tile(v);
+  const rg::TileShape ts = rg::tile_shape(tile);
+  out[0] = tile;
+  out[1] = rg::variant_split(v);
+  out[2] = rg::variant_streamk(v) ? 1 : 0;
+  out[3] = rg::variant_2sm(v) ? 1 : 0;
+  out[4] = ts.bm;
+  out[5] = ts.bn;
+  return RG_OK;
+}
+
+extern "C" int rg_streamk_geometry(int64_t tiles, int64_t kblocks, int64_t units, int64_t out[4]) {
+  rg::clear_error();
+  if (!out || tiles <= 0 || kblocks <= 0 || units <= 0 || tiles > (1LL << 30) || kblocks > (1LL << 24))
+    return rg::fail(RG_ERR_INVALID, "rg_streamk_geometry: sizes");
+  const rg::SkGeometry g = rg::sk_geometry(tiles, kblocks, units);
+  out[0] = g.grid;
+  out[1] = g.dp_tiles;
+  out[2] = g.tail_ctas;
+  out[3] = g.max_pieces;
+  return RG_OK;
+}
+
 extern "C" int rg_surface_stats(const rg_grid* grid, const int64_t* t_ns, double* tflops_out,
                                 double rough_out[5], double* mean_out) {
   rg::clear_error();

@@ -218,6 +218,8 @@ _sigs = {
     "rg_plan_save": (C.c_int, [_P, _P, C.c_char_p]),
     "rg_plan_load": (C.c_int, [C.c_char_p, _P, C.POINTER(_P)]),
     "rg_surface_stats": (C.c_int, [C.POINTER(rg_grid), _P, _P, _P, _P]),
+    "rg_variant_desc": (C.c_int, [_I32, _P]),
+    "rg_streamk_geometry": (C.c_int, [_I64, _I64, _I64, _P]),
     "rg_sweep": (C.c_int, [_P, C.POINTER(rg_grid), _I32, _P, _P, _P, _P, _P, C.POINTER(rg_sweep_opts), _P, _P, _P,
                            _P]),
     "rg_gemm_memtwin": (C.c_int, [_P, _I64, _I64, _I64, _P, _I64, _P, _I64, _P, _I64, _I32, _P]),
@@ -431,6 +433,20 @@ def rg_plan_load_status(path: str, ctx: int | None = None) -> int:
     if code == RG_OK:
         _lib.rg_plan_free(h.value)
     return code
+
+
+def rg_variant_desc(v: int) -> dict:
+    """The library's description of BF16 variant v (host)."""
+    out = np.zeros(6, np.int32)
+    _check(_lib.rg_variant_desc(v, out.ctypes.data), "rg_variant_desc")
+    return dict(zip(("tile", "split", "streamk", "two_sm", "bm", "bn"), (int(x) for x in out)))
+
+
+def rg_streamk_geometry(tiles: int, kblocks: int, units: int) -> dict:
+    """The stream-K schedule the library launches for `tiles` tiles of `kblocks` K blocks on `units` CTAs."""
+    out = np.zeros(4, np.int64)
+    _check(_lib.rg_streamk_geometry(tiles, kblocks, units, out.ctypes.data), "rg_streamk_geometry")
+    return dict(zip(("grid", "dp_tiles", "tail_ctas", "max_pieces"), (int(x) for x in out)))
 
 
 def rg_surface_stats(grid: rg_grid, t_ns: np.ndarray):

@@ -339,3 +339,86 @@ def test_plan_file_of_another_version_is_refused(rg, tmp_path):
     data[8:12] = (2).to_bytes(4, "little")                  # the version field: the six-tile numbering
     open(p, "wb").write(bytes(data))
     assert rg.rg_plan_load_status(p) == rg.RG_ERR_PLAN_MISMATCH
+
+
+def test_variant_desc_agrees_with_the_binding(rg):
+    """The library's own description of every BF16 variant id (tile, split, stream-K, cta_group::2, tile
+    shape) agrees with the binding's id arithmetic and names; ids outside the range are refused."""
+    for v in range(rg.RG_NUM_VARIANTS):
+        d = rg.rg_variant_desc(v)
+        name = rg.variant_name(v)
+        assert d["tile"] == rg.variant_tile(v), v
+        assert (d["bm"], d["bn"]) == rg.TILES[d["tile"]], v
+        assert d["two_sm"] == ("/2SM" in name) and d["streamk"] == name.endswith("SK"), (v, name, d)
+        if d["two_sm"]:
+            assert d["tile"] in rg.PAIR_TILES
+        if not d["streamk"]:
+            expect = name.endswith(f"/S{d['split']}") or name.endswith(f"-S{d['split']}") or \
+                (d["split"] == 1 and name.endswith("/2SM"))
+            assert expect, (v, name, d)
+    for bad in (-1, rg.RG_NUM_VARIANTS, rg.RG_FP8_VARIANT_BASE):
+        with pytest.raises(rg.RGError):
+            rg.rg_variant_desc(bad)
+
+
+def _streamk_units(g, tiles, kblocks, units):
+    """The (tile -> [(k0, k1, piece, pieces)]) cover that CTA g = 0..grid-1 runs under the library's
+    geometry: data-parallel tiles g, g + units, ... below dp_tiles, then the CTA's share
+    [h I / c, (h+1) I / c) of the tail's I = (tiles - dp_tiles) kblocks iterations, cut at tile edges."""
+    dp, c = g["dp_tiles"], g["tail_ctas"]
+    cover = {}
+    for cta in range(g["grid"]):
+        for t in range(cta, dp, units):
+            cover.setdefault(t, []).append((0, kblocks, 0, 1))
+    if c:
+        iters = (tiles - dp) * kblocks
+        begin = lambda h: h * iters // c
+        owner = lambda x: max(h for h in range(c) if begin(h) <= x)
+        for h in range(c):
+            b, e = begin(h), begin(h + 1)
+            if e <= b:
+                continue
+            for lt in range(b // kblocks, (e - 1) // kblocks + 1):
+                tb = lt * kblocks
+                first, last = owner(tb), owner(tb + kblocks - 1)
+                cover.setdefault(dp + lt, []).append((max(b, tb) - tb, min(e, tb + kblocks) - tb, h - first,
+                                                      last - first + 1))
+    return cover
+
+
+@pytest.mark.parametrize("units", [152, 76, 20])
+def test_streamk_geometry_covers_every_k_iteration_once(rg, units):
+    """The stream-K schedule covers each tile's K blocks exactly once, in pieces numbered in K order; a
+    tile is shared by at most max_pieces CTAs, and by at most 2 whenever the tiles fill a whole wave;
+    whole waves without a remainder run data-parallel; and the form follows the remainder r = tiles mod
+    units: the balanced form (all waves but the last data-parallel) where r <= units/4 or r >= units/2,
+    the remainder form (every whole wave data-parallel) in between."""
+    rs = np.random.default_rng(units)
+    cases = [(t, kb) for t in (1, 3, units - 1, units, units + 1, units + units // 4, units + units // 4 + 1,
+                               units + units // 2 - 1, units + units // 2, 2 * units - 1, 3 * units + 5)
+             for kb in (1, 2, 3, 4, 16, 64, 65)]
+    cases += [(int(rs.integers(1, 5 * units)), int(rs.integers(1, 80))) for _ in range(60)]
+    for tiles, kb in cases:
+        g = rg.rg_streamk_geometry(tiles, kb, units)
+        waves, rem = divmod(tiles, units)
+        assert g["grid"] <= max(units, 1)
+        if rem == 0:
+            assert g["dp_tiles"] == tiles and g["tail_ctas"] == 0 and g["max_pieces"] == 1
+        elif waves >= 1 and (4 * rem <= units or 2 * rem >= units):
+            assert g["dp_tiles"] == (waves - 1) * units and g["tail_ctas"] == units, (tiles, kb, g)
+        else:
+            assert g["dp_tiles"] == waves * units, (tiles, kb, g)
+        cover = _streamk_units(g, tiles, kb, units)
+        assert sorted(cover) == list(range(tiles)), (tiles, kb)
+        most = 1
+        for t, segs in cover.items():
+            segs.sort()
+            assert segs[0][0] == 0 and segs[-1][1] == kb and all(a[1] == b[0] for a, b in zip(segs, segs[1:]))
+            n = segs[0][3]
+            assert [s[2] for s in segs] == list(range(n)) and all(s[3] == n for s in segs), (tiles, kb, t, segs)
+            most = max(most, n)
+        assert most == g["max_pieces"], (tiles, kb, g, most)
+        if waves >= 1:
+            assert most <= 2, (tiles, kb, g)
+    with pytest.raises(rg.RGError):
+        rg.rg_streamk_geometry(0, 4, units)
