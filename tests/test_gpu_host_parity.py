@@ -7,7 +7,8 @@ tables and values equal to the oracle's bit for bit; this module re-collects the
 with the gpu marker, so that they also run against the build whose numbers a
 benchmark on that host reports: full-grid T0*/T1/T2/action/q, leaves, the
 tie-heavy seeded cases, surface statistics (including the wide dynamic range),
-landscapes, rg_decompose, rg_kol, the pad-only fine-grid plan and FP8 plans."""
+landscapes, rg_decompose, rg_kol, the pad-only fine-grid plan, FP8 plans, the variant
+descriptions and the stream-K schedule's cover."""
 import pytest
 
 from test_abi_host import (  # noqa: F401  (re-collected tests and their fixture)
@@ -26,7 +27,9 @@ from test_abi_host import (  # noqa: F401  (re-collected tests and their fixture
     test_plan_tables_match_oracle_with_many_ties_seeded,
     test_surface_stats_bit_exact_over_a_wide_dynamic_range,
     test_surface_stats_match_oracle_bit_exact,
+    test_streamk_geometry_covers_every_k_iteration_once,
     test_surface_stats_non_step_grid,
+    test_variant_desc_agrees_with_the_binding,
 )
 
 pytestmark = pytest.mark.gpu
