@@ -354,7 +354,7 @@ int rg_group_create(rg_ctx* ctx, int32_t tile, int32_t max_items, int64_t worksp
 void rg_group_destroy(rg_group* group);
 int rg_gemm_grouped(rg_group* group, const rg_group_problem* problems, int32_t n, void* stream);
 
-/* ---- serving: continuous batching over the grouped GEMM (the benchmark spec serving form) ----
+/* ---- serving: continuous batching over the grouped GEMM ----
  * One engine serves GEMM requests of arbitrary shape with operands resident in
  * device memory.  Requests are admitted in arrival order once arrived and once
  * their operand bytes (2MK + 2KN + 4MN) fit under hbm_budget_bytes next to the
