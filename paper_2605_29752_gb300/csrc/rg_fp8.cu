@@ -11,11 +11,13 @@
 //   warp 0     TMA producer: A block 128 x 128 bytes (K-major) and B block 128 K-rows
 //              x BN bytes (N-major, 128-byte-wide column boxes), 128-byte swizzle.
 //   warp 1     one thread issues tcgen05.mma kind::f8f6f4 (M = 128, N = BN, K = 32) into
-//              one of two TMEM buffers, a fresh accumulator per 128-deep K block.
-//   warps 2-9  promotion and epilogue, two warps per TMEM lane quarter, each owning one
-//              half of the tile's columns: per K block, tcgen05.ld the block product,
-//              multiply by sA * sB (one scalar per warp and K block) and add into FP32
-//              registers; after the unit's last block, 128B-swizzled staging and a TMA
+//              one of 512 / BN TMEM buffers, a fresh accumulator per 128-deep K block.
+//   warps 2-3  idle: they complete warpgroup 0, whose registers go to the promotion warps.
+//   warps 4-11 promotion and epilogue (224 registers each), two warps per TMEM lane
+//              quarter, each owning one half of the tile's columns: per K block, tcgen05.ld
+//              the block product 64 columns per wait, multiply by sA * sB (one scalar per
+//              warp and K block) and add into FP32 registers; after the unit's last block,
+//              128B-swizzled staging and a TMA
 //              store (beta = 0) or reduce-add (beta = 1).  With S > 1 the unit's partial
 //              goes to the split-K workspace instead, and the last arriving split of a
 //              (tile, warp) sums the S partials in the fixed order 0..S-1.
@@ -46,10 +48,18 @@ namespace rg {
 namespace fp8 {
 
 constexpr int kEpiWarps = 8;                  // two promotion warps per TMEM lane quarter
-constexpr int kThreads = 32 * (2 + kEpiWarps);
+constexpr int kEpiWarp0 = 4;                  // the promotion warps are warpgroups 1 and 2
+constexpr int kThreads = 32 * (kEpiWarp0 + kEpiWarps);
+// Register split.  Three warps per SM sub-partition launch with 168 registers each;
+// warpgroup 0 (producer, MMA issuer and two idle warps) then shrinks to 56 and the
+// promotion warpgroups grow to 224 (setmaxnreg), which holds a thread's BN / 2
+// accumulators plus 64 columns of a K block's product.  The shares add up to the
+// launch's registers, per CTA and per sub-partition (one warp of each warpgroup).
+constexpr int kLaunchRegs = 168, kRegsLow = 56, kRegsHigh = 224;
+static_assert(4 * kRegsLow + kEpiWarps * kRegsHigh == (kThreads / 32) * kLaunchRegs, "register split");
+static_assert(kRegsLow + 2 * kRegsHigh == 3 * kLaunchRegs, "register split per sub-partition");
 constexpr int BM = 128, BK = 128;             // BK: one 128-byte swizzle row of e4m3 = one scale block
 constexpr int SB = 128;                       // scale block edge
-constexpr int NACC = 2;                       // TMEM accumulator buffers of BN columns
 constexpr int STAGING_PER_WARP = 2 * 4096;
 constexpr long long kDrainCycles = 1LL << 30;
 constexpr uint32_t FULL = 0xffffffffu;
@@ -63,17 +73,29 @@ struct Cfg {
   static constexpr int A_BYTES = BM * BK;
   static constexpr int B_BYTES = BK * BN / CTAS;  // (BN / CTAS) / 128 N-major column boxes of BK rows
   static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+  static constexpr int NACC = 512 / BN;       // TMEM accumulator buffers of BN columns: all 512 columns
   static constexpr int TMEM_COLS = NACC * BN;
   static constexpr int STAGING_OFF = STAGES * STAGE_BYTES;
   static constexpr int BAR_OFF = STAGING_OFF + kEpiWarps * STAGING_PER_WARP;
   static constexpr int SMEM_BYTES = 1024 + BAR_OFF + 256;
   static constexpr int HALF = BN / 2;         // columns per promotion warp
+  static constexpr int LDG = 64;              // columns of a K block's product read per TMEM wait
   // E4M3 x E4M3, A K-major, B MN-major; M = 256 across a pair
   static constexpr uint32_t IDESC = instr_desc(0, 0, 0, 1, 128 * CTAS, BN);
   static_assert(SMEM_BYTES <= 232448, "shared memory budget");
   static_assert(BN == 128 || BN == 256, "tile width");
   static_assert(!PAIR || BN == 256, "pair tile");
+  static_assert((2 * STAGES + 2 * NACC + 1) * 8 + 8 <= 256, "barrier block");
 };
+
+template <uint32_t N>
+__device__ __forceinline__ void setmaxnreg_inc() {
+  asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(N));
+}
+template <uint32_t N>
+__device__ __forceinline__ void setmaxnreg_dec() {
+  asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(N));
+}
 
 // Arrive on an mbarrier given by its shared::cluster address with relaxed semantics: the pair's
 // "accumulator buffer read" signal publishes no memory (the TMEM reads it covers have completed,
@@ -154,9 +176,9 @@ __device__ __forceinline__ void fp8_body(const CUtensorMap& tmA, const CUtensorM
   auto full_bar = [&](int i) { return bar0 + 8u * i; };
   auto empty_bar = [&](int i) { return bar0 + 8u * (C::STAGES + i); };
   auto tfull_bar = [&](int b) { return bar0 + 8u * (2 * C::STAGES + b); };
-  auto tempty_bar = [&](int b) { return bar0 + 8u * (2 * C::STAGES + NACC + b); };
-  const uint32_t drain_bar = bar0 + 8u * (2 * C::STAGES + 2 * NACC);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * C::STAGES + 2 * NACC + 1);
+  auto tempty_bar = [&](int b) { return bar0 + 8u * (2 * C::STAGES + C::NACC + b); };
+  const uint32_t drain_bar = bar0 + 8u * (2 * C::STAGES + 2 * C::NACC);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * C::STAGES + 2 * C::NACC + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   int never = 0;
   volatile int* no_abort = &never;
@@ -192,7 +214,7 @@ __device__ __forceinline__ void fp8_body(const CUtensorMap& tmA, const CUtensorM
       mbar_init(full_bar(i), 1);
       mbar_init(empty_bar(i), 1);
     }
-    for (int b = 0; b < NACC; ++b) {
+    for (int b = 0; b < C::NACC; ++b) {
       mbar_init(tfull_bar(b), 1);
       mbar_init(tempty_bar(b), PAIR ? 2 * kEpiWarps : kEpiWarps);  // pair: both CTAs' warps, on the even CTA
     }
@@ -216,123 +238,128 @@ __device__ __forceinline__ void fp8_body(const CUtensorMap& tmA, const CUtensorM
   const uint32_t tmem_base = *tmem_slot;
   grid_dependency_wait();
   grid_launch_dependents();
-
-  if (warp == 0) {
-    if (lane == 0) {
-      int stage = 0, fills = 0;
-      uint32_t ph = 0, issued_mask = 0, issued_ph = 0;
-      bool ok = true;
-      for (int u = cid; ok && u < total; u += ncl) {
-        const int s = u % S;
-        int tm, tn;
-        tile_of(u, tm, tn);
-        const int kb1 = s + 1 == S ? args.kblocks : kb_lo(s + 1);
-        for (int kb = kb_lo(s); kb < kb1; ++kb) {
-          if (fills >= C::STAGES && !mbar_wait(empty_bar(stage), ph ^ 1u, args.timeout, abort_flag)) {
-            ok = false;
-            break;
+  // Role branches; each warpgroup first resizes its registers (setmaxnreg acts on whole
+  // warpgroups, so warps 0-3 take the same instruction before they part).
+  if (warp < kEpiWarp0) {
+    setmaxnreg_dec<kRegsLow>();
+    if (warp == 0) {
+      if (lane == 0) {
+        int stage = 0, fills = 0;
+        uint32_t ph = 0, issued_mask = 0, issued_ph = 0;
+        bool ok = true;
+        for (int u = cid; ok && u < total; u += ncl) {
+          const int s = u % S;
+          int tm, tn;
+          tile_of(u, tm, tn);
+          const int kb1 = s + 1 == S ? args.kblocks : kb_lo(s + 1);
+          for (int kb = kb_lo(s); kb < kb1; ++kb) {
+            if (fills >= C::STAGES && !mbar_wait(empty_bar(stage), ph ^ 1u, args.timeout, abort_flag)) {
+              ok = false;
+              break;
+            }
+            ++fills;
+            const uint32_t sa = sbase + stage * C::STAGE_BYTES;
+            if constexpr (PAIR) {
+              // both CTAs' loads complete on the even CTA's full barrier, which expects both halves
+              if (rank == 0) mbar_arrive_expect_tx(full_bar(stage), 2 * C::STAGE_BYTES);
+              const uint32_t fb = mapa_shared(full_bar(stage), 0);
+              tma_load_2d_pair(sa, &tmA, fb, kb * BK, tm * BM);
+              tma_load_2d_pair(sa + C::A_BYTES, &tmB, fb, tn * BN + rank * (BN / 2), kb * BK);
+            } else {
+              mbar_arrive_expect_tx(full_bar(stage), C::STAGE_BYTES);
+              tma_load_2d(sa, &tmA, full_bar(stage), kb * BK, tm * BM);
+  #pragma unroll
+              for (int j = 0; j < BN / 128; ++j)
+                tma_load_2d(sa + C::A_BYTES + j * (BK * 128), &tmB, full_bar(stage), tn * BN + j * 128, kb * BK);
+            }
+            issued_mask |= 1u << stage;
+            issued_ph = (issued_ph & ~(1u << stage)) | (ph << stage);
+            if (++stage == C::STAGES) {
+              stage = 0;
+              ph ^= 1u;
+            }
           }
-          ++fills;
-          const uint32_t sa = sbase + stage * C::STAGE_BYTES;
-          if constexpr (PAIR) {
-            // both CTAs' loads complete on the even CTA's full barrier, which expects both halves
-            if (rank == 0) mbar_arrive_expect_tx(full_bar(stage), 2 * C::STAGE_BYTES);
-            const uint32_t fb = mapa_shared(full_bar(stage), 0);
-            tma_load_2d_pair(sa, &tmA, fb, kb * BK, tm * BM);
-            tma_load_2d_pair(sa + C::A_BYTES, &tmB, fb, tn * BN + rank * (BN / 2), kb * BK);
-          } else {
-            mbar_arrive_expect_tx(full_bar(stage), C::STAGE_BYTES);
-            tma_load_2d(sa, &tmA, full_bar(stage), kb * BK, tm * BM);
-#pragma unroll
-            for (int j = 0; j < BN / 128; ++j)
-              tma_load_2d(sa + C::A_BYTES + j * (BK * 128), &tmB, full_bar(stage), tn * BN + j * 128, kb * BK);
-          }
-          issued_mask |= 1u << stage;
-          issued_ph = (issued_ph & ~(1u << stage)) | (ph << stage);
-          if (++stage == C::STAGES) {
-            stage = 0;
-            ph ^= 1u;
+        }
+        if (!ok) {
+          atomicExch(args.err, 1);
+          *abort_flag = 1;
+        }
+        // no TMA write may still be landing when the CTA exits
+        if (!PAIR || rank == 0) {
+          for (int i = 0; i < C::STAGES; ++i)
+            if (issued_mask & (1u << i)) mbar_wait(full_bar(i), (issued_ph >> i) & 1u, kDrainCycles, no_abort);
+        } else if (!ok) {
+          // the odd CTA's loads complete on its partner's barriers; after an abort it gives
+          // them a bounded time to land (normally every one of them was consumed)
+          const long long t0 = clock64();
+          while (clock64() - t0 < (kDrainCycles >> 6)) {
           }
         }
       }
-      if (!ok) {
-        atomicExch(args.err, 1);
-        *abort_flag = 1;
-      }
-      // no TMA write may still be landing when the CTA exits
-      if (!PAIR || rank == 0) {
-        for (int i = 0; i < C::STAGES; ++i)
-          if (issued_mask & (1u << i)) mbar_wait(full_bar(i), (issued_ph >> i) & 1u, kDrainCycles, no_abort);
-      } else if (!ok) {
-        // the odd CTA's loads complete on its partner's barriers; after an abort it gives
-        // them a bounded time to land (normally every one of them was consumed)
-        const long long t0 = clock64();
-        while (clock64() - t0 < (kDrainCycles >> 6)) {
+    } else if (warp == 1) {
+      // Lane 0 alone issues the MMAs and commits (no per-K-block warp vote); a pair's
+      // odd CTA issues nothing: the even CTA's MMAs read and write both.
+      if (lane == 0 && (!PAIR || rank == 0)) {
+        int stage = 0, acc = 0;
+        uint32_t ph = 0, aph = 0;
+        bool ok = true;
+        for (int u = cid; ok && u < total; u += ncl) {
+          const int s = u % S;
+          const int kb1 = s + 1 == S ? args.kblocks : kb_lo(s + 1);
+          for (int kb = kb_lo(s); kb < kb1; ++kb) {
+            ok = mbar_wait(tempty_bar(acc), aph ^ 1u, args.timeout, abort_flag);
+            if (!ok) break;
+            ok = mbar_wait(full_bar(stage), ph, args.timeout, abort_flag);
+            if (!ok) break;
+            tc_fence_after();
+            const uint32_t sa = sbase + stage * C::STAGE_BYTES;
+            const uint32_t sb = sa + C::A_BYTES;
+            const uint32_t d = tmem_base + static_cast<uint32_t>(acc * BN);
+            // K steps differ only in the descriptors' start address field (address >> 4)
+            const uint64_t adesc0 = smem_desc_sw128(sa, 16, 1024);
+            const uint64_t bdesc0 = smem_desc_sw128(sb, BK * 128, 1024);  // column boxes BK*128 apart
+  #pragma unroll
+            for (int k = 0; k < BK / 32; ++k) {
+              const uint64_t ad = adesc0 + static_cast<uint64_t>((k * 32) >> 4);
+              const uint64_t bd = bdesc0 + static_cast<uint64_t>((k * (32 * 128)) >> 4);
+              if constexpr (PAIR)
+                mma_f8_pair(d, ad, bd, C::IDESC, k > 0 ? 1u : 0u);
+              else
+                mma_f8(d, ad, bd, C::IDESC, k > 0 ? 1u : 0u);
+            }
+            if constexpr (PAIR) {
+              mma_commit_pair_multicast(empty_bar(stage), 3);  // the stage is free in both CTAs
+              mma_commit_pair_multicast(tfull_bar(acc), 3);    // both CTAs' rows of the product are ready
+            } else {
+              mma_commit(empty_bar(stage));
+              mma_commit(tfull_bar(acc));
+            }
+            if (++stage == C::STAGES) {
+              stage = 0;
+              ph ^= 1u;
+            }
+            if (++acc == C::NACC) {
+              acc = 0;
+              aph ^= 1u;
+            }
+          }
+        }
+        if (!ok) {
+          atomicExch(args.err, 2);
+          *abort_flag = 1;
+          if constexpr (PAIR)
+            mma_commit_pair(drain_bar);
+          else
+            mma_commit(drain_bar);  // completes once every issued MMA has finished
+          mbar_wait(drain_bar, 0, kDrainCycles, no_abort);
         }
       }
+      __syncwarp();
     }
-  } else if (warp == 1) {
-    // Lane 0 alone issues the MMAs and commits (no per-K-block warp vote); a pair's
-    // odd CTA issues nothing: the even CTA's MMAs read and write both.
-    if (lane == 0 && (!PAIR || rank == 0)) {
-      int stage = 0, acc = 0;
-      uint32_t ph = 0, aph = 0;
-      bool ok = true;
-      for (int u = cid; ok && u < total; u += ncl) {
-        const int s = u % S;
-        const int kb1 = s + 1 == S ? args.kblocks : kb_lo(s + 1);
-        for (int kb = kb_lo(s); kb < kb1; ++kb) {
-          ok = mbar_wait(tempty_bar(acc), aph ^ 1u, args.timeout, abort_flag);
-          if (!ok) break;
-          ok = mbar_wait(full_bar(stage), ph, args.timeout, abort_flag);
-          if (!ok) break;
-          tc_fence_after();
-          const uint32_t sa = sbase + stage * C::STAGE_BYTES;
-          const uint32_t sb = sa + C::A_BYTES;
-          const uint32_t d = tmem_base + static_cast<uint32_t>(acc * BN);
-          // K steps differ only in the descriptors' start address field (address >> 4)
-          const uint64_t adesc0 = smem_desc_sw128(sa, 16, 1024);
-          const uint64_t bdesc0 = smem_desc_sw128(sb, BK * 128, 1024);  // column boxes BK*128 apart
-#pragma unroll
-          for (int k = 0; k < BK / 32; ++k) {
-            const uint64_t ad = adesc0 + static_cast<uint64_t>((k * 32) >> 4);
-            const uint64_t bd = bdesc0 + static_cast<uint64_t>((k * (32 * 128)) >> 4);
-            if constexpr (PAIR)
-              mma_f8_pair(d, ad, bd, C::IDESC, k > 0 ? 1u : 0u);
-            else
-              mma_f8(d, ad, bd, C::IDESC, k > 0 ? 1u : 0u);
-          }
-          if constexpr (PAIR) {
-            mma_commit_pair_multicast(empty_bar(stage), 3);  // the stage is free in both CTAs
-            mma_commit_pair_multicast(tfull_bar(acc), 3);    // both CTAs' rows of the product are ready
-          } else {
-            mma_commit(empty_bar(stage));
-            mma_commit(tfull_bar(acc));
-          }
-          if (++stage == C::STAGES) {
-            stage = 0;
-            ph ^= 1u;
-          }
-          if (++acc == NACC) {
-            acc = 0;
-            aph ^= 1u;
-          }
-        }
-      }
-      if (!ok) {
-        atomicExch(args.err, 2);
-        *abort_flag = 1;
-        if constexpr (PAIR)
-          mma_commit_pair(drain_bar);
-        else
-          mma_commit(drain_bar);  // completes once every issued MMA has finished
-        mbar_wait(drain_bar, 0, kDrainCycles, no_abort);
-      }
-    }
-    __syncwarp();
   } else {
-    // promotion warps 2..9: lane quarter q (the TMEM lanes this warp may read), column half hc
-    const int e = warp - 2;
+    setmaxnreg_inc<kRegsHigh>();
+    // promotion warps 4..11: lane quarter q (the TMEM lanes this warp may read), column half hc
+    const int e = warp - kEpiWarp0;
     const int q = warp & 3;
     const int hc = e / 4;
     const uint32_t stg0 = sbase + C::STAGING_OFF + e * STAGING_PER_WARP;
@@ -370,12 +397,18 @@ __device__ __forceinline__ void fp8_body(const CUtensorMap& tmA, const CUtensorM
         const uint32_t t = tmem_base + (static_cast<uint32_t>(q * 32) << 16) +
                            static_cast<uint32_t>(acc * BN + hc * C::HALF);
 #pragma unroll
-        for (int c = 0; c < C::HALF / 32; ++c) {
-          uint32_t p[32];
-          tmem_ld_32x32b_x32(t + c * 32, p);
+        for (int c = 0; c < C::HALF / C::LDG; ++c) {
+          uint32_t p[C::LDG / 32][32];
+#pragma unroll
+          for (int j = 0; j < C::LDG / 32; ++j) tmem_ld_32x32b_x32(t + c * C::LDG + j * 32, p[j]);
           tmem_ld_wait();
 #pragma unroll
-          for (int i = 0; i < 32; ++i) r[c * 32 + i] = fmaf(sc, __uint_as_float(p[i]), r[c * 32 + i]);
+          for (int j = 0; j < C::LDG / 32; ++j)
+#pragma unroll
+            for (int i = 0; i < 32; ++i) {
+              float& acc_v = r[c * C::LDG + j * 32 + i];
+              acc_v = fmaf(sc, __uint_as_float(p[j][i]), acc_v);
+            }
         }
         tc_fence_before();
         __syncwarp();
@@ -385,7 +418,7 @@ __device__ __forceinline__ void fp8_body(const CUtensorMap& tmA, const CUtensorM
           else
             mbar_arrive(tempty_bar(acc));
         }
-        if (++acc == NACC) {
+        if (++acc == C::NACC) {
           acc = 0;
           aph ^= 1u;
         }
@@ -568,6 +601,16 @@ static int kernels_ready() {
     for (KernFn fn : {ti.fn, ti.fn_split}) {
       e = cudaFuncSetAttribute(reinterpret_cast<const void*>(fn), cudaFuncAttributeMaxDynamicSharedMemorySize, ti.smem);
       if (e != cudaSuccess) return fail(RG_ERR_CUDA, "FP8: shared-memory attribute");
+      // The register split grows the promotion warps to what warpgroup 0 gives back, so it
+      // holds only if every thread launches with exactly kLaunchRegs registers: a kernel built
+      // with fewer would wait forever in setmaxnreg.inc, and is never launched.
+      cudaFuncAttributes fa{};
+      e = cudaFuncGetAttributes(&fa, reinterpret_cast<const void*>(fn));
+      if (e != cudaSuccess) return fail(RG_ERR_CUDA, "FP8: kernel attributes");
+      if (fa.numRegs != kLaunchRegs)
+        return fail(RG_ERR_CUDA, "FP8: kernel built with " + std::to_string(fa.numRegs) +
+                                     " registers per thread; its register split needs " +
+                                     std::to_string(kLaunchRegs));
     }
   }
   if (dev >= 0 && dev < 64) done[dev] = true;
