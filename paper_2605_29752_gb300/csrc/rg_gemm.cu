@@ -6,7 +6,8 @@
 // Kernel structure (one CTA per SM, persistent over output tiles x K splits):
 //   warp 0     TMA producer: A tile (BM x 64, K-major, 128B swizzle) and B tile
 //              (64 x BN, N-major, 128B swizzle, 64-column boxes) into an
-//              mbarrier-guarded ring of STAGES shared-memory stages.
+//              mbarrier-guarded ring of STAGES shared-memory stages of one K
+//              block, or two for 128x64, 128x128 and the 256x128 pair.
 //   warp 1     allocates TMEM; one thread issues tcgen05.mma (M = 128, N = BN,
 //              K = 16) into a TMEM accumulator, double-buffered when it fits,
 //              and commits stage releases / accumulator-full to mbarriers.
@@ -45,7 +46,7 @@
 namespace rg {
 
 constexpr int kThreads = 192;
-constexpr int kBK = 64;                       // K per stage: one 128-byte swizzle row of BF16
+constexpr int kBK = 64;                       // K per block: one 128-byte swizzle row of BF16
 constexpr int kStagingPerWarp = 2 * 32 * 32 * 4;  // two 32x32 FP32 staging tiles per epilogue warp
 constexpr int kMaxTickets = 1 << 18;
 constexpr uint32_t FULL = 0xffffffffu;
@@ -105,12 +106,18 @@ struct GemmArgs {
 // columns of B in its shared memory, M = 256 per MMA instruction).
 template <int BM, int BN, int STAGES, int CTAS = 1>
 struct KCfg {
+  // K blocks per ring stage.  Every stage costs one full/empty barrier round, and a stage
+  // of one 64-deep K block of a 128-row tile with N <= 128 holds less MMA work than that
+  // round takes; those tiles (128x64, 128x128 and the 256x128 pair's CTAs) put two K
+  // blocks in a stage, with half as many stages in the same bytes.
+  static constexpr int SUB = (BM == 128 && BN <= 128) ? 2 : 1;
   static constexpr int A_BYTES = BM * kBK * 2;
   // B columns a CTA loads: its BN / CTAS rounded up to whole 64-column (128-byte) boxes
   // (a 256x192 pair's CTA loads 128 columns, of which its MMAs read 96)
   static constexpr int BN_LOAD = (BN / CTAS + 63) / 64 * 64;
   static constexpr int B_BYTES = kBK * BN_LOAD * 2;
-  static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+  static constexpr int SUB_BYTES = A_BYTES + B_BYTES;  // one K block: A, then B
+  static constexpr int STAGE_BYTES = SUB * SUB_BYTES;
   static constexpr int HALVES = BM / 128;
   static constexpr int ACC_COLS = HALVES * BN;
   static constexpr int NBUF = (2 * ACC_COLS <= 512) ? 2 : 1;
@@ -683,29 +690,38 @@ __device__ __forceinline__ void gemm_body(Sched& sched, float* ws, int32_t* tick
           tensormap_fence_acquire(w.a);
           tensormap_fence_acquire(w.b);
         }
-        for (int kb = w.kb0; kb < w.kb1; ++kb) {
+        for (int kbs = w.kb0; kbs < w.kb1; kbs += C::SUB) {
+          const int nsub = w.kb1 - kbs < C::SUB ? w.kb1 - kbs : C::SUB;  // K blocks in this stage
           // a stage's first fill needs no wait: nothing has used it yet
           if (fills >= STAGES && !mbar_wait(empty_bar(stage), ph ^ 1u, timeout, abort_flag)) {
             ok = false;
             break;
           }
           ++fills;
-          const uint32_t sa = sbase + stage * C::STAGE_BYTES;
-          const uint32_t sb = sa + C::A_BYTES;
           if constexpr (P2) {
             // Both CTAs' loads complete on the even CTA's full barrier, which expects both halves.
-            if (sched.rank == 0) mbar_arrive_expect_tx(full_bar(stage), 2 * C::STAGE_BYTES);
+            if (sched.rank == 0) mbar_arrive_expect_tx(full_bar(stage), 2 * nsub * C::SUB_BYTES);
             const uint32_t fb = mapa_shared(full_bar(stage), 0);
-            tma_load_2d_pair(sa, w.a, fb, kb * kBK, w.tm * BM);
+            for (int u = 0; u < nsub; ++u) {
+              const int kb = kbs + u;
+              const uint32_t sa = sbase + stage * C::STAGE_BYTES + u * C::SUB_BYTES;
+              const uint32_t sb = sa + C::A_BYTES;
+              tma_load_2d_pair(sa, w.a, fb, kb * kBK, w.tm * BM);
 #pragma unroll
-            for (int j = 0; j < C::BN_LOAD / 64; ++j)
-              tma_load_2d_pair(sb + j * (kBK * 128), w.b, fb, w.tn * BN + sched.rank * (BN / 2) + j * 64, kb * kBK);
+              for (int j = 0; j < C::BN_LOAD / 64; ++j)
+                tma_load_2d_pair(sb + j * (kBK * 128), w.b, fb, w.tn * BN + sched.rank * (BN / 2) + j * 64, kb * kBK);
+            }
           } else {
-            mbar_arrive_expect_tx(full_bar(stage), C::STAGE_BYTES);
-            tma_load_2d(sa, w.a, full_bar(stage), kb * kBK, w.tm * BM);
+            mbar_arrive_expect_tx(full_bar(stage), nsub * C::SUB_BYTES);
+            for (int u = 0; u < nsub; ++u) {
+              const int kb = kbs + u;
+              const uint32_t sa = sbase + stage * C::STAGE_BYTES + u * C::SUB_BYTES;
+              const uint32_t sb = sa + C::A_BYTES;
+              tma_load_2d(sa, w.a, full_bar(stage), kb * kBK, w.tm * BM);
 #pragma unroll
-            for (int j = 0; j < BN / 64; ++j)
-              tma_load_2d(sb + j * (kBK * 128), w.b, full_bar(stage), w.tn * BN + j * 64, kb * kBK);
+              for (int j = 0; j < BN / 64; ++j)
+                tma_load_2d(sb + j * (kBK * 128), w.b, full_bar(stage), w.tn * BN + j * 64, kb * kBK);
+            }
           }
           issued_mask |= 1u << stage;
           issued_ph = (issued_ph & ~(1u << stage)) | (ph << stage);
@@ -751,32 +767,35 @@ __device__ __forceinline__ void gemm_body(Sched& sched, float* ws, int32_t* tick
         if (!ok) break;
         tc_fence_after();
         const uint32_t d0 = tmem_base + static_cast<uint32_t>(acc * C::ACC_COLS);
-        for (int kb = kb0; kb < kb1; ++kb) {
+        for (int kbs = kb0; kbs < kb1; kbs += C::SUB) {
+          const int nsub = kb1 - kbs < C::SUB ? kb1 - kbs : C::SUB;  // K blocks in this stage
           ok = mbar_wait(full_bar(stage), ph, timeout, abort_flag);
           if (!ok) break;
-          if (i == 0 && kb == kb0) RG_STAMP(4);
+          if (i == 0 && kbs == kb0) RG_STAMP(4);
           tc_fence_after();
           if constexpr (Sched::kMemOnly) {
             mbar_arrive(empty_bar(stage));  // no MMA reads the stage: it is free once its bytes have landed
           } else {
-            const uint32_t sa = sbase + stage * C::STAGE_BYTES;
-            const uint32_t sb = sa + C::A_BYTES;
-            // The descriptors of the stage's K steps differ only in their start
-            // address field (bits 0-13, address >> 4; no carry: shared addresses
-            // stay below 2^18), so they are the stage's base descriptors plus constants.
-            const uint64_t adesc0 = smem_desc_sw128(sa, 16, 1024);
-            const uint64_t bdesc0 = smem_desc_sw128(sb, kBK * 128, 1024);
-            const uint32_t first = kb > kb0 ? 1u : 0u;
+            for (int u = 0; u < nsub; ++u) {
+              const uint32_t sa = sbase + stage * C::STAGE_BYTES + u * C::SUB_BYTES;
+              const uint32_t sb = sa + C::A_BYTES;
+              // The descriptors of the block's K steps differ only in their start
+              // address field (bits 0-13, address >> 4; no carry: shared addresses
+              // stay below 2^18), so they are the block's base descriptors plus constants.
+              const uint64_t adesc0 = smem_desc_sw128(sa, 16, 1024);
+              const uint64_t bdesc0 = smem_desc_sw128(sb, kBK * 128, 1024);
+              const uint32_t first = kbs + u > kb0 ? 1u : 0u;
 #pragma unroll
-            for (int k = 0; k < kBK / 16; ++k) {
-              const uint64_t bdesc = bdesc0 + static_cast<uint64_t>((k * 2048) >> 4);
+              for (int k = 0; k < kBK / 16; ++k) {
+                const uint64_t bdesc = bdesc0 + static_cast<uint64_t>((k * 2048) >> 4);
 #pragma unroll
-              for (int h = 0; h < C::HALVES; ++h) {
-                const uint64_t adesc = adesc0 + static_cast<uint64_t>((h * (128 * 128) + k * 32) >> 4);
-                if constexpr (P2)
-                  mma_f16_pair(d0, adesc, bdesc, C::IDESC, k > 0 ? 1u : first);
-                else
-                  mma_f16(d0 + h * BN, adesc, bdesc, C::IDESC, k > 0 ? 1u : first);
+                for (int h = 0; h < C::HALVES; ++h) {
+                  const uint64_t adesc = adesc0 + static_cast<uint64_t>((h * (128 * 128) + k * 32) >> 4);
+                  if constexpr (P2)
+                    mma_f16_pair(d0, adesc, bdesc, C::IDESC, k > 0 ? 1u : first);
+                  else
+                    mma_f16(d0 + h * BN, adesc, bdesc, C::IDESC, k > 0 ? 1u : first);
+                }
               }
             }
             if constexpr (P2)
@@ -1264,9 +1283,10 @@ struct TileKernel {
   int ring;             // bytes of the operand ring (the cluster split-K receive space)
 };
 
-// Stages of the cta_group::2 instances: 16 KB of A + BN/2 x 64 of B per stage and CTA.
+// Stages of the cta_group::2 instances, per CTA: 16 KB of A + BN/2 x 64 of B per K block;
+// the 256x128 pair's stages hold two K blocks.
 template <int BN>
-constexpr int kStages2Sm = BN == 128 ? 8 : 6;
+constexpr int kStages2Sm = BN == 128 ? 4 : 6;
 
 template <int BM, int BN, int ST>
 TileKernel make_tile_kernel() {
@@ -1285,7 +1305,7 @@ TileKernel make_tile_kernel() {
 
 static const TileKernel& tile_kernel(int tile) {
   static const TileKernel table[RG_NUM_TILES] = {
-      make_tile_kernel<128, 64, 8>(),  make_tile_kernel<128, 128, 6>(), make_tile_kernel<128, 256, 4>(),
+      make_tile_kernel<128, 64, 4>(),  make_tile_kernel<128, 128, 3>(), make_tile_kernel<128, 256, 4>(),
       make_tile_kernel<256, 64, 4>(),  make_tile_kernel<256, 128, 4>(), make_tile_kernel<256, 256, 3>(),
       make_tile_kernel<128, 192, 4>(), make_tile_kernel<256, 192, 3>(),
   };
@@ -1299,7 +1319,7 @@ using GroupedFn = void (*)(const GroupHeader*, const GroupItem*, const CUtensorM
                            long long);
 static const void* grouped_kernel(int family) {
   static const GroupedFn table[kGroupFamilies] = {
-      gemm_bf16_grouped_kernel<128, 64, 8>,  gemm_bf16_grouped_kernel<128, 128, 6>,
+      gemm_bf16_grouped_kernel<128, 64, 4>,  gemm_bf16_grouped_kernel<128, 128, 3>,
       gemm_bf16_grouped_kernel<128, 256, 4>, gemm_bf16_grouped_kernel<256, 64, 4>,
       gemm_bf16_grouped_kernel<256, 128, 4>, gemm_bf16_grouped_kernel<256, 256, 3>,
       gemm_bf16_grouped_kernel<128, 192, 4>, gemm_bf16_grouped_kernel<256, 192, 3>,
