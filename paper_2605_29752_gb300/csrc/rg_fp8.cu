@@ -268,7 +268,7 @@ __device__ __forceinline__ void fp8_body(const CUtensorMap& tmA, const CUtensorM
             } else {
               mbar_arrive_expect_tx(full_bar(stage), C::STAGE_BYTES);
               tma_load_2d(sa, &tmA, full_bar(stage), kb * BK, tm * BM);
-  #pragma unroll
+#pragma unroll
               for (int j = 0; j < BN / 128; ++j)
                 tma_load_2d(sa + C::A_BYTES + j * (BK * 128), &tmB, full_bar(stage), tn * BN + j * 128, kb * BK);
             }
@@ -318,7 +318,7 @@ __device__ __forceinline__ void fp8_body(const CUtensorMap& tmA, const CUtensorM
             // K steps differ only in the descriptors' start address field (address >> 4)
             const uint64_t adesc0 = smem_desc_sw128(sa, 16, 1024);
             const uint64_t bdesc0 = smem_desc_sw128(sb, BK * 128, 1024);  // column boxes BK*128 apart
-  #pragma unroll
+#pragma unroll
             for (int k = 0; k < BK / 32; ++k) {
               const uint64_t ad = adesc0 + static_cast<uint64_t>((k * 32) >> 4);
               const uint64_t bd = bdesc0 + static_cast<uint64_t>((k * (32 * 128)) >> 4);
