@@ -764,6 +764,7 @@ CAPTURE_PROFILE = "gemm_bf16_256x256_2sm_8192x8192x4096"   # profiles/<name>.md 
 CAPTURE_VARIANT = "256x256/2SM"
 # ncu captures of kernels that can dominate the smoothed pass, each on a mid-size landscape cell it wins
 TRAFFIC_PROFILES = {"256x256/2SM": "gemm_bf16_256x256_2sm_2048x2048x4096",
+                    "128x128/S1": "gemm_bf16_128x128_2048x2048x4096",
                     "128x192/S1": "gemm_bf16_128x192_2048x1536x4096",
                     "256x192/S1": "gemm_bf16_256x192_4096x1536x4096"}
 
