@@ -167,6 +167,12 @@ template <int BN, bool SPLIT, bool PAIR>
 __device__ __forceinline__ void fp8_body(const CUtensorMap& tmA, const CUtensorMap& tmB, const CUtensorMap& tmC,
                                          const CUtensorMap& tmW, const Args& args) {
   using C = Cfg<BN, PAIR>;
+  // Coupled ring (as many stages as accumulator buffers, one CTA: the 128x128 tile): K block kb
+  // uses stage kb % STAGES and buffer kb % NACC, the same index.  The producer refills a stage
+  // only once the promotion warps have released its buffer, which they do after the block's
+  // MMAs completed, so a landed stage also means a free buffer: the MMA thread waits on one
+  // barrier and commits to one per K block.
+  constexpr bool COUPLED = C::NACC == C::STAGES && !PAIR;
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw_s = smem_u32(smem_raw);
   uint8_t* smem = smem_raw + ((1024u - (raw_s & 1023u)) & 1023u);
@@ -253,7 +259,8 @@ __device__ __forceinline__ void fp8_body(const CUtensorMap& tmA, const CUtensorM
           tile_of(u, tm, tn);
           const int kb1 = s + 1 == S ? args.kblocks : kb_lo(s + 1);
           for (int kb = kb_lo(s); kb < kb1; ++kb) {
-            if (fills >= C::STAGES && !mbar_wait(empty_bar(stage), ph ^ 1u, args.timeout, abort_flag)) {
+            if (fills >= C::STAGES &&
+                !mbar_wait(COUPLED ? tempty_bar(stage) : empty_bar(stage), ph ^ 1u, args.timeout, abort_flag)) {
               ok = false;
               break;
             }
@@ -307,8 +314,10 @@ __device__ __forceinline__ void fp8_body(const CUtensorMap& tmA, const CUtensorM
           const int s = u % S;
           const int kb1 = s + 1 == S ? args.kblocks : kb_lo(s + 1);
           for (int kb = kb_lo(s); kb < kb1; ++kb) {
-            ok = mbar_wait(tempty_bar(acc), aph ^ 1u, args.timeout, abort_flag);
-            if (!ok) break;
+            if constexpr (!COUPLED) {
+              ok = mbar_wait(tempty_bar(acc), aph ^ 1u, args.timeout, abort_flag);
+              if (!ok) break;
+            }
             ok = mbar_wait(full_bar(stage), ph, args.timeout, abort_flag);
             if (!ok) break;
             tc_fence_after();
@@ -331,7 +340,7 @@ __device__ __forceinline__ void fp8_body(const CUtensorMap& tmA, const CUtensorM
               mma_commit_pair_multicast(empty_bar(stage), 3);  // the stage is free in both CTAs
               mma_commit_pair_multicast(tfull_bar(acc), 3);    // both CTAs' rows of the product are ready
             } else {
-              mma_commit(empty_bar(stage));
+              if constexpr (!COUPLED) mma_commit(empty_bar(stage));
               mma_commit(tfull_bar(acc));
             }
             if (++stage == C::STAGES) {
