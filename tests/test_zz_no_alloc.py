@@ -106,7 +106,7 @@ def test_rejects_split_beyond_scratch(rg):
     scratch's ticket limit (RG_NOALLOC_MAX_TILES tiles, counted per 128-row tile) cannot be reached first:
     a launch with partials has at least 2 slots of at least 32 KiB per tile (128x64), so the 16 MiB of
     partials bound it to 256 tiles (512 counted for cta_group::2), far below 4096."""
-    assert 2 * 2 * (rg.RG_NOALLOC_PARTIAL_BYTES // (2 * 128 * 64 * 4)) <= rg.RG_NOALLOC_MAX_TILES
+    assert 2 * (rg.RG_NOALLOC_PARTIAL_BYTES // (2 * 128 * 64 * 4)) <= rg.RG_NOALLOC_MAX_TILES
     M = N = 4096
     K = 1024
     A = torch.zeros((M, K), device="cuda", dtype=torch.bfloat16)
