@@ -223,6 +223,34 @@ def test_fp8_pair_matches_one_cta_tile(rg, ctx, shape):
         _check_fp8(c2, *(x.cpu().numpy() for x in ops), K)
 
 
+@pytest.mark.parametrize("split", [1, 2])
+@pytest.mark.parametrize("shape", [(2048, 1536, 1152), (1000, 528, 1664), (256, 256, 4096)])
+def test_fp8_coupled_ring_128x128(rg, ctx, shape, split):
+    """The 128x128 tile pairs its four operand stages with its four accumulator buffers (the producer
+    refills a stage once the promotion warps released the buffer of the same index).  Shapes where CTAs run
+    several tiles, K-block counts that are not a multiple of the ring (9, 13) and a 32-block K: within the
+    FP8 bound of the float64 product of the dequantised operands, deterministic, and, at split 1, equal
+    bit for bit to the 128x256 tile, whose per-element MMA steps and promotion order are the same."""
+    M, N, K = shape
+    ops = _operands(rg, ctx, M, N, K, seed=12)
+    v = rg.fp8_variant(1, split)
+    c = _run_ex(rg, ctx, M, N, K, ops, v)
+    assert not np.any(np.isnan(c))
+    assert np.array_equal(c, _run_ex(rg, ctx, M, N, K, ops, v))
+    if split == 1:
+        assert np.array_equal(c, _run_ex(rg, ctx, M, N, K, ops, rg.fp8_variant(0, 1)))
+    host = [x.cpu().numpy() for x in ops]
+    if M * N * K <= 1024 ** 3:
+        _check_fp8(c, *host, K)
+    else:
+        rs = np.random.default_rng(5)
+        rows, cols = rs.choice(M, 16, replace=False), rs.choice(N, 16, replace=False)
+        A, B = of.dequantize(host[0], host[1]), of.dequantize(host[2], host[3])
+        for got, a, b in ((c[rows, :], A[rows, :], B), (c[:, cols], A, B[:, cols])):
+            ratio, exact_zero = og.error_ratio(got, a @ b, np.abs(a) @ np.abs(b))
+            assert exact_zero and ratio <= FP8_BOUND_FACTOR * K * 2.0 ** -24, ratio
+
+
 def test_fp8_scale_sub_views(rg, ctx):
     """A sub-problem of a quantised matrix (offsets multiples of 128) through its scale sub-views,
     with leading dimensions of the whole arrays."""
