@@ -173,6 +173,10 @@ __device__ __forceinline__ void fp8_body(const CUtensorMap& tmA, const CUtensorM
   // MMAs completed, so a landed stage also means a free buffer: the MMA thread waits on one
   // barrier and commits to one per K block.
   constexpr bool COUPLED = C::NACC == C::STAGES && !PAIR;
+  // Otherwise the MMA thread commits only to the accumulator-full barrier, and the first
+  // promotion warp of each CTA frees the K block's stage once it has seen that barrier (the
+  // block's MMAs, which read the stage, have completed): one commit per K block, not two.
+  constexpr bool STAGE_BY_PROMOTION = !COUPLED;
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw_s = smem_u32(smem_raw);
   uint8_t* smem = smem_raw + ((1024u - (raw_s & 1023u)) & 1023u);
@@ -337,10 +341,10 @@ __device__ __forceinline__ void fp8_body(const CUtensorMap& tmA, const CUtensorM
                 mma_f8(d, ad, bd, C::IDESC, k > 0 ? 1u : 0u);
             }
             if constexpr (PAIR) {
-              mma_commit_pair_multicast(empty_bar(stage), 3);  // the stage is free in both CTAs
+              if constexpr (!STAGE_BY_PROMOTION) mma_commit_pair_multicast(empty_bar(stage), 3);
               mma_commit_pair_multicast(tfull_bar(acc), 3);    // both CTAs' rows of the product are ready
             } else {
-              if constexpr (!COUPLED) mma_commit(empty_bar(stage));
+              if constexpr (!COUPLED && !STAGE_BY_PROMOTION) mma_commit(empty_bar(stage));
               mma_commit(tfull_bar(acc));
             }
             if (++stage == C::STAGES) {
@@ -372,7 +376,7 @@ __device__ __forceinline__ void fp8_body(const CUtensorMap& tmA, const CUtensorM
     const int q = warp & 3;
     const int hc = e / 4;
     const uint32_t stg0 = sbase + C::STAGING_OFF + e * STAGING_PER_WARP;
-    int acc = 0, sbuf = 0;
+    int acc = 0, sbuf = 0, pstage = 0;  // pstage: the operand stage of the current K block
     uint32_t aph = 0;
     bool ok = true;
     for (int u = cid; ok && u < total; u += ncl) {
@@ -402,6 +406,10 @@ __device__ __forceinline__ void fp8_body(const CUtensorMap& tmA, const CUtensorM
         const float sc = __shfl_sync(FULL, sc_lane, rel & 31);
         ok = __all_sync(FULL, mbar_wait(tfull_bar(acc), aph, args.timeout, abort_flag));
         if (!ok) break;
+        if constexpr (STAGE_BY_PROMOTION) {
+          if (e == 0 && lane == 0) mbar_arrive(empty_bar(pstage));  // this CTA's copy of the stage is free
+          if (++pstage == C::STAGES) pstage = 0;
+        }
         tc_fence_after();
         const uint32_t t = tmem_base + (static_cast<uint32_t>(q * 32) << 16) +
                            static_cast<uint32_t>(acc * BN + hc * C::HALF);
