@@ -11,16 +11,18 @@
 //   warp 0     TMA producer: A block 128 x 128 bytes (K-major) and B block 128 K-rows
 //              x BN bytes (N-major, 128-byte-wide column boxes), 128-byte swizzle.
 //   warp 1     one thread issues tcgen05.mma kind::f8f6f4 (M = 128, N = BN, K = 32) into
-//              one of 512 / BN TMEM buffers, a fresh accumulator per 128-deep K block.
+//              one of 512 / BN TMEM buffers, a fresh accumulator per 128-deep K block,
+//              and commits once per K block to the buffer's full barrier.
 //   warps 2-3  idle: they complete warpgroup 0, whose registers go to the promotion warps.
 //   warps 4-11 promotion and epilogue (224 registers each), two warps per TMEM lane
 //              quarter, each owning one half of the tile's columns: per K block, tcgen05.ld
 //              the block product 64 columns per wait, multiply by sA * sB (one scalar per
 //              warp and K block) and add into FP32 registers; after the unit's last block,
-//              128B-swizzled staging and a TMA
-//              store (beta = 0) or reduce-add (beta = 1).  With S > 1 the unit's partial
-//              goes to the split-K workspace instead, and the last arriving split of a
-//              (tile, warp) sums the S partials in the fixed order 0..S-1.
+//              128B-swizzled staging and a TMA store (beta = 0) or reduce-add (beta = 1).
+//              With S > 1 the unit's partial goes to the split-K workspace instead, and the
+//              last arriving split of a (tile, warp) sums the S partials in the fixed order
+//              0..S-1.  Their release of a buffer (and, through warp 4, of the K block's
+//              operand stage) is what lets the producer and the MMA thread reuse it.
 // The 256 x 256 tile also runs as a tcgen05 cta_group::2 pair (gemm_fp8_2sm_kernel):
 // each CTA of a 2-CTA cluster loads its 128 rows of A and 128 columns of B, the even
 // CTA issues the M = 256 MMAs, and each CTA promotes and stores its own 128 rows.
