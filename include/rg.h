@@ -463,7 +463,9 @@ int rg_serve_stop(rg_server* server, rg_serve_stats* stats);
  * it; (pm, pn, pk) >= (M, N, K) run it as the zero-padded problem of that size (0
  * = same), never materialised (zero-filled reads, clipped stores, scales of
  * padding blocks read as 0).  Errors as rg_gemm (RG_ERR_SHAPE when split-K
- * partials exceed the workspace).  rg_gemm_fp8 = rg_gemm_fp8_ex with variant
+ * partials exceed the workspace), and RG_ERR_CUDA, before any launch, when the
+ * library's FP8 kernels were not built with the 168 registers per thread that
+ * their in-kernel register split (setmaxnreg) adds up to.  rg_gemm_fp8 = rg_gemm_fp8_ex with variant
  * RG_FP8_VARIANT(0, 0), compact scales (lds_a = ceil(K/128), lds_b = ceil(N/128)),
  * beta 0 and no padding.
  * rg_gemm_fp8_plan: the O(1) plan lookup (Sec. 7.1) of an FP8 plan (a plan built
